@@ -1,0 +1,410 @@
+"""Benchmark: FastFCA IP+EM throughput (time-frequency-bin iterations per second) on GB300.
+
+One step = one complete FastFCA run on the M=4, N=6, F=513, T=1250 workload (100 IP+EM
+iterations, Algorithm 1, then the Wiener-filter separation of Eq. 39), starting from the
+seeded random initialisation, through the library's C ABI.  The metric counts F*T*iters
+bin-iterations per step.  Inputs are model-generated (synthetic) and resident in HBM when a
+timed step starts; L2 is flushed (a 512 MiB write) between steps, outside the timed spans.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank separates its own mixture (independent problems, no data
+collective): weak scaling, value = all ranks' bin-iterations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2101_08563_gb300 import synth  # noqa: E402
+
+WORKLOAD = synth.WORKLOADS["fca_cmp"]
+METRIC = "FastFCA EM TF-bin-iters/s"
+UNIT = "bin-iters/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 arithmetic peak from unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x
+# 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops_per_bin_iter(M: int, N: int) -> float:
+    """FP32 flops one bin-iteration of Algorithm 1 needs (excluding the per-frequency IP):
+    Q accumulation 6*M(M+1)/2 + 4*M*M(M+1)/2, decorrelation 8M^2, U 3M, NMF EM 13*M*N,
+    log-likelihood terms 4M."""
+    tri = M * (M + 1) / 2
+    return 6 * tri + 4 * M * tri + 8 * M * M + 3 * M + 13 * M * N + 4 * M
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+_WORKER_STATE = {}
+
+
+def _pool_init(seed_index):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    w = WORKLOAD
+    mix = synth.workload_mixture(w, seed_index)
+    init = synth.random_init(mix.x, w.N, seed=w.seed + seed_index)
+    _WORKER_STATE["x"] = mix.x
+    _WORKER_STATE["init"] = init
+
+
+def _noop(_):
+    return 0
+
+
+def _oracle_worker(args):
+    """Algorithm 1 (with the per-iteration log-likelihood) and Eq. 39 on a list of
+    frequencies of the workload mixture held by this worker process."""
+    freqs, iters = args
+    from oracle import fastfca as off
+    x, init = _WORKER_STATE["x"], _WORKER_STATE["init"]
+    out = off.run(x, init.P, init.lam, init.v, iters=iters, freqs=freqs, with_ll=True)
+    for i, f in enumerate(out["freqs"]):
+        off.separate_fast(x[f], out["W"][i], out["L"][i], out["H"][i])
+    return len(freqs)
+
+
+class OraclePool:
+    """Spawned worker processes, each holding the workload mixture (generated at start-up,
+    outside any timed span); `run` times the oracle over frequencies split across them."""
+
+    def __init__(self, workers, seed_index=0):
+        import multiprocessing as mp
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(seed_index,))
+        self.pool.map(_noop, range(workers))
+
+    def run(self, freqs, iters):
+        chunks = [c for c in (freqs[i::self.workers] for i in range(self.workers)) if c]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_worker, [(c, iters) for c in chunks], chunksize=1)
+        return time.perf_counter() - t0, len(chunks)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline():
+    """The oracle on the whole workload (every frequency, all iterations, separation) across
+    the host's cores."""
+    w = WORKLOAD
+    cores = os.cpu_count() or 1
+    pool = OraclePool(cores)
+    try:
+        wall, used = pool.run(list(range(w.F)), w.iters)
+    finally:
+        pool.close()
+    sample = (f"whole workload: {w.F} frequencies x {w.iters} iterations (+ log-likelihood each "
+              f"iteration) + separation, split over {used} processes")
+    return {"value": w.F * w.T * w.iters / wall, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": sample, "seconds": round(wall, 3)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2101_08563_gb300 import build, fastfca
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOAD
+    mix = synth.workload_mixture(w, rank)
+    init = synth.random_init(mix.x, w.N, seed=w.seed + rank)
+    build.build()
+    x = torch.from_numpy(mix.x).to(dev)
+    P0 = torch.from_numpy(init.P).to(dev)
+    lam0 = torch.from_numpy(init.lam).to(dev)
+    v0 = torch.from_numpy(init.v).to(dev)
+    c = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sep = fastfca.Separator(x, w.N, stream=stream.cuda_stream)
+
+    def step():
+        sep.set_params(P0, lam0, v0)
+        sep.iterate(w.iters, return_ll=False)
+        sep.separate(c)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    # per-launch timing of the dominant kernel (the fused IP+EM launch) inside each step
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        sep.set_params(P0, lam0, v0)
+        starts[i].record(stream)
+        sep.iterate(w.iters, return_ll=False)
+        mids[i].record(stream)
+        sep.separate(c)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clock_info = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    em_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
+    tot_ms = sum(step_ms)
+    tot_ms = allreduce_max(tot_ms, world, dev)
+    # the set_params copies are outside the event spans; one step is iterate + separate
+    units = w.F * w.T * w.iters
+    value = world * units * args.steps / (tot_ms * 1e-3)
+
+    # FCA comparison path on the same GPU (fewer iterations: it is ~an order slower)
+    fca_iters = 10
+    R0, h0 = synth.fca_random_init(mix.x, w.N, seed=w.seed + rank)
+    R0d = torch.from_numpy(R0).to(dev)
+    h0d = torch.from_numpy(h0).to(dev)
+    fsep = fastfca.Separator(x, w.N, model="fca", stream=stream.cuda_stream)
+    fsep.set_params_fca(R0d, h0d)
+    fsep.iterate(2, return_ll=False)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    fsep.set_params_fca(R0d, h0d)
+    f0.record(stream)
+    fsep.iterate(fca_iters, return_ll=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fca_ms = f0.elapsed_time(f1)
+    fsep.close()
+
+    # end-to-end through the public API with host buffers (pinned), copies inside the span
+    x_h = torch.from_numpy(mix.x).pin_memory()
+    P_h = torch.from_numpy(init.P).pin_memory()
+    lam_h = torch.from_numpy(init.lam).pin_memory()
+    v_h = torch.from_numpy(init.v).pin_memory()
+    c_h = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        s = fastfca.Separator(x_h, w.N, stream=stream.cuda_stream)
+        s.set_params(P_h, lam_h, v_h)
+        ll = s.iterate(w.iters, return_ll=True)
+        s.separate(c_h)
+        s.close()
+        return ll
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ll = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = allreduce_max(e2e_s, world, dev)
+    h2d = mix.x.nbytes + init.P.nbytes + init.lam.nbytes + init.v.nbytes
+    d2h = c_h.numel() * 8 + w.iters * 8
+    sep.close()
+    return {
+        "value": value, "ms_per_step": tot_ms / args.steps, "em_ms": em_ms, "step_ms": step_ms,
+        "clocks": clock_info, "fca_ms": fca_ms, "fca_iters": fca_iters,
+        "e2e_value": world * units * e2e_steps / e2e_s, "h2d": h2d, "d2h": d2h,
+        "final_ll": float(ll[-1]),
+    }
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world, dev):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOAD
+    config = {"workload": w.name, "M": w.M, "N": w.N, "F": w.F, "T": w.T, "iters": w.iters,
+              "K_nmf": w.K, "array": f"{w.array} {w.spacing * 100:.0f} cm",
+              "step": "IP+EM x iters + Wiener separation, from the seeded init",
+              "l2": "flushed between steps (512 MiB write, untimed)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cores = os.cpu_count() or 1
+        freqs = list(range(0, w.F, max(1, w.F // (2 * cores))))[: 2 * cores]
+        iters = 25
+        pool = OraclePool(cores)
+        try:
+            for _ in range(args.warmup):
+                pool.run(freqs, iters)
+            times = []
+            for _ in range(args.steps):
+                wall, used = pool.run(freqs, iters)
+                times.append(wall)
+        finally:
+            pool.close()
+        units = len(freqs) * w.T * iters
+        value = units * len(times) / sum(times)
+        sample = (f"{len(freqs)} of {w.F} frequencies x {iters} iterations + separation per step, "
+                  f"{used} processes")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()                   # spawned workers, before any CUDA work
+
+    r = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    flops = algorithmic_flops_per_bin_iter(w.M, w.N) * w.F * w.T * w.iters
+    em_avg_s = statistics.mean(r["em_ms"]) * 1e-3
+    achieved = flops / em_avg_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("fastfca_em_kernel_bytes_per_launch")
+        except Exception:
+            traffic = None
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 bins, f64 IP+loglik",
+        "data": "synthetic (model-generated mixtures, seeded)", "config": config,
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "fastfca_em_kernel", "flops_per_bin_iter": algorithmic_flops_per_bin_iter(w.M, w.N),
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
+        "clocks": r["clocks"],
+        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "fca_comparison": {"value": w.F * w.T * r["fca_iters"] / (r["fca_ms"] * 1e-3), "unit": UNIT,
+                           "iters": r["fca_iters"], "ms": r["fca_ms"]},
+        "em_launch_ms": statistics.mean(r["em_ms"]),
+        "final_loglik": r["final_ll"],
+        "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

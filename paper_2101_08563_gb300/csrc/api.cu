@@ -1,0 +1,482 @@
+// C ABI of libfastfca.so (declared in include/fastfca.h): argument checking, buffer
+// ownership, host/device transfers and kernel dispatch.  All arithmetic of the method runs in
+// the kernels; this file only moves data and launches.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fastfca.h"
+#include "fca.cuh"
+#include "launch.cuh"
+
+namespace {
+
+constexpr int kMaxM = 4;
+constexpr int kMaxN = 8;
+
+thread_local char g_create_error[512] = "";
+
+}  // namespace
+
+struct fastfca_ctx {
+  fastfca_config cfg{};
+  cudaStream_t stream = nullptr;
+  const float2* x = nullptr;     // device mixture (borrowed or owned)
+  float2* x_owned = nullptr;
+  // FastFCA parameters
+  double2* P = nullptr;
+  float* lam = nullptr;
+  float* v = nullptr;
+  float2* winv = nullptr;        // W^{-H} complex64 scratch for the filter
+  double2* Bst = nullptr;        // W^{-H} (FP64) carried between FastFCA launches
+  double* detst = nullptr;       // |det W|^2 as (mantissa, exponent) per frequency
+  int b_valid = 0;               // Bst/detst match the current P
+  // FCA parameters
+  double2* R = nullptr;
+  float* h = nullptr;
+  ffca::FcaWork fca{};
+  // log-likelihood
+  double* ll_hist = nullptr;     // F x ll_cap
+  int ll_cap = 0;
+  double* ll_last = nullptr;     // F
+  double* ll_sum = nullptr;      // ll_cap totals (device)
+  int* err = nullptr;
+  ffca::FastOps ops{};
+  ffca::FcaOps fops{};
+  fastfca_status sticky = FASTFCA_OK;
+  char msg[512] = "";
+};
+
+namespace {
+
+fastfca_status fail(fastfca_ctx* c, fastfca_status st, const char* fmt, ...) {
+  char* dst = c ? c->msg : g_create_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  if (c && st == FASTFCA_ECUDA) c->sticky = st;
+  return st;
+}
+
+fastfca_status cuda_fail(fastfca_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, FASTFCA_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(c, FASTFCA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(c, expr, what)                               \
+  do {                                                  \
+    cudaError_t e__ = (expr);                           \
+    if (e__ != cudaSuccess) return cuda_fail(c, e__, what); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from src (host or device) to device dst on the stream.
+cudaError_t to_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (is_device_ptr(src)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);   // the host buffer may be reused after return
+}
+
+cudaError_t from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (is_device_ptr(dst)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+size_t FT(const fastfca_config& c) { return (size_t)c.F * c.T; }
+
+fastfca_status check_ready(fastfca_ctx* c) {
+  if (!c) return FASTFCA_EINVAL;
+  if (c->sticky == FASTFCA_ECUDA) return c->sticky;
+  return FASTFCA_OK;
+}
+
+// Reads and clears the device status word; maps set bits to ENUMERIC.
+fastfca_status collect_device_status(fastfca_ctx* c) {
+  int bits = 0;
+  CK(c, cudaMemcpyAsync(&bits, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+  CK(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (bits == 0) return FASTFCA_OK;
+  CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "status clear");
+  if (bits & ffca::kErrConfig) return fail(c, FASTFCA_ECUDA, "kernel launch configuration rejected (bits 0x%x)", bits);
+  c->sticky = FASTFCA_ENUMERIC;
+  return fail(c, FASTFCA_ENUMERIC,
+              "numerical failure in a kernel (bits 0x%x: 1 sigma^2, 2 IP norm, 4 Q not PD, 8 W singular, 16 FCA not PD)",
+              bits);
+}
+
+__global__ void sum_over_f_kernel(const double* __restrict__ hist, int F, int stride, int n, double* __restrict__ out) {
+  // one thread per column (iteration), fixed summation order over f
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n) return;
+  double s = 0.0;
+  for (int f = 0; f < F; ++f) s += hist[(size_t)f * stride + it];
+  out[it] = s;
+}
+
+__global__ void init_fastfca_params_kernel(const float2* __restrict__ x, double2* __restrict__ P,
+                                           float* __restrict__ lam, float* __restrict__ v, int F,
+                                           int T, int M, int N) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < (size_t)F * M * M) {
+    const size_t r = i % ((size_t)M * M);
+    P[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
+  }
+  if (i < (size_t)F * M * N) lam[i] = 1.0f;
+  if (i < (size_t)F * N * T) {
+    const size_t f = i / ((size_t)N * T), t = i % T;
+    float pw = 0.f;
+    for (int m = 0; m < M; ++m) {
+      const float2 a = x[(f * T + t) * M + m];
+      pw += a.x * a.x + a.y * a.y;
+    }
+    v[i] = fmaxf(pw / (float)(M * N), 1e-30f);
+  }
+}
+
+__global__ void init_fca_params_kernel(double2* __restrict__ R, int F, int N, int M) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < (size_t)F * N * M * M) {
+    const size_t r = i % ((size_t)M * M);
+    R[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
+  }
+}
+
+void free_all(fastfca_ctx* c) {
+  cudaFree(c->x_owned);
+  cudaFree(c->P);
+  cudaFree(c->lam);
+  cudaFree(c->v);
+  cudaFree(c->winv);
+  cudaFree(c->Bst);
+  cudaFree(c->detst);
+  cudaFree(c->R);
+  cudaFree(c->h);
+  ffca::fca_work_free(&c->fca);
+  cudaFree(c->ll_hist);
+  cudaFree(c->ll_last);
+  cudaFree(c->ll_sum);
+  cudaFree(c->err);
+}
+
+fastfca_status ensure_ll_capacity(fastfca_ctx* c, int n) {
+  if (n <= c->ll_cap) return FASTFCA_OK;
+  cudaFree(c->ll_hist);
+  cudaFree(c->ll_sum);
+  c->ll_hist = nullptr;
+  c->ll_sum = nullptr;
+  c->ll_cap = 0;
+  CK(c, cudaMalloc(&c->ll_hist, sizeof(double) * (size_t)c->cfg.F * n), "ll history alloc");
+  CK(c, cudaMalloc(&c->ll_sum, sizeof(double) * n), "ll sum alloc");
+  c->ll_cap = n;
+  return FASTFCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fastfca_version(void) { return "fastfca-gb300 0.1 (sm_103a)"; }
+
+const char* fastfca_last_error(const fastfca_ctx* ctx) { return ctx ? ctx->msg : g_create_error; }
+
+fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream, fastfca_ctx** out) {
+  if (!out) return fail(nullptr, FASTFCA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !x) return fail(nullptr, FASTFCA_EINVAL, "cfg and x are required");
+  const fastfca_config c = *cfg;
+  if (c.F < 1 || c.T < 1 || c.M < 1 || c.N < 1)
+    return fail(nullptr, FASTFCA_EINVAL, "F, T, M, N must be positive (got %d %d %d %d)", c.F, c.T, c.M, c.N);
+  if (c.model != FASTFCA_MODEL_FASTFCA && c.model != FASTFCA_MODEL_FCA)
+    return fail(nullptr, FASTFCA_EINVAL, "unknown model %d", c.model);
+  ffca::FastOps ops{};
+  ffca::FcaOps fops{};
+  if (c.model == FASTFCA_MODEL_FASTFCA) {
+    if (!ffca::fast_ops(c.M, c.N, &ops))
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FastFCA kernel for M=%d N=%d (M in 2..%d, N in 2..%d)", c.M, c.N, kMaxM, kMaxN);
+    if (c.T > ops.max_T)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "T=%d exceeds the %d frames one CTA holds", c.T, ops.max_T);
+  } else {
+    if (!ffca::fca_ops(c.M, c.N, &fops))
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FCA kernel for M=%d N=%d", c.M, c.N);
+    if (c.T > fops.max_T)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "T=%d exceeds the %d frames one FCA CTA holds", c.T, fops.max_T);
+  }
+  fastfca_ctx* ctx = new (std::nothrow) fastfca_ctx();
+  if (!ctx) return fail(nullptr, FASTFCA_ENOMEM, "host allocation failed");
+  ctx->cfg = c;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->ops = ops;
+  ctx->fops = fops;
+  const size_t nx = FT(c) * c.M;
+  auto bail = [&](fastfca_status st) {
+    snprintf(g_create_error, sizeof g_create_error, "%s", ctx->msg);
+    free_all(ctx);
+    delete ctx;
+    return st;
+  };
+#define CKC(expr, what)                                              \
+  do {                                                               \
+    cudaError_t e__ = (expr);                                        \
+    if (e__ != cudaSuccess) return bail(cuda_fail(ctx, e__, what));  \
+  } while (0)
+  if (is_device_ptr(x)) {
+    ctx->x = static_cast<const float2*>(x);
+  } else {
+    CKC(cudaMalloc(&ctx->x_owned, sizeof(float2) * nx), "x alloc");
+    CKC(cudaMemcpyAsync(ctx->x_owned, x, sizeof(float2) * nx, cudaMemcpyHostToDevice, ctx->stream), "x upload");
+    ctx->x = ctx->x_owned;
+  }
+  CKC(cudaMalloc(&ctx->err, sizeof(int)), "status alloc");
+  CKC(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "status clear");
+  CKC(cudaMalloc(&ctx->ll_last, sizeof(double) * c.F), "ll alloc");
+  const int threads = 256;
+  if (c.model == FASTFCA_MODEL_FASTFCA) {
+    CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
+    CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "v alloc");
+    CKC(cudaMalloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    size_t n = FT(c) * c.N;
+    if ((size_t)c.F * c.M * c.M > n) n = (size_t)c.F * c.M * c.M;
+    if ((size_t)c.F * c.M * c.N > n) n = (size_t)c.F * c.M * c.N;
+    init_fastfca_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        ctx->x, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N);
+    CKC(cudaGetLastError(), "init launch");
+  } else {
+    CKC(cudaMalloc(&ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M), "R alloc");
+    CKC(cudaMalloc(&ctx->h, sizeof(float) * FT(c) * c.N), "h alloc");
+    // FastFCA's initial v is also FCA's initial h
+    double2* Ptmp = nullptr;
+    float* lamtmp = nullptr;
+    CKC(cudaMalloc(&Ptmp, sizeof(double2) * (size_t)c.F * c.M * c.M), "tmp alloc");
+    CKC(cudaMalloc(&lamtmp, sizeof(float) * (size_t)c.F * c.M * c.N), "tmp alloc");
+    size_t n = FT(c) * c.N;
+    if ((size_t)c.F * c.M * c.M > n) n = (size_t)c.F * c.M * c.M;
+    if ((size_t)c.F * c.M * c.N > n) n = (size_t)c.F * c.M * c.N;
+    init_fastfca_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        ctx->x, Ptmp, lamtmp, ctx->h, c.F, c.T, c.M, c.N);
+    const size_t nr = (size_t)c.F * c.N * c.M * c.M;
+    init_fca_params_kernel<<<(unsigned)((nr + threads - 1) / threads), threads, 0, ctx->stream>>>(ctx->R, c.F, c.N, c.M);
+    cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(Ptmp);
+    cudaFree(lamtmp);
+    CKC(e, "init launch");
+    CKC(ffca::fca_work_alloc(&ctx->fca, c.F, c.T, c.M, c.N), "FCA workspace alloc");
+  }
+  CKC(cudaStreamSynchronize(ctx->stream), "create synchronize");
+#undef CKC
+  *out = ctx;
+  return FASTFCA_OK;
+}
+
+void fastfca_destroy(fastfca_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+}
+
+fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* lam, const float* v) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FASTFCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  if (!P || !lam || !v) return fail(ctx, FASTFCA_EINVAL, "P, lam and v are required");
+  const fastfca_config& c = ctx->cfg;
+  CK(ctx, to_device(ctx->P, P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P upload");
+  CK(ctx, to_device(ctx->lam, lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam upload");
+  CK(ctx, to_device(ctx->v, v, sizeof(float) * FT(c) * c.N, ctx->stream), "v upload");
+  ctx->b_valid = 0;
+  if (ctx->sticky == FASTFCA_ENUMERIC) ctx->sticky = FASTFCA_OK;
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* v) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FASTFCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  const fastfca_config& c = ctx->cfg;
+  if (P) CK(ctx, from_device(P, ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P download");
+  if (lam) CK(ctx, from_device(lam, ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam download");
+  if (v) CK(ctx, from_device(v, ctx->v, sizeof(float) * FT(c) * c.N, ctx->stream), "v download");
+  return collect_device_status(ctx);
+}
+
+fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const float* h) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  if (!R || !h) return fail(ctx, FASTFCA_EINVAL, "R and h are required");
+  const fastfca_config& c = ctx->cfg;
+  CK(ctx, to_device(ctx->R, R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R upload");
+  CK(ctx, to_device(ctx->h, h, sizeof(float) * FT(c) * c.N, ctx->stream), "h upload");
+  if (ctx->sticky == FASTFCA_ENUMERIC) ctx->sticky = FASTFCA_OK;
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  const fastfca_config& c = ctx->cfg;
+  if (R) CK(ctx, from_device(R, ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R download");
+  if (h) CK(ctx, from_device(h, ctx->h, sizeof(float) * FT(c) * c.N, ctx->stream), "h download");
+  return collect_device_status(ctx);
+}
+
+fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_iter) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (n_iter < 1) return fail(ctx, FASTFCA_EINVAL, "n_iter must be >= 1 (got %d)", n_iter);
+  const fastfca_config& c = ctx->cfg;
+  double* hist = nullptr;
+  if (ll_per_iter) {
+    st = ensure_ll_capacity(ctx, n_iter);
+    if (st) return st;
+    hist = ctx->ll_hist;
+  }
+  if (c.model == FASTFCA_MODEL_FASTFCA) {
+    ffca::EmArgs a{};
+    a.x = ctx->x;
+    a.P = ctx->P;
+    a.lam = ctx->lam;
+    a.v = ctx->v;
+    a.ll_hist = hist;
+    a.ll_last = ctx->ll_last;
+    a.Bst = ctx->Bst;
+    a.detst = ctx->detst;
+    a.b_valid = ctx->b_valid;
+    a.err = ctx->err;
+    a.F = c.F;
+    a.T = c.T;
+    a.n_iter = n_iter;
+    a.ll_stride = n_iter;
+    CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA EM launch");
+    ctx->b_valid = 1;
+  } else {
+    ffca::FcaArgs a{};
+    a.x = ctx->x;
+    a.R = ctx->R;
+    a.h = ctx->h;
+    a.ll_hist = hist;
+    a.ll_last = ctx->ll_last;
+    a.err = ctx->err;
+    a.F = c.F;
+    a.T = c.T;
+    a.n_iter = n_iter;
+    a.ll_stride = n_iter;
+    CK(ctx, ctx->fops.em(a, &ctx->fca, ctx->stream), "FCA EM launch");
+  }
+  if (!ll_per_iter) return FASTFCA_OK;
+  sum_over_f_kernel<<<(n_iter + 127) / 128, 128, 0, ctx->stream>>>(ctx->ll_hist, c.F, n_iter, n_iter, ctx->ll_sum);
+  CK(ctx, cudaGetLastError(), "ll sum launch");
+  CK(ctx, cudaMemcpyAsync(ll_per_iter, ctx->ll_sum, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, ctx->stream), "ll download");
+  return collect_device_status(ctx);
+}
+
+fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per_f) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  const fastfca_config& c = ctx->cfg;
+  if (c.model == FASTFCA_MODEL_FASTFCA) {
+    ffca::EmArgs a{};
+    a.x = ctx->x;
+    a.P = ctx->P;
+    a.lam = ctx->lam;
+    a.v = ctx->v;
+    a.ll_hist = nullptr;
+    a.ll_last = ctx->ll_last;
+    a.Bst = ctx->Bst;
+    a.detst = ctx->detst;
+    a.b_valid = ctx->b_valid;
+    a.err = ctx->err;
+    a.F = c.F;
+    a.T = c.T;
+    a.n_iter = 0;
+    a.ll_stride = 0;
+    CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA log-likelihood launch");
+    ctx->b_valid = 1;
+  } else {
+    ffca::FcaArgs a{};
+    a.x = ctx->x;
+    a.R = ctx->R;
+    a.h = ctx->h;
+    a.ll_last = ctx->ll_last;
+    a.err = ctx->err;
+    a.F = c.F;
+    a.T = c.T;
+    a.n_iter = 0;
+    CK(ctx, ctx->fops.em(a, &ctx->fca, ctx->stream), "FCA log-likelihood launch");
+  }
+  if (ll_total) {
+    st = ensure_ll_capacity(ctx, 1);
+    if (st) return st;
+    sum_over_f_kernel<<<1, 32, 0, ctx->stream>>>(ctx->ll_last, c.F, 1, 1, ctx->ll_sum);
+    CK(ctx, cudaGetLastError(), "ll sum launch");
+    CK(ctx, cudaMemcpyAsync(ll_total, ctx->ll_sum, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "ll download");
+  }
+  if (ll_per_f) CK(ctx, from_device(ll_per_f, ctx->ll_last, sizeof(double) * c.F, ctx->stream), "ll per f download");
+  return collect_device_status(ctx);
+}
+
+fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (!c_out) return fail(ctx, FASTFCA_EINVAL, "c is required");
+  const fastfca_config& c = ctx->cfg;
+  const size_t bytes = sizeof(float2) * FT(c) * c.N * c.M;
+  const bool dev = is_device_ptr(c_out);
+  float2* dst = static_cast<float2*>(c_out);
+  float2* tmp = nullptr;
+  if (!dev) {
+    CK(ctx, cudaMallocAsync(&tmp, bytes, ctx->stream), "c staging alloc");
+    dst = tmp;
+  }
+  cudaError_t e;
+  if (c.model == FASTFCA_MODEL_FASTFCA) {
+    e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
+    if (e == cudaSuccess) e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, c.T, ctx->stream);
+  } else {
+    e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
+  }
+  if (e != cudaSuccess) {
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    return cuda_fail(ctx, e, "separate launch");
+  }
+  if (!dev) {
+    e = cudaMemcpyAsync(c_out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(tmp, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "c download");
+    return collect_device_status(ctx);
+  }
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_sync(fastfca_ctx* ctx) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  return collect_device_status(ctx);
+}
+
+}  // extern "C"

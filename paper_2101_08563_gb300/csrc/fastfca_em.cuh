@@ -1,0 +1,604 @@
+// FastFCA IP+EM (Algorithm 1), frequency-resident: one CTA owns one frequency bin f and runs
+// every iteration on it without leaving the SM.
+//
+// Per iteration and frequency (Sec. IV-E, Algorithm 1):
+//   sigma^2 = L H                                   Eq. 28, Eq. 38
+//   Q_m = (1/T) sum_t x_t x_t^H / sigma^2_{mt}       Eq. 33   (all m in one pass over t)
+//   for m: w_m <- (W^H Q_m)^{-1} e_m, normalise      Eq. 34-35 (FP64, see ip_sweep below)
+//   U_{mt} = |w_m^H x_t|^2                           Eq. 37
+//   for n: G_n, Phi_n, L[:,n], H[n,:]                Algorithm 1 n-loop (Gauss-Seidel)
+//   log-likelihood of the updated parameters        Eq. 31 (+ constant)
+//
+// Layout and ownership.  Thread `tid` of the CTA owns frames t = tid + k*blockDim,
+// k < kSlots.  H (N x T), U (M x T) and L (M x N) live in shared memory for the whole run;
+// x is re-read from global memory (it stays in L2 for the workload sizes this kernel takes).
+// The per-frame NMF quantities r_{mt} (see below) stay in registers of the owning thread.
+//
+// NMF update in factored form.  With S = L[:,n] H[n,:], G = S / sigma^2 and
+// Phi = G^2 U + (1 - G) S, one has Phi = S * r with r = 1 + G (U / sigma^2 - 1).  Hence
+//   L[m,n] <- (1/T) sum_t Phi/H[n,t]  = L[m,n] * mean_t r_{mt}
+//   H[n,t] <- (1/M) sum_m Phi/L'[m,n] = H[n,t] * (1/M) sum_m r_{mt} / mean_t r_{mt}
+// (the same numbers as Algorithm 1 with one reciprocal per (m,t) instead of three).
+//
+// IP in FP64 (Eq. 34-35).  With B = W^{-H} (columns b_m), (W^H Q_m)^{-1} e_m = Q_m^{-1} b_m,
+// so Eq. 34 is w = Q_m^{-1} b_m and Eq. 35 divides by sqrt(s), s = b_m^H Q_m^{-1} b_m.  The
+// M inverses Q_m^{-1} do not depend on W and are formed in parallel (one warp each); the
+// column loop then only needs matrix-vector products.  After w_m changes, B is kept equal to
+// W^{-H} by the rank-one update b_k <- b_k - (w_m^H b_k)/(w_m^H b_m) b_m (k != m),
+// b_m <- b_m / (w_m^H b_m), where w_m^H b_m = sqrt(s); and |det W|^2 is multiplied by s.
+#pragma once
+#include "common.cuh"
+
+namespace ffca {
+
+constexpr int kSlots = 4;          // frames per thread
+constexpr int kMaxThreads = 512;   // so at most kSlots * 512 = 2048 frames per frequency
+constexpr int kMaxWarps = kMaxThreads / 32;
+
+struct EmArgs {
+  const float2* x;      // F x T x M complex64, m fastest
+  double2* P;           // F x M x M complex128, W[a][m] at P[(f*M + a)*M + m]
+  float* lam;           // F x M x N, L[m][n]
+  float* v;             // F x N x T, H[n][t]
+  double* ll_hist;      // F x ll_stride or null: log-likelihood after iteration it
+  double* ll_last;      // F or null: log-likelihood of the parameters on exit
+  double2* Bst;         // F x M x M: W^{-H} carried between launches (row-major)
+  double* detst;        // F x 2: |det W|^2 as (mantissa, exponent)
+  int b_valid;          // Bst/detst hold W^{-H} and |det W|^2 of the current P
+  int* err;             // status bits (ErrBits)
+  int F, T, n_iter, ll_stride;
+};
+
+// Packed Hermitian entries of x x^H: e < M -> diagonal |x_a|^2; then for each pair a < b
+// (row-major) two entries: Re(x_a conj x_b), Im(x_a conj x_b).
+template <int M>
+__device__ __forceinline__ void xxh_packed(const float2 (&xv)[M], float (&e)[M * M]) {
+#pragma unroll
+  for (int a = 0; a < M; ++a) e[a] = fmaf(xv[a].x, xv[a].x, xv[a].y * xv[a].y);
+  int k = M;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < M; ++b) {
+      e[k] = fmaf(xv[a].x, xv[b].x, xv[a].y * xv[b].y);
+      e[k + 1] = fmaf(xv[a].y, xv[b].x, -xv[a].x * xv[b].y);
+      k += 2;
+    }
+  }
+}
+
+// Host-visible shared-memory size for a CTA of `threads` threads.
+template <int M, int N>
+struct EmSmem {
+  static constexpr int kQCH = (M <= 3) ? 1 : (M / 2);     // chunks of the Q accumulation
+  static constexpr int kMC = M / kQCH;                     // m values per chunk
+  static constexpr int kV = kMC * M * M;                   // values reduced per chunk
+  static constexpr int kVP = pow2_ceil(kV);
+  static_assert(kVP <= 32, "Q chunk must fit one reduction row");
+  static constexpr int kRedW = 32;                         // floats per warp per buffer
+  // sQ holds the M matrices Q_m; once per launch it is also the scratch of the pivoted
+  // inverse of W^H (M*M source + M*2M augmented work).
+  static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
+  static size_t bytes(int threads) {
+    const size_t Tp = (size_t)threads * kSlots;
+    size_t b = 0;
+    b += sizeof(double2) * M * M * 3;        // sW, sB, sWork
+    b += sizeof(double2) * kQsz;             // sQ
+    b += sizeof(double) * 4;                 // sDet (mantissa, exponent), spare
+    b += sizeof(float2) * M * M;             // sWc
+    b += sizeof(float) * ((M * N + 3) & ~3); // sL
+    b += sizeof(float) * 2 * kMaxWarps * kRedW;
+    b += sizeof(float) * kMaxWarps;          // sLL
+    b += sizeof(float) * N * Tp;             // sH
+    b += sizeof(float) * M * Tp;             // sU
+    return b;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// FP64 helpers executed by one warp.
+
+// In-place inverse of the M x M Hermitian positive definite matrix A (row-major, smem) by
+// Gauss-Jordan without pivoting (pivots of an HPD matrix are its positive Schur complements).
+template <int M>
+__device__ void warp_hpd_inverse(double2* A, int lane, int* err) {
+  constexpr int E = M * M;
+  constexpr int EPL = (E + 31) / 32;
+  for (int k = 0; k < M; ++k) {
+    const double d = A[k * M + k].x;
+    bool bad = !(d > 0.0) || !isfinite(d);
+    const double rd = rcp_pos_f64(bad ? 1.0 : d);
+    double2 nv[EPL];
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+      const int e = lane + 32 * q;
+      if (e < E) {
+        const int i = e / M, j = e - (e / M) * M;
+        const double2 aij = A[e];
+        const double2 aik = A[i * M + k];
+        const double2 akj = A[k * M + j];
+        double2 r;
+        if (i == k) {
+          r = (j == k) ? make_double2(rd, 0.0) : cscale(akj, rd);
+        } else if (j == k) {
+          r = cscale(aik, -rd);
+        } else {
+          r = csub(aij, cscale(cmul(aik, akj), rd));
+        }
+        nv[q] = r;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+      const int e = lane + 32 * q;
+      if (e < E) A[e] = nv[q];
+    }
+    __syncwarp();
+    if (bad && lane == 0) atomicOr(err, kErrQPivot);
+  }
+}
+
+// Gauss-Jordan with partial pivoting on the M x (2M) matrix [A | I] (row-major in work,
+// A given in `src` row-major): leaves A^{-1} in `dst` (row-major) and returns
+// |det A|^2 as mantissa * 2^expo.  One warp; used once per launch.
+template <int M>
+__device__ void warp_inverse_pivot(const double2* src, double2* work, double2* dst, double& mant,
+                                   double& expo, int lane, int* err) {
+  constexpr int C = 2 * M;
+  for (int e = lane; e < M * C; e += 32) {
+    const int i = e / C, j = e - (e / C) * C;
+    work[e] = (j < M) ? src[i * M + j] : make_double2((j - M == i) ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  mant = 1.0;
+  expo = 0.0;
+  for (int k = 0; k < M; ++k) {
+    float mag = -1.f;
+    int piv = lane;
+    if (lane >= k && lane < M) {
+      const double2 a = work[lane * C + k];
+      mag = (float)(a.x * a.x + a.y * a.y);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, mag, off);
+      const int op = __shfl_xor_sync(0xffffffffu, piv, off);
+      if (om > mag || (om == mag && op < piv)) { mag = om; piv = op; }
+    }
+    if (piv != k) {
+      for (int j = lane; j < C; j += 32) {
+        const double2 t = work[k * C + j];
+        work[k * C + j] = work[piv * C + j];
+        work[piv * C + j] = t;
+      }
+    }
+    __syncwarp();
+    const double2 p = work[k * C + k];
+    const double pm = p.x * p.x + p.y * p.y;
+    if (!(pm > 0.0) || !isfinite(pm)) {
+      if (lane == 0) atomicOr(err, kErrWSingular);
+    }
+    mant *= pm;
+    renorm(mant, expo);
+    const double rp = rcp_pos_f64(pm > 0.0 ? pm : 1.0);
+    const double2 ip = make_double2(p.x * rp, -p.y * rp);     // 1/p
+    __syncwarp();
+    for (int j = lane; j < C; j += 32) {
+      if (j > k) work[k * C + j] = cmul(work[k * C + j], ip);
+      else if (j == k) work[k * C + k] = make_double2(1.0, 0.0);
+    }
+    __syncwarp();
+    for (int e = lane; e < M * C; e += 32) {
+      const int i = e / C, j = e - (e / C) * C;
+      if (i != k && j > k) {
+        const double2 f = work[i * C + k];
+        work[e] = csub(work[e], cmul(f, work[k * C + j]));
+      }
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    dst[e] = work[i * C + M + j];
+  }
+  __syncwarp();
+}
+
+// The IP column loop (warp 0).  Q holds Q_m^{-1} (row-major per m).  Updates W (sW, row-major
+// W[a][m]), B = W^{-H} (sB), the float copy conj(W[a][m]) at sWc[m*M + a], and |det W|^2.
+template <int M>
+__device__ void ip_columns(const double2* Qi, double2* sW, double2* sB, double2* tmp, float2* sWc,
+                           double* sDet, int lane, int* err) {
+  double mant = sDet[0], expo = sDet[1];
+  for (int m = 0; m < M; ++m) {
+    const double2* Q = Qi + m * M * M;
+    // w_raw = Q_m^{-1} b_m   (lane i < M computes entry i; two partial sums for latency)
+    double2 wr = make_double2(0.0, 0.0);
+    if (lane < M) {
+      double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int a = 0; a < M; a += 2) {
+        s0 = cfma(Q[lane * M + a], sB[a * M + m], s0);
+        if (a + 1 < M) s1 = cfma(Q[lane * M + a + 1], sB[(a + 1) * M + m], s1);
+      }
+      wr = cadd(s0, s1);
+      tmp[lane] = wr;
+    }
+    __syncwarp();
+    // beta_k = w_raw^H b_k (lane k < M); s = Re(beta_m) = b_m^H Q_m^{-1} b_m
+    double2 beta = make_double2(0.0, 0.0);
+    if (lane < M) {
+      double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int i = 0; i < M; i += 2) {
+        s0 = cfmac(tmp[i], sB[i * M + lane], s0);
+        if (i + 1 < M) s1 = cfmac(tmp[i + 1], sB[(i + 1) * M + lane], s1);
+      }
+      beta = cadd(s0, s1);
+    }
+    const double s = __shfl_sync(0xffffffffu, beta.x, m);
+    const bool ok = (s > 0.0) && isfinite(s);
+    const double sc = rsqrt_pos_f64(ok ? s : 1.0);
+    const double sc2 = sc * sc;
+    // new B from the old one; new column m of W
+    constexpr int E = M * M;
+    constexpr int EPL = (E + 31) / 32;
+    double2 nb[EPL];
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+      const int e = lane + 32 * q;
+      const int i = e / M, k = e - (e / M) * M;
+      const double2 bk = (e < E) ? sB[e] : make_double2(0.0, 0.0);
+      const double2 bm = (e < E) ? sB[i * M + m] : make_double2(0.0, 0.0);
+      const double bkx = __shfl_sync(0xffffffffu, beta.x, k & 31);
+      const double bky = __shfl_sync(0xffffffffu, beta.y, k & 31);
+      if (k == m) nb[q] = cscale(bm, sc);
+      else nb[q] = csub(bk, cmul(make_double2(bkx * sc2, bky * sc2), bm));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+      const int e = lane + 32 * q;
+      if (e < E) sB[e] = nb[q];
+    }
+    if (lane < M) {
+      const double2 w = cscale(wr, sc);
+      sW[lane * M + m] = w;
+      sWc[m * M + lane] = make_float2((float)w.x, (float)-w.y);
+    }
+    if (!ok && lane == 0) atomicOr(err, kErrIpNorm);
+    mant *= ok ? s : 1.0;
+    renorm(mant, expo);
+    __syncwarp();
+  }
+  if (lane == 0) { sDet[0] = mant; sDet[1] = expo; }
+  __syncwarp();
+}
+
+template <int M, int N>
+__global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
+  using SM = EmSmem<M, N>;
+  constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
+  constexpr int MP = pow2_ceil(M);
+  constexpr int NE = M * M;                   // packed Hermitian entries per Q_m
+
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bd = blockDim.x, nw = bd >> 5;
+  const int T = p.T;
+  const int Tp = bd * kSlots;
+  if (f >= p.F) return;
+  if (Tp < T || nw > kMaxWarps) {             // uniform over the CTA
+    if (tid == 0) atomicOr(p.err, kErrConfig);
+    return;
+  }
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sW = reinterpret_cast<double2*>(smem_raw);
+  double2* sB = sW + M * M;
+  double2* sWork = sB + M * M;
+  double2* sQ = sWork + M * M;
+  double* sDet = reinterpret_cast<double*>(sQ + SM::kQsz);
+  float2* sWc = reinterpret_cast<float2*>(sDet + 4);
+  float* sL = reinterpret_cast<float*>(sWc + M * M);
+  float* sRed = sL + ((M * N + 3) & ~3);
+  float* sLL = sRed + 2 * kMaxWarps * SM::kRedW;
+  float* sH = sLL + kMaxWarps;
+  float* sU = sH + N * Tp;
+
+  const float2* xf = p.x + (size_t)f * T * M;
+  const double invT = 1.0 / (double)T;
+
+  // ---- load the parameters of frequency f
+  for (int i = tid; i < M * N; i += bd) sL[i] = p.lam[(size_t)f * M * N + i];
+  for (int i = tid; i < M * M; i += bd) sW[i] = p.P[(size_t)f * M * M + i];
+  for (int n = 0; n < N; ++n) {
+    const float* vf = p.v + ((size_t)f * N + n) * T;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+      const int t = tid + k * bd;
+      sH[n * Tp + t] = (t < T) ? vf[t] : 1.0f;
+    }
+  }
+  __syncthreads();
+  // ---- B = W^{-H}, |det W|^2: carried over from the previous launch when valid, else
+  // formed once by pivoted Gauss-Jordan on W^H (warp 0)
+  if (warp == 0) {
+    if (p.b_valid) {
+      for (int e = lane; e < M * M; e += 32) sB[e] = p.Bst[(size_t)f * M * M + e];
+      if (lane == 0) { sDet[0] = p.detst[2 * f]; sDet[1] = p.detst[2 * f + 1]; }
+    } else {
+      for (int e = lane; e < M * M; e += 32) {
+        const int i = e / M, j = e - (e / M) * M;
+        const double2 w = sW[j * M + i];
+        sQ[e] = make_double2(w.x, -w.y);
+      }
+      __syncwarp();
+      double mant, expo;
+      warp_inverse_pivot<M>(sQ, sQ + M * M, sB, mant, expo, lane, p.err);
+      if (lane == 0) { sDet[0] = mant; sDet[1] = expo; }
+    }
+    for (int e = lane; e < M * M; e += 32) {
+      const int a = e / M, m = e - (e / M) * M;
+      const double2 w = sW[a * M + m];
+      sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    }
+  }
+  __syncthreads();
+
+  float r[kSlots][M];
+  int par = 0;
+
+  // U for the current W (needed when only the log-likelihood is asked for)
+  auto pass_U = [&]() {
+    float2 wc[M * M];
+#pragma unroll
+    for (int i = 0; i < M * M; ++i) wc[i] = sWc[i];
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+      const int t = tid + k * bd;
+      if (t < T) {
+        float2 xv[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) xv[a] = __ldg(xf + (size_t)t * M + a);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int a = 0; a < M; ++a) y = cfmaf(wc[m * M + a], xv[a], y);
+          sU[m * Tp + t] = fmaf(y.x, y.x, y.y * y.y);
+        }
+      }
+    }
+  };
+  if (p.n_iter == 0) pass_U();
+
+  for (int it = 0;; ++it) {
+    const bool have_ll = (it > 0) || (p.n_iter == 0);
+    const bool do_iter = it < p.n_iter;
+
+    // ---- pass A: sigma^2 = LH, 1/sigma^2 -> r, log-likelihood terms
+    {
+      float Lr[M][N];
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int n = 0; n < N; ++n) Lr[m][n] = sL[m * N + n];
+      float llp = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float h[N];
+#pragma unroll
+          for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
+            bad |= !(s2 > 0.f) || !(s2 < INFINITY);
+            const float rs = fast_rcp(s2);
+            r[k][m] = rs;
+            if (have_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
+          }
+        }
+      }
+      if (bad) atomicOr(p.err, kErrSigma);
+      if (have_ll) {
+        llp = warp_sum(llp);
+        if (lane == 0) sLL[warp] = llp;
+      }
+    }
+
+    if (!do_iter) {
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += (double)sLL[w];
+        const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
+        const double ll = (double)T * logdet - s - (double)M * (double)T * kLnPi;
+        if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+        if (p.ll_last) p.ll_last[f] = ll;
+      }
+      break;
+    }
+
+    // ---- Q_m accumulation, chunk by chunk over m, and its CTA reduction
+#pragma unroll 1
+    for (int c = 0; c < QCH; ++c) {
+      float acc[VP];
+#pragma unroll
+      for (int i = 0; i < VP; ++i) acc[i] = 0.f;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float2 xv[M];
+#pragma unroll
+          for (int a = 0; a < M; ++a) xv[a] = __ldg(xf + (size_t)t * M + a);
+          float e[NE];
+          xxh_packed<M>(xv, e);
+#pragma unroll
+          for (int mm = 0; mm < MC; ++mm) {
+            // r[k][c*MC + mm] with a compile-time index per unrolled c is not available
+            // (c is a runtime loop), so select it.
+            float w = r[k][0];
+#pragma unroll
+            for (int m2 = 1; m2 < M; ++m2)
+              if (m2 == c * MC + mm) w = r[k][m2];
+#pragma unroll
+            for (int q = 0; q < NE; ++q) acc[mm * NE + q] = fmaf(w, e[q], acc[mm * NE + q]);
+          }
+        }
+      }
+      warp_reduce_scatter<VP>(acc, lane);
+      {
+        float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
+        if (VP >= 32) {
+#pragma unroll
+          for (int i = 0; i < VP / 32; ++i) red[lane * (VP / 32) + i] = acc[i];
+        } else if ((lane * VP) % 32 == 0) {
+          red[(lane * VP) / 32] = acc[0];
+        }
+      }
+      __syncthreads();
+      if (tid < V) {
+        const float* red = sRed + par * kMaxWarps * SM::kRedW;
+        float q = 0.f;
+        for (int w = 0; w < nw; ++w) q += red[w * SM::kRedW + tid];
+        const int mm = tid / NE, e = tid - mm * NE;
+        const int m = c * MC + mm;
+        double2* Qm = sQ + m * M * M;
+        const double qd = (double)q * invT;
+        if (e < M) {
+          Qm[e * M + e] = make_double2(qd, 0.0);
+        } else {
+          // decode pair index
+          int idx = (e - M) >> 1;
+          const bool im = ((e - M) & 1) != 0;
+          int a = 0;
+          while (idx >= M - 1 - a) { idx -= M - 1 - a; ++a; }
+          const int b = a + 1 + idx;
+          if (!im) { Qm[a * M + b].x = qd; Qm[b * M + a].x = qd; }
+          else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
+        }
+      }
+      if (c == 0 && have_ll && tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += (double)sLL[w];
+        const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
+        const double ll = (double)T * logdet - s - (double)M * (double)T * kLnPi;
+        if (p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+      }
+      par ^= 1;
+    }
+    __syncthreads();
+
+    // ---- IP (FP64): Q_m^{-1} for all m (warp m), then the column loop (warp 0)
+    for (int m = warp; m < M; m += nw) warp_hpd_inverse<M>(sQ + m * M * M, lane, p.err);
+    __syncthreads();
+    if (warp == 0) ip_columns<M>(sQ, sW, sB, sWork, sWc, sDet, lane, p.err);
+    __syncthreads();
+
+    // ---- U = |W^H x|^2
+    pass_U();
+
+    // ---- NMF EM sweep over sources (Gauss-Seidel)
+#pragma unroll 1
+    for (int n = 0; n < N; ++n) {
+      float Lr[M][N];
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int n2 = 0; n2 < N; ++n2) Lr[m][n2] = sL[m * N + n2];
+      float Ln[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float v = Lr[m][0];
+#pragma unroll
+        for (int n2 = 1; n2 < N; ++n2)
+          if (n2 == n) v = Lr[m][n2];
+        Ln[m] = v;
+      }
+      float acc[MP];
+#pragma unroll
+      for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float h[N];
+#pragma unroll
+          for (int n2 = 0; n2 < N; ++n2) h[n2] = sH[n2 * Tp + t];
+          const float hn = sH[n * Tp + t];
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
+            bad |= !(s2 > 0.f) || !(s2 < INFINITY);
+            const float rs = fast_rcp(s2);
+            const float G = Ln[m] * hn * rs;
+            const float rr = fmaf(G, fmaf(sU[m * Tp + t], rs, -1.f), 1.f);
+            r[k][m] = rr;
+            acc[m] += rr;
+          }
+        }
+      }
+      if (bad) atomicOr(p.err, kErrSigma);
+      warp_reduce_scatter<MP>(acc, lane);
+      {
+        float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
+        if ((lane * MP) % 32 == 0) red[(lane * MP) / 32] = acc[0];
+      }
+      __syncthreads();
+      float coef[M];
+      {
+        const float* red = sRed + par * kMaxWarps * SM::kRedW;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float s = 0.f;
+          for (int w = 0; w < nw; ++w) s += red[w * SM::kRedW + m];
+          const float mean = s * (float)invT;
+          coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+          if (tid == m) sL[m * N + n] = Ln[m] * mean;
+        }
+      }
+      par ^= 1;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float g = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
+          sH[n * Tp + t] *= g;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- write back
+  __syncthreads();
+  for (int i = tid; i < M * N; i += bd) p.lam[(size_t)f * M * N + i] = sL[i];
+  for (int i = tid; i < M * M; i += bd) {
+    p.P[(size_t)f * M * M + i] = sW[i];
+    p.Bst[(size_t)f * M * M + i] = sB[i];
+  }
+  if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
+  for (int n = 0; n < N; ++n) {
+    float* vf = p.v + ((size_t)f * N + n) * T;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+      const int t = tid + k * bd;
+      if (t < T) vf[t] = sH[n * Tp + t];
+    }
+  }
+}
+
+}  // namespace ffca

@@ -1,0 +1,112 @@
+// FastFCA multichannel Wiener filter (Sec. IV-F, Eq. 39):
+//   c_tn = W^{-H} diag(g_n(t)) W^H x_t,   g_{mn}(t) = L[m,n] H[n,t] / sigma^2_{mt}.
+// Decorrelate, scale each decorrelated channel by its single-channel Wiener gain, project
+// back.  The gains of one frame sum to one over n, so the images add up to x_t (Eq. 2).
+#pragma once
+#include "common.cuh"
+#include "fastfca_em.cuh"
+
+namespace ffca {
+
+// W^{-H} for every frequency in FP64 (one warp per frequency, pivoted Gauss-Jordan on W^H),
+// written as complex64 row-major for the filter kernel.
+template <int M>
+__global__ void __launch_bounds__(32) winv_kernel(const double2* __restrict__ P, float2* __restrict__ WmH,
+                                                  int F, int* err) {
+  __shared__ double2 s[4 * M * M];
+  const int f = blockIdx.x, lane = threadIdx.x;
+  if (f >= F) return;
+  double2* src = s;
+  double2* work = s + M * M;
+  for (int e = lane; e < M * M; e += 32) {
+    const int i = e / M, j = e - (e / M) * M;
+    const double2 w = P[(size_t)f * M * M + j * M + i];
+    src[e] = make_double2(w.x, -w.y);          // W^H
+  }
+  __syncwarp();
+  double mant, expo;
+  __shared__ double2 dst[M * M];
+  warp_inverse_pivot<M>(src, work, dst, mant, expo, lane, err);
+  for (int e = lane; e < M * M; e += 32)
+    WmH[(size_t)f * M * M + e] = make_float2((float)dst[e].x, (float)dst[e].y);
+}
+
+constexpr int kMwfThreads = 128;
+
+// One thread per frame; grid (F, ceil(T / kMwfThreads)).  The N x M images of a frame are
+// staged in shared memory so that each warp writes its frames' output as one contiguous span.
+template <int M, int N>
+__global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
+    const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
+    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T) {
+  __shared__ float2 sWc[M * M];       // conj(W[a][m]) at [m*M + a]
+  __shared__ float2 sWi[M * M];       // W^{-H}[a][m] at [a*M + m]
+  __shared__ float sL[M * N];
+  __shared__ float4 sOut[kMwfThreads * N * M / 2 + 1];
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int t0 = blockIdx.y * kMwfThreads;
+  const int t = t0 + tid;
+  for (int e = tid; e < M * M; e += kMwfThreads) {
+    const int a = e / M, m = e - (e / M) * M;
+    const double2 w = P[(size_t)f * M * M + e];
+    sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    sWi[e] = WmH[(size_t)f * M * M + e];
+  }
+  for (int e = tid; e < M * N; e += kMwfThreads) sL[e] = lam[(size_t)f * M * N + e];
+  __syncthreads();
+  float2* out = reinterpret_cast<float2*>(sOut);
+  if (t < T) {
+    float2 xv[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) xv[a] = x[((size_t)f * T + t) * M + a];
+    float2 y[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < M; ++a) acc = cfmaf(sWc[m * M + a], xv[a], acc);
+      y[m] = acc;
+    }
+    float h[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) h[n] = v[((size_t)f * N + n) * T + t];
+    float rs[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float s2 = 0.f;
+#pragma unroll
+      for (int n = 0; n < N; ++n) s2 = fmaf(sL[m * N + n], h[n], s2);
+      rs[m] = 1.0f / s2;
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float2 z[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float g = sL[m * N + n] * h[n] * rs[m];
+        z[m] = make_float2(g * y[m].x, g * y[m].y);
+      }
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc = cfmaf(sWi[a * M + m], z[m], acc);
+        out[(tid * N + n) * M + a] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // contiguous write-out of the CTA's frames: (nt * N * M) complex64 values
+  const int nt = min(kMwfThreads, T - t0);
+  const int total = nt * N * M;                     // float2 count
+  float2* dst = c + ((size_t)f * T + t0) * N * M;
+  if (((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (total % 2 == 0)) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = tid; i < total / 2; i += kMwfThreads) d4[i] = sOut[i];
+  } else {
+    for (int i = tid; i < total; i += kMwfThreads) dst[i] = out[i];
+  }
+}
+
+}  // namespace ffca

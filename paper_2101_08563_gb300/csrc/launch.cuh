@@ -1,0 +1,72 @@
+// Host-side launchers for one (M, N) specialisation of the FastFCA kernels.
+#pragma once
+#include "fastfca_em.cuh"
+#include "fastfca_mwf.cuh"
+
+namespace ffca {
+
+struct FastOps {
+  cudaError_t (*em)(const EmArgs& a, cudaStream_t s);
+  cudaError_t (*winv)(const double2* P, float2* WmH, int F, int* err, cudaStream_t s);
+  cudaError_t (*mwf)(const float2* x, const double2* P, const float2* WmH, const float* lam,
+                     const float* v, float2* c, int F, int T, cudaStream_t s);
+  int max_T;
+};
+
+// Threads for a frequency of T frames: whole warps, kSlots frames each.
+inline int em_threads(int T) {
+  const int warps = (T + 32 * kSlots - 1) / (32 * kSlots);
+  return (warps < 1 ? 1 : warps) * 32;
+}
+
+template <int M, int N>
+cudaError_t launch_em(const EmArgs& a, cudaStream_t s) {
+  const int threads = em_threads(a.T);
+  if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
+  const size_t smem = EmSmem<M, N>::bytes(threads);
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fastfca_em_kernel<M, N><<<a.F, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_winv(const double2* P, float2* WmH, int F, int* err, cudaStream_t s) {
+  winv_kernel<M><<<F, 32, 0, s>>>(P, WmH, F, err);
+  return cudaGetLastError();
+}
+
+template <int M, int N>
+cudaError_t launch_mwf(const float2* x, const double2* P, const float2* WmH, const float* lam,
+                       const float* v, float2* c, int F, int T, cudaStream_t s) {
+  dim3 grid(F, (T + kMwfThreads - 1) / kMwfThreads);
+  fastfca_mwf_kernel<M, N><<<grid, kMwfThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T);
+  return cudaGetLastError();
+}
+
+template <int M, int N>
+FastOps make_fast_ops() {
+  FastOps o;
+  o.em = &launch_em<M, N>;
+  o.winv = &launch_winv<M>;
+  o.mwf = &launch_mwf<M, N>;
+  o.max_T = kMaxThreads * kSlots;
+  return o;
+}
+
+// Defined in the per-M translation units.
+bool fast_ops_m2(int N, FastOps* o);
+bool fast_ops_m3(int N, FastOps* o);
+bool fast_ops_m4(int N, FastOps* o);
+
+inline bool fast_ops(int M, int N, FastOps* o) {
+  switch (M) {
+    case 2: return fast_ops_m2(N, o);
+    case 3: return fast_ops_m3(N, o);
+    case 4: return fast_ops_m4(N, o);
+    default: return false;
+  }
+}
+
+}  // namespace ffca

@@ -1,0 +1,236 @@
+"""ctypes binding of libfastfca.so (C ABI in include/fastfca.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+Arrays may be torch tensors (CPU or CUDA) or NumPy arrays (host); they must be C-contiguous
+with the dtype and shape that include/fastfca.h gives.  The library reports errors through
+status codes, raised here as FastFCAError.  Importing this module loads the library and
+raises if it has not been built (``paper_2101_08563_gb300.build.build()``): there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+try:  # torch is optional for host-only use
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "EUNSUPPORTED"}
+MODEL_FASTFCA = 0
+MODEL_FCA = 1
+
+# Every entry point of include/fastfca.h with (restype, argtypes).
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "fastfca_create": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "fastfca_set_params": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fastfca_get_params": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fastfca_set_params_fca": (ctypes.c_int, [_P, _P, _P]),
+    "fastfca_get_params_fca": (ctypes.c_int, [_P, _P, _P]),
+    "fastfca_iterate": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "fastfca_loglik": (ctypes.c_int, [_P, _P, _P]),
+    "fastfca_separate": (ctypes.c_int, [_P, _P]),
+    "fastfca_sync": (ctypes.c_int, [_P]),
+    "fastfca_last_error": (ctypes.c_char_p, [_P]),
+    "fastfca_destroy": (None, [_P]),
+    "fastfca_version": (ctypes.c_char_p, []),
+}
+
+
+class FastFCAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int32), ("T", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("N", ctypes.c_int32), ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Loads libfastfca.so (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_2101_08563_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype_np, shape, name, writable=False):
+    """(pointer, keepalive) for a torch tensor or NumPy array with the expected layout."""
+    if a is None:
+        return None, None
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = {np.complex64: torch.complex64, np.complex128: torch.complex128,
+                np.float32: torch.float32, np.float64: torch.float64}[dtype_np]
+        if a.dtype != want:
+            raise TypeError(f"{name}: expected {want}, got {a.dtype}")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = a
+    if not isinstance(arr, np.ndarray):
+        raise TypeError(f"{name}: expected a torch tensor or NumPy array")
+    if arr.dtype != dtype_np:
+        raise TypeError(f"{name}: expected {np.dtype(dtype_np)}, got {arr.dtype}")
+    if tuple(arr.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(arr.shape)}")
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name}: must be C-contiguous")
+    if writable and not arr.flags["WRITEABLE"]:
+        raise ValueError(f"{name}: must be writable")
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _default_stream():
+    if torch is not None and torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+class Separator:
+    """One separation problem (one mixture) held by the library.
+
+    x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" or "fca".
+    A CUDA x is borrowed (kept referenced here); a host x is copied by the library.
+    """
+
+    def __init__(self, x, N: int, model: str = "fastfca", stream=None):
+        self.lib = load()
+        shape = tuple(x.shape)
+        if len(shape) != 3:
+            raise ValueError("x must have shape (F, T, M)")
+        self.F, self.T, self.M = (int(s) for s in shape)
+        self.N = int(N)
+        self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA}[model]
+        cfg = Config(self.F, self.T, self.M, self.N, self.model, 0)
+        px, self._x = _ptr(x, np.complex64, shape, "x")
+        self.stream = _default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        st = self.lib.fastfca_create(ctypes.byref(cfg), px, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if st != 0:
+            raise FastFCAError(st, self.lib.fastfca_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, st):
+        if st != 0:
+            raise FastFCAError(st, self.lib.fastfca_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fastfca_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ parameters
+    def set_params(self, P, lam, v):
+        F, M, N, T = self.F, self.M, self.N, self.T
+        pP, kP = _ptr(P, np.complex128, (F, M, M), "P")
+        pl, kl = _ptr(lam, np.float32, (F, M, N), "lam")
+        pv, kv = _ptr(v, np.float32, (F, N, T), "v")
+        self._check(self.lib.fastfca_set_params(self._h, pP, pl, pv))
+
+    def get_params(self):
+        F, M, N, T = self.F, self.M, self.N, self.T
+        P = np.empty((F, M, M), np.complex128)
+        lam = np.empty((F, M, N), np.float32)
+        v = np.empty((F, N, T), np.float32)
+        self._check(self.lib.fastfca_get_params(self._h, _ptr(P, np.complex128, P.shape, "P", True)[0],
+                                                _ptr(lam, np.float32, lam.shape, "lam", True)[0],
+                                                _ptr(v, np.float32, v.shape, "v", True)[0]))
+        return P, lam, v
+
+    def get_params_into(self, P=None, lam=None, v=None):
+        F, M, N, T = self.F, self.M, self.N, self.T
+        self._check(self.lib.fastfca_get_params(self._h, _ptr(P, np.complex128, (F, M, M), "P", True)[0],
+                                                _ptr(lam, np.float32, (F, M, N), "lam", True)[0],
+                                                _ptr(v, np.float32, (F, N, T), "v", True)[0]))
+
+    def set_params_fca(self, R, h):
+        F, M, N, T = self.F, self.M, self.N, self.T
+        pR, kR = _ptr(R, np.complex128, (F, N, M, M), "R")
+        ph, kh = _ptr(h, np.float32, (F, N, T), "h")
+        self._check(self.lib.fastfca_set_params_fca(self._h, pR, ph))
+
+    def get_params_fca(self):
+        F, M, N, T = self.F, self.M, self.N, self.T
+        R = np.empty((F, N, M, M), np.complex128)
+        h = np.empty((F, N, T), np.float32)
+        self._check(self.lib.fastfca_get_params_fca(self._h, _ptr(R, np.complex128, R.shape, "R", True)[0],
+                                                    _ptr(h, np.float32, h.shape, "h", True)[0]))
+        return R, h
+
+    # ------------------------------------------------------------------ algorithm
+    def iterate(self, n_iter: int, return_ll: bool = True):
+        """n_iter iterations; returns the total log-likelihood after each (np.float64) or None."""
+        if return_ll:
+            ll = np.empty(n_iter, np.float64)
+            self._check(self.lib.fastfca_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p)))
+            return ll
+        self._check(self.lib.fastfca_iterate(self._h, int(n_iter), None))
+        return None
+
+    def loglik(self, per_f: bool = False):
+        tot = np.zeros(1, np.float64)
+        pf = np.empty(self.F, np.float64) if per_f else None
+        self._check(self.lib.fastfca_loglik(self._h, tot.ctypes.data_as(ctypes.c_void_p),
+                                            pf.ctypes.data_as(ctypes.c_void_p) if per_f else None))
+        return (float(tot[0]), pf) if per_f else float(tot[0])
+
+    def separate(self, out=None):
+        """Source images complex64 (F, T, N, M); into `out` (host or CUDA) when given."""
+        shape = (self.F, self.T, self.N, self.M)
+        if out is None:
+            out = np.empty(shape, np.complex64)
+        p, keep = _ptr(out, np.complex64, shape, "c", True)
+        self._check(self.lib.fastfca_separate(self._h, p))
+        return out
+
+    def sync(self):
+        self._check(self.lib.fastfca_sync(self._h))
+
+
+def abi_symbols_from_header(path: str | None = None):
+    """Names of the functions declared in include/fastfca.h."""
+    import re
+    path = path or os.path.join(_build.ROOT, "include", "fastfca.h")
+    txt = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(fastfca_[a-z0-9_]+)\s*\(",
+                                 txt, flags=re.M)))

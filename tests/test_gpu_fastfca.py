@@ -1,0 +1,209 @@
+"""Parity of the CUDA FastFCA path (through the C ABI) with the complex128 oracle.
+
+Tolerances (from the FP32 bin arithmetic against the FP64 oracle): total log-likelihood
+relative error <= 1e-5 per iteration, source images relative Frobenius error <= 1e-4;
+parameters are compared through scale-free quantities (sigma^2 and the per-source powers
+L[:, n] H[n, :]) at a looser element-wise tolerance, as diagnostics.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fastfca as off  # noqa: E402
+from paper_2101_08563_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+LL_TOL = 1e-5
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ff():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2101_08563_gb300 import build, fastfca
+    build.build()
+    fastfca.load()
+    return fastfca
+
+
+def oracle_images(x, ref):
+    return np.stack([off.separate_fast(x[f], ref["W"][i], ref["L"][i], ref["H"][i])
+                     for i, f in enumerate(ref["freqs"])])
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def run_gpu(ff, x, init, N, iters, device_x=True):
+    xd = torch.from_numpy(x).cuda() if device_x else x
+    sep = ff.Separator(xd, N)
+    sep.set_params(init.P, init.lam, init.v)
+    ll = sep.iterate(iters)
+    c = sep.separate()
+    P, lam, v = sep.get_params()
+    ll_f = sep.loglik(per_f=True)[1]
+    sep.close()
+    return ll, c, P, lam, v, ll_f
+
+
+@pytest.mark.parametrize("M,N,F,T,iters", [
+    (2, 3, 9, 250, 1),     # one iteration, ragged last warp
+    (2, 3, 5, 37, 3),      # T < one CTA row of frames
+    (3, 5, 4, 500, 2),
+    (4, 6, 3, 1250, 2),
+    (2, 2, 3, 130, 4),
+    (4, 8, 2, 2048, 1),    # the largest T one CTA holds
+])
+def test_parity_small(ff, M, N, F, T, iters):
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=100 + M * 10 + N)
+    init = synth.random_init(mix.x, N, seed=5)
+    ll, c, P, lam, v, ll_f = run_gpu(ff, mix.x, init, N, iters)
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters)
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
+    assert np.allclose(ll_f, ref["ll"][:, -1], rtol=LL_TOL, atol=1e-6)
+    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    # sigma^2 = L H and the per-source powers, element-wise (scale-free diagnostics)
+    s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
+    s2_ref = np.einsum("fmn,fnt->fmt", ref["L"], ref["H"])
+    assert np.allclose(s2, s2_ref, rtol=2e-3 if T > 1 else 1e-2)
+
+
+def test_trajectory_small_config(ff):
+    """M=2, N=3, F=257, T=250, 20 iterations (the small workload), whole problem vs oracle."""
+    w = synth.WORKLOADS["small"]
+    mix = synth.workload_mixture(w)
+    init = synth.random_init(mix.x, w.N, seed=w.seed)
+    ll, c, P, lam, v, ll_f = run_gpu(ff, mix.x, init, w.N, w.iters)
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=w.iters)
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref))
+    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+
+
+def test_full_size_m4n6_sampled_frequencies(ff):
+    """M=4, N=6, F=513, T=1250, 100 iterations in the benchmark's launch configuration;
+    the oracle recomputes a sample of frequencies (each frequency is independent)."""
+    w = synth.WORKLOADS["fca_cmp"]
+    mix = synth.workload_mixture(w)
+    init = synth.random_init(mix.x, w.N, seed=w.seed)
+    xd = torch.from_numpy(mix.x).cuda()
+    sep = ff.Separator(xd, w.N)
+    sep.set_params(init.P, init.lam, init.v)
+    hist = sep.iterate(w.iters)
+    c = sep.separate(torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device="cuda"))
+    _, ll_f = sep.loglik(per_f=True)
+    sep.close()
+    assert np.all(np.diff(hist) >= -1e-6 * np.abs(hist[1:]))
+    freqs = [3, 130, 257, 511]
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=w.iters, freqs=freqs)
+    for i, f in enumerate(freqs):
+        assert abs(ll_f[f] - ref["ll"][i, -1]) <= LL_TOL * abs(ref["ll"][i, -1]), f
+        cr = off.separate_fast(mix.x[f], ref["W"][i], ref["L"][i], ref["H"][i])
+        assert rel(c[f].cpu().numpy(), cr) <= IMG_TOL, f
+    # images sum to the mixture everywhere (Eq. 2)
+    xs = c.sum(dim=2)
+    assert float((xs - xd).abs().pow(2).sum().sqrt() / xd.abs().pow(2).sum().sqrt()) < 1e-5
+
+
+def test_images_sum_to_mixture_and_ll_monotone(ff):
+    mix = synth.generate_mixture(3, 5, 16, 700, 8, seed=9)
+    init = synth.random_init(mix.x, 5, seed=9)
+    ll, c, *_ = run_gpu(ff, mix.x, init, 5, 15)
+    assert rel(c.sum(axis=2), mix.x) < 1e-5
+    assert np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
+
+
+def test_loglik_of_given_parameters(ff):
+    """fastfca_loglik (no iteration) equals Eq. 31 of the oracle at arbitrary parameters."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    M, N, F, T = 3, 4, 6, 300
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=3)
+    P = (rng.standard_normal((F, M, M)) + 1j * rng.standard_normal((F, M, M))) * 0.3 + np.eye(M)
+    lam = rng.uniform(0.2, 2.0, (F, M, N)).astype(np.float32)
+    v = rng.uniform(0.2, 5.0, (F, N, T)).astype(np.float32)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N)
+    sep.set_params(P, lam, v)
+    tot, per_f = sep.loglik(per_f=True)
+    sep.close()
+    ref = [off.loglik(off.Xhat_from_x(mix.x[f]), P[f], lam[f].astype(np.float64), v[f].astype(np.float64))
+           for f in range(F)]
+    assert np.allclose(per_f, ref, rtol=1e-6)
+    assert tot == pytest.approx(sum(ref), rel=1e-6)
+
+
+def test_resume_is_bitwise(ff):
+    """iterate(a) then iterate(b) gives the same parameters as iterate(a + b), bit for bit
+    (fixed-order reductions; W^{-H} carried between launches).  A get/set round trip in
+    between rebuilds W^{-H} from W and so agrees to rounding only."""
+    mix = synth.generate_mixture(2, 4, 7, 333, 4, seed=4)
+    init = synth.random_init(mix.x, 4, seed=4)
+    xd = torch.from_numpy(mix.x).cuda()
+    a = ff.Separator(xd, 4)
+    a.set_params(init.P, init.lam, init.v)
+    a.iterate(7, return_ll=False)
+    Pa, la, va = a.get_params()
+    b = ff.Separator(xd, 4)
+    b.set_params(init.P, init.lam, init.v)
+    b.iterate(3, return_ll=False)
+    b.iterate(4, return_ll=False)
+    Pb, lb, vb = b.get_params()
+    assert np.array_equal(Pa, Pb) and np.array_equal(la, lb) and np.array_equal(va, vb)
+    c = ff.Separator(xd, 4)
+    c.set_params(init.P, init.lam, init.v)
+    c.iterate(3, return_ll=False)
+    c.set_params(*c.get_params())
+    c.iterate(4, return_ll=False)
+    Pc, lc, vc = c.get_params()
+    assert rel(vc, va) < 1e-5 and rel(lc, la) < 1e-5
+    for s in (a, b, c):
+        s.close()
+
+
+def test_host_buffers_match_device_buffers(ff):
+    mix = synth.generate_mixture(2, 3, 5, 200, 4, seed=8)
+    init = synth.random_init(mix.x, 3, seed=8)
+    ll_d, c_d, *_ = run_gpu(ff, mix.x, init, 3, 4, device_x=True)
+    ll_h, c_h, *_ = run_gpu(ff, mix.x, init, 3, 4, device_x=False)
+    assert np.array_equal(ll_d, ll_h)
+    assert np.array_equal(c_d, c_h)
+
+
+def test_errors_are_reported(ff):
+    x = torch.zeros((2, 10, 5), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
+        ff.Separator(x, 3)                    # M = 5 has no kernel
+    x = torch.zeros((2, 5000, 2), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
+        ff.Separator(x, 3)                    # T beyond one CTA
+    mix = synth.generate_mixture(2, 3, 3, 64, 4, seed=1)
+    init = synth.random_init(mix.x, 3, seed=1)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 3)
+    with pytest.raises(ff.FastFCAError, match="EINVAL"):
+        sep.iterate(0)
+    # a non-positive power makes sigma^2 <= 0: reported as ENUMERIC, then cleared by set_params
+    bad_v = init.v.copy()
+    bad_v[1, :, 5] = 0.0
+    sep.set_params(init.P, init.lam, bad_v)
+    with pytest.raises(ff.FastFCAError, match="ENUMERIC"):
+        sep.iterate(2)
+    sep.set_params(init.P, init.lam, init.v)
+    ll = sep.iterate(2)
+    assert np.all(np.isfinite(ll))
+    sep.close()
+
+
+def test_fewer_frames_than_mics_is_rejected_numerically(ff):
+    """With T < M every Q_m (Eq. 33) is singular and Eq. 34 has no solution: the kernel
+    reports ENUMERIC instead of returning garbage."""
+    mix = synth.generate_mixture(3, 4, 2, 2, 4, seed=2)
+    init = synth.random_init(mix.x, 4, seed=2)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 4)
+    sep.set_params(init.P, init.lam, init.v)
+    with pytest.raises(ff.FastFCAError, match="ENUMERIC"):
+        sep.iterate(1)
+    sep.close()
