@@ -10,9 +10,13 @@
 //   log-likelihood of the updated parameters        Eq. 31 (+ constant)
 //
 // Layout and ownership.  Thread `tid` of the CTA owns frames t = tid + k*blockDim,
-// k < kSlots.  H (N x T), U (M x T) and L (M x N) live in shared memory for the whole run;
-// x is re-read from global memory (it stays in L2 for the workload sizes this kernel takes).
-// The per-frame NMF quantities r_{mt} (see below) stay in registers of the owning thread.
+// k < kSlots.  H (N x T) and U (M x T) live in shared memory for the whole run; every thread
+// holds its own copy of L (M x N) in registers and applies the same updates to it; x is
+// re-read from global memory (it stays in L2 for the workload sizes this kernel takes).
+// The per-frame quantities r_{mt} (see below) stay in registers of the owning thread.
+// Phase 2 of source n (the H[n,:] update) and phase 1 of source n+1 run in one pass over
+// the frames, so each source costs one CTA barrier; the last phase 2 shares its pass with
+// the next iteration's sigma^2 / log-likelihood pass.
 //
 // NMF update in factored form.  With S = L[:,n] H[n,:], G = S / sigma^2 and
 // Phi = G^2 U + (1 - G) S, one has Phi = S * r with r = 1 + G (U / sigma^2 - 1).  Hence
@@ -31,8 +35,8 @@
 
 namespace ffca {
 
-constexpr int kSlots = 4;          // frames per thread
-constexpr int kMaxThreads = 512;   // so at most kSlots * 512 = 2048 frames per frequency
+constexpr int kSlots = 8;          // frames per thread
+constexpr int kMaxThreads = 256;   // so at most kSlots * 256 = 2048 frames per frequency
 constexpr int kMaxWarps = kMaxThreads / 32;
 
 struct EmArgs {
@@ -47,7 +51,21 @@ struct EmArgs {
   int b_valid;          // Bst/detst hold W^{-H} and |det W|^2 of the current P
   int* err;             // status bits (ErrBits)
   int F, T, n_iter, ll_stride;
+  long long* clocks;    // phase timestamps of frequency 0 (only with FFCA_PHASE_CLOCKS)
 };
+
+// Phase timestamps (clock64) of frequency 0, thread 0, for the first 8 iterations; compiled
+// in only with -DFFCA_PHASE_CLOCKS (profiling builds), otherwise empty.
+#ifdef FFCA_PHASE_CLOCKS
+#define FFCA_MARK(it, slot)                                                       \
+  do {                                                                            \
+    if (p.clocks && f == 0 && tid == 0 && (it) < 8) p.clocks[(it) * 16 + (slot)] = clock64(); \
+  } while (0)
+#else
+#define FFCA_MARK(it, slot) \
+  do {                      \
+  } while (0)
+#endif
 
 // Packed Hermitian entries of x x^H: e < M -> diagonal |x_a|^2; then for each pair a < b
 // (row-major) two entries: Re(x_a conj x_b), Im(x_a conj x_b).
@@ -86,7 +104,6 @@ struct EmSmem {
     b += sizeof(double2) * kQsz;             // sQ
     b += sizeof(double) * 4;                 // sDet (mantissa, exponent), spare
     b += sizeof(float2) * M * M;             // sWc
-    b += sizeof(float) * ((M * N + 3) & ~3); // sL
     b += sizeof(float) * 2 * kMaxWarps * kRedW;
     b += sizeof(float) * kMaxWarps;          // sLL
     b += sizeof(float) * N * Tp;             // sH
@@ -98,44 +115,56 @@ struct EmSmem {
 // ---------------------------------------------------------------------------------------
 // FP64 helpers executed by one warp.
 
-// In-place inverse of the M x M Hermitian positive definite matrix A (row-major, smem) by
-// Gauss-Jordan without pivoting (pivots of an HPD matrix are its positive Schur complements).
+// In-place inverses of the M matrices Q_0..Q_{M-1} (each M x M Hermitian positive definite,
+// row-major, consecutive in smem) by Gauss-Jordan without pivoting (the pivots of an HPD
+// matrix are its positive Schur complements), all by one warp.  On this part every FP64
+// warp instruction occupies the sub-partition's FP64 unit for ~70 cycles whatever its lane
+// mask, so the M matrices share the warp's lanes: lane l works on matrix l / kLPM, entries
+// (l % kLPM) + q * kLPM.
 template <int M>
-__device__ void warp_hpd_inverse(double2* A, int lane, int* err) {
-  constexpr int E = M * M;
-  constexpr int EPL = (E + 31) / 32;
+struct HpdPack {
+  static constexpr int kE = M * M;
+  static constexpr int kLPM = (32 / M < kE) ? 32 / M : kE;   // lanes per matrix
+  static constexpr int kEPL = (kE + kLPM - 1) / kLPM;         // entries per lane
+};
+
+template <int M>
+__device__ void warp_hpd_inverse_all(double2* Q, int lane, int* err) {
+  using PK = HpdPack<M>;
+  constexpr int E = PK::kE, LPM = PK::kLPM, EPL = PK::kEPL;
+  const int mat = lane / LPM;
+  const bool act = mat < M;
+  double2* A = Q + (act ? mat : 0) * E;
+  const int l0 = lane - mat * LPM;
   for (int k = 0; k < M; ++k) {
     const double d = A[k * M + k].x;
-    bool bad = !(d > 0.0) || !isfinite(d);
+    const float df = (float)d;
+    const bool bad = act && !(df > 0.f && df < INFINITY);
     const double rd = rcp_pos_f64(bad ? 1.0 : d);
     double2 nv[EPL];
 #pragma unroll
     for (int q = 0; q < EPL; ++q) {
-      const int e = lane + 32 * q;
-      if (e < E) {
+      const int e = l0 + q * LPM;
+      if (act && e < E) {
         const int i = e / M, j = e - (e / M) * M;
-        const double2 aij = A[e];
-        const double2 aik = A[i * M + k];
-        const double2 akj = A[k * M + j];
-        double2 r;
-        if (i == k) {
-          r = (j == k) ? make_double2(rd, 0.0) : cscale(akj, rd);
-        } else if (j == k) {
-          r = cscale(aik, -rd);
-        } else {
-          r = csub(aij, cscale(cmul(aik, akj), rd));
-        }
-        nv[q] = r;
+        // new = base - (c1 rd) c2 with base = a_ij (i,j != k) else 0, c1 = a_ik (i != k)
+        // else -1, c2 = a_kj (j != k) else 1: covers the four Gauss-Jordan cases at once.
+        const double2 aij = A[e], aik = A[i * M + k], akj = A[k * M + j];
+        const double2 base = (i != k && j != k) ? aij : make_double2(0.0, 0.0);
+        const double2 c1 = (i != k) ? aik : make_double2(-1.0, 0.0);
+        const double2 c2 = (j != k) ? akj : make_double2(1.0, 0.0);
+        const double2 t = make_double2(c1.x * rd, c1.y * rd);
+        nv[q] = make_double2(fma(t.y, c2.y, fma(-t.x, c2.x, base.x)), fma(-t.y, c2.x, fma(-t.x, c2.y, base.y)));
       }
     }
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < EPL; ++q) {
-      const int e = lane + 32 * q;
-      if (e < E) A[e] = nv[q];
+      const int e = l0 + q * LPM;
+      if (act && e < E) A[e] = nv[q];
     }
     __syncwarp();
-    if (bad && lane == 0) atomicOr(err, kErrQPivot);
+    if (bad) atomicOr(err, kErrQPivot);
   }
 }
 
@@ -207,65 +236,68 @@ __device__ void warp_inverse_pivot(const double2* src, double2* work, double2* d
 
 // The IP column loop (warp 0).  Q holds Q_m^{-1} (row-major per m).  Updates W (sW, row-major
 // W[a][m]), B = W^{-H} (sB), the float copy conj(W[a][m]) at sWc[m*M + a], and |det W|^2.
+// Every product is split into its real and imaginary part on two lanes: lane
+// l = (r * MP + c) * 2 + part, so that each FP64 instruction does 2*M*M lanes of work.
 template <int M>
-__device__ void ip_columns(const double2* Qi, double2* sW, double2* sB, double2* tmp, float2* sWc,
-                           double* sDet, int lane, int* err) {
+__device__ void ip_columns(const double2* Qi, double2* sW, double2* sB, float2* sWc, double* sDet,
+                           int lane, int* err) {
+  constexpr int MP = pow2_ceil(M);
+  static_assert(2 * MP * MP <= 32 || M > 4, "lane split needs 2 M^2 <= 32");
+  const int part = lane & 1;
+  const int r = (lane >> 1) / MP, c = (lane >> 1) - ((lane >> 1) / MP) * MP;
+  const bool act = r < M && c < M;
   double mant = sDet[0], expo = sDet[1];
   for (int m = 0; m < M; ++m) {
     const double2* Q = Qi + m * M * M;
-    // w_raw = Q_m^{-1} b_m   (lane i < M computes entry i; two partial sums for latency)
-    double2 wr = make_double2(0.0, 0.0);
-    if (lane < M) {
-      double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int a = 0; a < M; a += 2) {
-        s0 = cfma(Q[lane * M + a], sB[a * M + m], s0);
-        if (a + 1 < M) s1 = cfma(Q[lane * M + a + 1], sB[(a + 1) * M + m], s1);
-      }
-      wr = cadd(s0, s1);
-      tmp[lane] = wr;
+    // w_raw[r] = sum_c Qinv[r][c] b_m[c]          (lane (r, c, part))
+    double pw = 0.0;
+    if (act) {
+      const double2 q = Q[r * M + c];
+      const double2 bb = sB[c * M + m];
+      const double x1 = part ? bb.y : bb.x;
+      const double x2 = part ? bb.x : -bb.y;
+      pw = fma(q.x, x1, q.y * x2);
     }
-    __syncwarp();
-    // beta_k = w_raw^H b_k (lane k < M); s = Re(beta_m) = b_m^H Q_m^{-1} b_m
-    double2 beta = make_double2(0.0, 0.0);
-    if (lane < M) {
-      double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
 #pragma unroll
-      for (int i = 0; i < M; i += 2) {
-        s0 = cfmac(tmp[i], sB[i * M + lane], s0);
-        if (i + 1 < M) s1 = cfmac(tmp[i + 1], sB[(i + 1) * M + lane], s1);
-      }
-      beta = cadd(s0, s1);
+    for (int off = 2; off < 2 * MP; off <<= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
+    // beta_k = sum_i conj(w_raw[i]) B[i][k]           (lane (k, i, part) with k = r, i = c)
+    const double wre = __shfl_sync(0xffffffffu, pw, (c * MP) * 2 + 0);
+    const double wim = __shfl_sync(0xffffffffu, pw, (c * MP) * 2 + 1);
+    double pb = 0.0;
+    if (act) {
+      const double2 bk = sB[c * M + r];
+      pb = part ? fma(wre, bk.y, -wim * bk.x) : fma(wre, bk.x, wim * bk.y);
     }
-    const double s = __shfl_sync(0xffffffffu, beta.x, m);
-    const bool ok = (s > 0.0) && isfinite(s);
+#pragma unroll
+    for (int off = 2; off < 2 * MP; off <<= 1) pb += __shfl_xor_sync(0xffffffffu, pb, off);
+    // s = Re(beta_m) = b_m^H Q_m^{-1} b_m; scale 1/sqrt(s)
+    const double s = __shfl_sync(0xffffffffu, pb, (m * MP) * 2 + 0);
+    const float sf = (float)s;
+    const bool ok = sf > 0.f && sf < INFINITY;
     const double sc = rsqrt_pos_f64(ok ? s : 1.0);
     const double sc2 = sc * sc;
-    // new B from the old one; new column m of W
-    constexpr int E = M * M;
-    constexpr int EPL = (E + 31) / 32;
-    double2 nb[EPL];
-#pragma unroll
-    for (int q = 0; q < EPL; ++q) {
-      const int e = lane + 32 * q;
-      const int i = e / M, k = e - (e / M) * M;
-      const double2 bk = (e < E) ? sB[e] : make_double2(0.0, 0.0);
-      const double2 bm = (e < E) ? sB[i * M + m] : make_double2(0.0, 0.0);
-      const double bkx = __shfl_sync(0xffffffffu, beta.x, k & 31);
-      const double bky = __shfl_sync(0xffffffffu, beta.y, k & 31);
-      if (k == m) nb[q] = cscale(bm, sc);
-      else nb[q] = csub(bk, cmul(make_double2(bkx * sc2, bky * sc2), bm));
+    // B update (lane (i, k, part) with i = r, k = c):
+    //   b_k <- b_k - (beta_k / s) b_m  (k != m),   b_m <- b_m / sqrt(s)
+    const double bre = __shfl_sync(0xffffffffu, pb, (c * MP) * 2 + 0);
+    const double bim = __shfl_sync(0xffffffffu, pb, (c * MP) * 2 + 1);
+    double nb = 0.0;
+    if (act) {
+      const double2 bki = sB[r * M + c];
+      const double2 bmi = sB[r * M + m];
+      if (c == m) {
+        nb = (part ? bmi.y : bmi.x) * sc;
+      } else {
+        const double cr = bre * sc2, ci = bim * sc2;
+        nb = part ? fma(-ci, bmi.x, fma(-cr, bmi.y, bki.y)) : fma(ci, bmi.y, fma(-cr, bmi.x, bki.x));
+      }
     }
+    // w_m = w_raw / sqrt(s) on lanes (i, 0, part)
+    const double wv = pw * sc;
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < EPL; ++q) {
-      const int e = lane + 32 * q;
-      if (e < E) sB[e] = nb[q];
-    }
-    if (lane < M) {
-      const double2 w = cscale(wr, sc);
-      sW[lane * M + m] = w;
-      sWc[m * M + lane] = make_float2((float)w.x, (float)-w.y);
+    if (act) reinterpret_cast<double*>(sB)[2 * (r * M + c) + part] = nb;
+    if (act && c == 0) {
+      reinterpret_cast<double*>(sW)[2 * (r * M + m) + part] = wv;
+      reinterpret_cast<float*>(sWc)[2 * (m * M + r) + part] = part ? (float)-wv : (float)wv;
     }
     if (!ok && lane == 0) atomicOr(err, kErrIpNorm);
     mant *= ok ? s : 1.0;
@@ -276,12 +308,26 @@ __device__ void ip_columns(const double2* Qi, double2* sW, double2* sB, double2*
   __syncwarp();
 }
 
+// Sum over the warps of a CTA of the per-warp rows red[w][0..MP) written before the barrier;
+// every lane of every warp returns the same M totals (same order everywhere).
+template <int M, int MP>
+__device__ __forceinline__ void cta_rows_sum(const float* red, int nw, int lane, float (&tot)[M]) {
+  // lane l = w*MP + m reads warp w's value m; butterfly over the warp index bits
+  const int w = lane / MP, m = lane - (lane / MP) * MP;
+  float v = (w < nw && m < M) ? red[w * 32 + m] : 0.f;
+#pragma unroll
+  for (int off = MP; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+#pragma unroll
+  for (int i = 0; i < M; ++i) tot[i] = __shfl_sync(0xffffffffu, v, i);
+}
+
 template <int M, int N>
-__global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
+__global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
   constexpr int MP = pow2_ceil(M);
   constexpr int NE = M * M;                   // packed Hermitian entries per Q_m
+  static_assert(MP * (kMaxWarps) <= 32, "n-step reduction rows must fit one warp");
 
   const int f = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -301,17 +347,21 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
   double2* sQ = sWork + M * M;
   double* sDet = reinterpret_cast<double*>(sQ + SM::kQsz);
   float2* sWc = reinterpret_cast<float2*>(sDet + 4);
-  float* sL = reinterpret_cast<float*>(sWc + M * M);
-  float* sRed = sL + ((M * N + 3) & ~3);
+  float* sRed = reinterpret_cast<float*>(sWc + M * M);
   float* sLL = sRed + 2 * kMaxWarps * SM::kRedW;
   float* sH = sLL + kMaxWarps;
   float* sU = sH + N * Tp;
 
   const float2* xf = p.x + (size_t)f * T * M;
   const double invT = 1.0 / (double)T;
+  const float invTf = 1.0f / (float)T;
 
   // ---- load the parameters of frequency f
-  for (int i = tid; i < M * N; i += bd) sL[i] = p.lam[(size_t)f * M * N + i];
+  float Lr[M][N];
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int n = 0; n < N; ++n) Lr[m][n] = __ldg(p.lam + (size_t)f * M * N + m * N + n);
   for (int i = tid; i < M * M; i += bd) sW[i] = p.P[(size_t)f * M * M + i];
   for (int n = 0; n < N; ++n) {
     const float* vf = p.v + ((size_t)f * N + n) * T;
@@ -347,10 +397,26 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
   }
   __syncthreads();
 
+  // per-slot registers: r[k][m] holds 1/sigma^2 during the Q pass and r_{mt} in the sweep
   float r[kSlots][M];
   int par = 0;
 
-  // U for the current W (needed when only the log-likelihood is asked for)
+  auto load_x = [&](int t, float2 (&xv)[M]) {
+    const float2* src = xf + (size_t)t * M;
+    if constexpr (M % 2 == 0) {
+#pragma unroll
+      for (int a = 0; a < M; a += 2) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src + a));
+        xv[a] = make_float2(q.x, q.y);
+        xv[a + 1] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
+    }
+  };
+
+  // U = |W^H x|^2 for the current W
   auto pass_U = [&]() {
     float2 wc[M * M];
 #pragma unroll
@@ -360,8 +426,7 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
       const int t = tid + k * bd;
       if (t < T) {
         float2 xv[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a) xv[a] = __ldg(xf + (size_t)t * M + a);
+        load_x(t, xv);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           float2 y = make_float2(0.f, 0.f);
@@ -372,62 +437,77 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
       }
     }
   };
+
+  // sigma^2 = LH, 1/sigma^2 -> r, log-likelihood terms (when U is current); optionally first
+  // applies the pending H[nprev,:] update of the last source of the sweep.
+  auto pass_A = [&](bool with_ll, bool apply_prev, int nprev, const float (&coef)[M]) -> float {
+    float llp = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+      const int t = tid + k * bd;
+      if (t < T) {
+        float h[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
+        if (apply_prev) {
+          float g = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
+#pragma unroll
+          for (int n = 0; n < N; ++n)
+            if (n == nprev) { h[n] *= g; sH[n * Tp + t] = h[n]; }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float s2 = 0.f;
+#pragma unroll
+          for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
+          bad |= !(s2 > 0.f && s2 < INFINITY);
+          const float rs = fast_rcp(s2);
+          r[k][m] = rs;
+          if (with_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
+        }
+      }
+    }
+    if (bad) atomicOr(p.err, kErrSigma);
+    return llp;
+  };
+
+  auto ll_from_sum = [&](double s) {
+    const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
+    return (double)T * logdet - s - (double)M * (double)T * kLnPi;
+  };
+
+  float coef[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) coef[m] = 0.f;
+
   if (p.n_iter == 0) pass_U();
+  float llp = pass_A(p.n_iter == 0, false, 0, coef);
 
   for (int it = 0;; ++it) {
     const bool have_ll = (it > 0) || (p.n_iter == 0);
     const bool do_iter = it < p.n_iter;
-
-    // ---- pass A: sigma^2 = LH, 1/sigma^2 -> r, log-likelihood terms
-    {
-      float Lr[M][N];
-#pragma unroll
-      for (int m = 0; m < M; ++m)
-#pragma unroll
-        for (int n = 0; n < N; ++n) Lr[m][n] = sL[m * N + n];
-      float llp = 0.f;
-      bool bad = false;
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        const int t = tid + k * bd;
-        if (t < T) {
-          float h[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            float s2 = 0.f;
-#pragma unroll
-            for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
-            bad |= !(s2 > 0.f) || !(s2 < INFINITY);
-            const float rs = fast_rcp(s2);
-            r[k][m] = rs;
-            if (have_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
-          }
-        }
-      }
-      if (bad) atomicOr(p.err, kErrSigma);
-      if (have_ll) {
-        llp = warp_sum(llp);
-        if (lane == 0) sLL[warp] = llp;
-      }
+    FFCA_MARK(it, 0);
+    if (have_ll) {
+      llp = warp_sum(llp);
+      if (lane == 0) sLL[warp] = llp;
     }
-
     if (!do_iter) {
       __syncthreads();
       if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += (double)sLL[w];
-        const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
-        const double ll = (double)T * logdet - s - (double)M * (double)T * kLnPi;
+        const double ll = ll_from_sum(s);
         if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
         if (p.ll_last) p.ll_last[f] = ll;
       }
       break;
     }
 
-    // ---- Q_m accumulation, chunk by chunk over m, and its CTA reduction
-#pragma unroll 1
+    // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33), chunk by chunk over m
+#pragma unroll
     for (int c = 0; c < QCH; ++c) {
       float acc[VP];
 #pragma unroll
@@ -437,18 +517,12 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
         const int t = tid + k * bd;
         if (t < T) {
           float2 xv[M];
-#pragma unroll
-          for (int a = 0; a < M; ++a) xv[a] = __ldg(xf + (size_t)t * M + a);
+          load_x(t, xv);
           float e[NE];
           xxh_packed<M>(xv, e);
 #pragma unroll
           for (int mm = 0; mm < MC; ++mm) {
-            // r[k][c*MC + mm] with a compile-time index per unrolled c is not available
-            // (c is a runtime loop), so select it.
-            float w = r[k][0];
-#pragma unroll
-            for (int m2 = 1; m2 < M; ++m2)
-              if (m2 == c * MC + mm) w = r[k][m2];
+            const float w = r[k][c * MC + mm];
 #pragma unroll
             for (int q = 0; q < NE; ++q) acc[mm * NE + q] = fmaf(w, e[q], acc[mm * NE + q]);
           }
@@ -476,7 +550,6 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
         if (e < M) {
           Qm[e * M + e] = make_double2(qd, 0.0);
         } else {
-          // decode pair index
           int idx = (e - M) >> 1;
           const bool im = ((e - M) & 1) != 0;
           int a = 0;
@@ -486,47 +559,35 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
           else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
         }
       }
-      if (c == 0 && have_ll && tid == 0) {
+      if (c == 0 && have_ll && tid == 32 % bd) {
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += (double)sLL[w];
-        const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
-        const double ll = (double)T * logdet - s - (double)M * (double)T * kLnPi;
-        if (p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+        if (p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(s);
       }
       par ^= 1;
     }
     __syncthreads();
+    FFCA_MARK(it, 1);
 
     // ---- IP (FP64): Q_m^{-1} for all m (warp m), then the column loop (warp 0)
-    for (int m = warp; m < M; m += nw) warp_hpd_inverse<M>(sQ + m * M * M, lane, p.err);
+    if (warp == 0) warp_hpd_inverse_all<M>(sQ, lane, p.err);
+    __syncwarp();
+    FFCA_MARK(it, 2);
+    if (warp == 0) ip_columns<M>(sQ, sW, sB, sWc, sDet, lane, p.err);
     __syncthreads();
-    if (warp == 0) ip_columns<M>(sQ, sW, sB, sWork, sWc, sDet, lane, p.err);
-    __syncthreads();
+    FFCA_MARK(it, 3);
 
-    // ---- U = |W^H x|^2
+    // ---- U = |W^H x|^2 (Eq. 37)
     pass_U();
+    FFCA_MARK(it, 4);
 
-    // ---- NMF EM sweep over sources (Gauss-Seidel)
-#pragma unroll 1
+    // ---- NMF EM sweep over sources (Algorithm 1 n-loop, Gauss-Seidel).  Pass n applies
+    // the H[n-1,:] update of the previous source, then forms r for source n.
+#pragma unroll
     for (int n = 0; n < N; ++n) {
-      float Lr[M][N];
-#pragma unroll
-      for (int m = 0; m < M; ++m)
-#pragma unroll
-        for (int n2 = 0; n2 < N; ++n2) Lr[m][n2] = sL[m * N + n2];
-      float Ln[M];
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        float v = Lr[m][0];
-#pragma unroll
-        for (int n2 = 1; n2 < N; ++n2)
-          if (n2 == n) v = Lr[m][n2];
-        Ln[m] = v;
-      }
       float acc[MP];
 #pragma unroll
       for (int m = 0; m < MP; ++m) acc[m] = 0.f;
-      bool bad = false;
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
         const int t = tid + k * bd;
@@ -534,58 +595,56 @@ __global__ void __launch_bounds__(kMaxThreads) fastfca_em_kernel(EmArgs p) {
           float h[N];
 #pragma unroll
           for (int n2 = 0; n2 < N; ++n2) h[n2] = sH[n2 * Tp + t];
-          const float hn = sH[n * Tp + t];
+          if (n > 0) {
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
+            h[n - 1] *= g;
+            sH[(n - 1) * Tp + t] = h[n - 1];
+          }
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             float s2 = 0.f;
 #pragma unroll
             for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
-            bad |= !(s2 > 0.f) || !(s2 < INFINITY);
             const float rs = fast_rcp(s2);
-            const float G = Ln[m] * hn * rs;
+            const float G = Lr[m][n] * h[n] * rs;
             const float rr = fmaf(G, fmaf(sU[m * Tp + t], rs, -1.f), 1.f);
             r[k][m] = rr;
             acc[m] += rr;
           }
         }
       }
-      if (bad) atomicOr(p.err, kErrSigma);
       warp_reduce_scatter<MP>(acc, lane);
       {
         float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
         if ((lane * MP) % 32 == 0) red[(lane * MP) / 32] = acc[0];
       }
       __syncthreads();
-      float coef[M];
-      {
-        const float* red = sRed + par * kMaxWarps * SM::kRedW;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          float s = 0.f;
-          for (int w = 0; w < nw; ++w) s += red[w * SM::kRedW + m];
-          const float mean = s * (float)invT;
-          coef[m] = fast_rcp(mean) * (1.0f / (float)M);
-          if (tid == m) sL[m * N + n] = Ln[m] * mean;
-        }
-      }
+      float tot[M];
+      cta_rows_sum<M, MP>(sRed + par * kMaxWarps * SM::kRedW, nw, lane, tot);
       par ^= 1;
 #pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        const int t = tid + k * bd;
-        if (t < T) {
-          float g = 0.f;
-#pragma unroll
-          for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-          sH[n * Tp + t] *= g;
-        }
+      for (int m = 0; m < M; ++m) {
+        const float mean = tot[m] * invTf;
+        Lr[m][n] *= mean;
+        coef[m] = fast_rcp(mean) * (1.0f / (float)M);
       }
-      __syncthreads();
+      FFCA_MARK(it, 5 + (n < 9 ? n : 9));
     }
+    // last source's H update, then sigma^2 / 1/sigma^2 / log-likelihood of the new parameters
+    llp = pass_A(true, true, N - 1, coef);
+    FFCA_MARK(it, 15);
   }
 
   // ---- write back
   __syncthreads();
-  for (int i = tid; i < M * N; i += bd) p.lam[(size_t)f * M * N + i] = sL[i];
+  if (tid == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int n = 0; n < N; ++n) p.lam[(size_t)f * M * N + m * N + n] = Lr[m][n];
+  }
   for (int i = tid; i < M * M; i += bd) {
     p.P[(size_t)f * M * M + i] = sW[i];
     p.Bst[(size_t)f * M * M + i] = sB[i];
