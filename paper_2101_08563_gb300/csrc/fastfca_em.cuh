@@ -438,42 +438,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     }
   };
 
-  // sigma^2 = LH, 1/sigma^2 -> r, log-likelihood terms (when U is current); optionally first
-  // applies the pending H[nprev,:] update of the last source of the sweep.
-  auto pass_A = [&](bool with_ll, bool apply_prev, int nprev, const float (&coef)[M]) -> float {
-    float llp = 0.f;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      const int t = tid + k * bd;
-      if (t < T) {
-        float h[N];
-#pragma unroll
-        for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
-        if (apply_prev) {
-          float g = 0.f;
-#pragma unroll
-          for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-#pragma unroll
-          for (int n = 0; n < N; ++n)
-            if (n == nprev) { h[n] *= g; sH[n * Tp + t] = h[n]; }
-        }
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          float s2 = 0.f;
-#pragma unroll
-          for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
-          bad |= !(s2 > 0.f && s2 < INFINITY);
-          const float rs = fast_rcp(s2);
-          r[k][m] = rs;
-          if (with_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
-        }
-      }
-    }
-    if (bad) atomicOr(p.err, kErrSigma);
-    return llp;
-  };
-
   auto ll_from_sum = [&](double s) {
     const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
     return (double)T * logdet - s - (double)M * (double)T * kLnPi;
@@ -484,15 +448,51 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
   for (int m = 0; m < M; ++m) coef[m] = 0.f;
 
   if (p.n_iter == 0) pass_U();
-  float llp = pass_A(p.n_iter == 0, false, 0, coef);
 
+  // The loop body is written once (n and the Q chunks are runtime loops) so that the
+  // kernel's code stays small enough for the instruction cache; register arrays are indexed
+  // with compile-time indices only, through selects.
+#pragma unroll 1
   for (int it = 0;; ++it) {
     const bool have_ll = (it > 0) || (p.n_iter == 0);
     const bool do_iter = it < p.n_iter;
     FFCA_MARK(it, 0);
-    if (have_ll) {
-      llp = warp_sum(llp);
-      if (lane == 0) sLL[warp] = llp;
+
+    // ---- pass A: the pending H[N-1,:] update of the last sweep (it > 0), then
+    // sigma^2 = LH, 1/sigma^2 -> r, and the log-likelihood terms of the current parameters
+    {
+      float llp = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          if (it > 0) {
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
+            sH[(N - 1) * Tp + t] *= g;
+          }
+          float h[N];
+#pragma unroll
+          for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
+            bad |= !(s2 > 0.f && s2 < INFINITY);
+            const float rs = fast_rcp(s2);
+            r[k][m] = rs;
+            if (have_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
+          }
+        }
+      }
+      if (bad) atomicOr(p.err, kErrSigma);
+      if (have_ll) {
+        llp = warp_sum(llp);
+        if (lane == 0) sLL[warp] = llp;
+      }
     }
     if (!do_iter) {
       __syncthreads();
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     }
 
     // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33), chunk by chunk over m
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < QCH; ++c) {
       float acc[VP];
 #pragma unroll
@@ -522,7 +522,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
           xxh_packed<M>(xv, e);
 #pragma unroll
           for (int mm = 0; mm < MC; ++mm) {
-            const float w = r[k][c * MC + mm];
+            float w = r[k][mm];
+#pragma unroll
+            for (int cc = 1; cc < QCH; ++cc)
+              if (cc == c) w = r[k][cc * MC + mm];
 #pragma unroll
             for (int q = 0; q < NE; ++q) acc[mm * NE + q] = fmaf(w, e[q], acc[mm * NE + q]);
           }
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     __syncthreads();
     FFCA_MARK(it, 1);
 
-    // ---- IP (FP64): Q_m^{-1} for all m (warp m), then the column loop (warp 0)
+    // ---- IP (FP64): Q_m^{-1} for all m, then the column loop (warp 0)
     if (warp == 0) warp_hpd_inverse_all<M>(sQ, lane, p.err);
     __syncwarp();
     FFCA_MARK(it, 2);
@@ -583,8 +586,17 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
 
     // ---- NMF EM sweep over sources (Algorithm 1 n-loop, Gauss-Seidel).  Pass n applies
     // the H[n-1,:] update of the previous source, then forms r for source n.
-#pragma unroll
+#pragma unroll 1
     for (int n = 0; n < N; ++n) {
+      float Ln[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float v = Lr[m][0];
+#pragma unroll
+        for (int n2 = 1; n2 < N; ++n2)
+          if (n2 == n) v = Lr[m][n2];
+        Ln[m] = v;
+      }
       float acc[MP];
 #pragma unroll
       for (int m = 0; m < MP; ++m) acc[m] = 0.f;
@@ -592,23 +604,23 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
       for (int k = 0; k < kSlots; ++k) {
         const int t = tid + k * bd;
         if (t < T) {
-          float h[N];
-#pragma unroll
-          for (int n2 = 0; n2 < N; ++n2) h[n2] = sH[n2 * Tp + t];
           if (n > 0) {
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-            h[n - 1] *= g;
-            sH[(n - 1) * Tp + t] = h[n - 1];
+            sH[(n - 1) * Tp + t] *= g;
           }
+          float h[N];
+#pragma unroll
+          for (int n2 = 0; n2 < N; ++n2) h[n2] = sH[n2 * Tp + t];
+          const float hn = sH[n * Tp + t];
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             float s2 = 0.f;
 #pragma unroll
             for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
             const float rs = fast_rcp(s2);
-            const float G = Lr[m][n] * h[n] * rs;
+            const float G = Ln[m] * hn * rs;
             const float rr = fmaf(G, fmaf(sU[m * Tp + t], rs, -1.f), 1.f);
             r[k][m] = rr;
             acc[m] += rr;
@@ -627,13 +639,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const float mean = tot[m] * invTf;
-        Lr[m][n] *= mean;
+#pragma unroll
+        for (int n2 = 0; n2 < N; ++n2)
+          if (n2 == n) Lr[m][n2] *= mean;
         coef[m] = fast_rcp(mean) * (1.0f / (float)M);
       }
       FFCA_MARK(it, 5 + (n < 9 ? n : 9));
     }
-    // last source's H update, then sigma^2 / 1/sigma^2 / log-likelihood of the new parameters
-    llp = pass_A(true, true, N - 1, coef);
     FFCA_MARK(it, 15);
   }
 
