@@ -133,6 +133,35 @@ void fastfca_destroy(fastfca_ctx* ctx);
 /* Library version string. */
 const char* fastfca_version(void);
 
+/* Largest F*M*M that fastfca_separate_noalloc accepts (complex64 values of its static
+ * scratch: 512 KiB of device memory). */
+#define FASTFCA_NOALLOC_MAX_FMM 65536
+
+/* The Wiener-filter separation of fastfca_separate (Eq. 39), for callers that must not
+ * allocate device memory, with no context.  The paper has no counterpart: this is a
+ * deployment variant.  Who needs it: code that separates audio inside a real-time callback
+ * (or another section where an allocation may block the thread or synchronise the device
+ * and so miss a deadline) cannot call cudaMalloc there.  This call allocates nothing: the
+ * caller supplies every input and the output, and the one intermediate (W^{-H}, F*M*M
+ * complex64 values) lives in a fixed array compiled into the library, present in the
+ * memory of every GPU that loads it until the process exits.
+ *
+ *   x    complex64  [F][T][M]  device     P    complex128 [F][M][M]  device
+ *   lam  float32    [F][M][N]  device     v    float32    [F][N][T]  device
+ *   c    complex64  [F][T][N][M] device (output, caller-allocated)
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ *
+ * Returns EINVAL when F*M*M > FASTFCA_NOALLOC_MAX_FMM, a size is not positive, a pointer is
+ * NULL or not a device pointer; EUNSUPPORTED for an (M, N) without a kernel; ECUDA when a
+ * launch fails.  The message is in fastfca_last_error(NULL).  Asynchronous on the stream;
+ * it reports no kernel-side numerical status.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress): make that call before any stream capture.
+ * All calls share the array, which keeps the last call's contents: calls that overlap on
+ * the GPU (other streams, other host threads) race on it and must be serialised. */
+fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t N, const void* x,
+                                        const void* P, const float* lam, const float* v, void* c,
+                                        void* stream);
+
 #ifdef __cplusplus
 }
 #endif

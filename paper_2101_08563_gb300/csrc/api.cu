@@ -22,6 +22,10 @@ thread_local char g_create_error[512] = "";
 
 }  // namespace
 
+namespace ffca {
+void set_thread_error(const char* msg) { snprintf(g_create_error, sizeof g_create_error, "%s", msg); }
+}  // namespace ffca
+
 struct fastfca_ctx {
   fastfca_config cfg{};
   cudaStream_t stream = nullptr;

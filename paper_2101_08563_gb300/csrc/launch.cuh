@@ -55,6 +55,9 @@ FastOps make_fast_ops() {
   return o;
 }
 
+// Records a message for fastfca_last_error(NULL) on the calling thread (api.cu).
+void set_thread_error(const char* msg);
+
 // Defined in the per-M translation units.
 bool fast_ops_m2(int N, FastOps* o);
 bool fast_ops_m3(int N, FastOps* o);

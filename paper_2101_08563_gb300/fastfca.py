@@ -40,6 +40,8 @@ _SIGNATURES = {
     "fastfca_last_error": (ctypes.c_char_p, [_P]),
     "fastfca_destroy": (None, [_P]),
     "fastfca_version": (ctypes.c_char_p, []),
+    "fastfca_separate_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                _P, _P, _P, _P, _P, _P]),
 }
 
 

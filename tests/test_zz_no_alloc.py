@@ -1,0 +1,68 @@
+"""fastfca_separate_noalloc: the separation entry point for callers that cannot allocate.
+
+Code that separates audio inside a real-time callback (or any section where an allocator
+call may block the thread or synchronise the device) cannot call cudaMalloc there.  The
+library gives such callers one entry point that takes every input and output from them and
+keeps its single intermediate in a fixed array compiled into the library.  This test calls it
+through the C ABI, twice in a row, and checks both outputs against the context-based
+fastfca_separate on the same parameters.  It lives in its own file, collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2101_08563_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4   # the source-image tolerance the other GPU tests use
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def test_noalloc_separation_matches_context_separation():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2101_08563_gb300 import build, fastfca
+    build.build()
+    lib = fastfca.load()
+
+    M, N, F, T = 3, 4, 11, 300
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=21)
+    rng = np.random.Generator(np.random.PCG64(21))
+    P = (rng.standard_normal((F, M, M)) + 1j * rng.standard_normal((F, M, M))) * 0.3 + np.eye(M)
+    lam = rng.uniform(0.2, 2.0, (F, M, N)).astype(np.float32)
+    v = rng.uniform(0.2, 5.0, (F, N, T)).astype(np.float32)
+
+    xd = torch.from_numpy(mix.x).cuda()
+    sep = fastfca.Separator(xd, N)
+    sep.set_params(P, lam, v)
+    ref = sep.separate()
+    sep.close()
+
+    Pd = torch.from_numpy(P).cuda()
+    lamd = torch.from_numpy(lam).cuda()
+    vd = torch.from_numpy(v).cuda()
+    c = torch.empty((F, T, N, M), dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        c.fill_(float("nan"))
+        st = lib.fastfca_separate_noalloc(F, T, M, N, _p(xd), _p(Pd), _p(lamd), _p(vd), _p(c),
+                                          ctypes.c_void_p(stream))
+        assert st == 0, lib.fastfca_last_error(None)
+        torch.cuda.synchronize()
+        got = c.cpu().numpy()
+        assert np.all(np.isfinite(got)), f"call {call}: output not fully written"
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= IMG_TOL, f"call {call}: relative error {err}"
+
+    # sizes beyond the static scratch are refused before any launch
+    big_F = 65536 // (M * M) + 1
+    st = lib.fastfca_separate_noalloc(big_F, T, M, N, _p(xd), _p(Pd), _p(lamd), _p(vd), _p(c),
+                                      ctypes.c_void_p(stream))
+    assert st == 1 and b"exceeds" in lib.fastfca_last_error(None)
