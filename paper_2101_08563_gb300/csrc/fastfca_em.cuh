@@ -38,6 +38,8 @@ namespace ffca {
 constexpr int kSlots = 8;          // frames per thread
 constexpr int kMaxThreads = 256;   // so at most kSlots * 256 = 2048 frames per frequency
 constexpr int kMaxWarps = kMaxThreads / 32;
+// Register cap: 4 CTAs of 160 threads (T <= 1280) or 2 of 256 fit an SM's 64K registers.
+constexpr int kEmMaxRegs = 96;
 
 struct EmArgs {
   const float2* x;      // F x T x M complex64, m fastest
@@ -98,16 +100,16 @@ struct EmSmem {
   // inverse of W^H (M*M source + M*2M augmented work).
   static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
   static size_t bytes(int threads) {
-    const size_t Tp = (size_t)threads * kSlots;
     size_t b = 0;
     b += sizeof(double2) * M * M * 3;        // sW, sB, sWork
     b += sizeof(double2) * kQsz;             // sQ
     b += sizeof(double) * 4;                 // sDet (mantissa, exponent), spare
     b += sizeof(float2) * M * M;             // sWc
+    b += sizeof(float) * ((M * N + 3) & ~3); // sL
     b += sizeof(float) * 2 * kMaxWarps * kRedW;
     b += sizeof(float) * kMaxWarps;          // sLL
-    b += sizeof(float) * N * Tp;             // sH
-    b += sizeof(float) * M * Tp;             // sU
+    b += sizeof(float) * (size_t)threads * (kSlots * N + 1);   // sH, thread-major
+    b += sizeof(float) * (size_t)threads * (kSlots * M + 1);   // sU, thread-major
     return b;
   }
 };
@@ -322,7 +324,7 @@ __device__ __forceinline__ void cta_rows_sum(const float* red, int nw, int lane,
 }
 
 template <int M, int N>
-__global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
+__global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
   constexpr int MP = pow2_ceil(M);
@@ -347,28 +349,30 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
   double2* sQ = sWork + M * M;
   double* sDet = reinterpret_cast<double*>(sQ + SM::kQsz);
   float2* sWc = reinterpret_cast<float2*>(sDet + 4);
-  float* sRed = reinterpret_cast<float*>(sWc + M * M);
+  float* sL = reinterpret_cast<float*>(sWc + M * M);
+  float* sRed = sL + ((M * N + 3) & ~3);
   float* sLL = sRed + 2 * kMaxWarps * SM::kRedW;
   float* sH = sLL + kMaxWarps;
-  float* sU = sH + N * Tp;
+  // H and U are stored thread-major: thread tid's frames (slot k) at sH[tid*SH + k*N + n]
+  // and sU[tid*SU + k*M + m].  The odd strides SH, SU keep a warp's accesses on distinct
+  // banks, and every access in the passes is a compile-time offset from one base pointer.
+  constexpr int SH = kSlots * N + 1, SU = kSlots * M + 1;
+  float* sU = sH + bd * SH;
+  float* pH = sH + tid * SH;
+  float* pU = sU + tid * SU;
 
   const float2* xf = p.x + (size_t)f * T * M;
   const double invT = 1.0 / (double)T;
   const float invTf = 1.0f / (float)T;
 
   // ---- load the parameters of frequency f
-  float Lr[M][N];
-#pragma unroll
-  for (int m = 0; m < M; ++m)
-#pragma unroll
-    for (int n = 0; n < N; ++n) Lr[m][n] = __ldg(p.lam + (size_t)f * M * N + m * N + n);
+  for (int i = tid; i < M * N; i += bd) sL[i] = p.lam[(size_t)f * M * N + i];
   for (int i = tid; i < M * M; i += bd) sW[i] = p.P[(size_t)f * M * M + i];
   for (int n = 0; n < N; ++n) {
     const float* vf = p.v + ((size_t)f * N + n) * T;
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      const int t = tid + k * bd;
-      sH[n * Tp + t] = (t < T) ? vf[t] : 1.0f;
+    for (int t = tid; t < Tp; t += bd) {
+      const int owner = t % bd, k = t / bd;
+      sH[owner * SH + k * N + n] = (t < T) ? vf[t] : 1.0f;
     }
   }
   __syncthreads();
@@ -396,6 +400,17 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     }
   }
   __syncthreads();
+
+  // L (M x N) lives in shared memory and every thread reads it into registers at the start
+  // of each pass.  After a source's reduction every thread stores the same new column
+  // (identical values), so each thread's later reads see the new column through its own
+  // store, without another barrier.
+  auto load_L = [&](float (&Lr)[M][N]) {
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int n = 0; n < N; ++n) Lr[m][n] = sL[m * N + n];
+  };
 
   // per-slot registers: r[k][m] holds 1/sigma^2 during the Q pass and r_{mt} in the sweep
   float r[kSlots][M];
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
           float2 y = make_float2(0.f, 0.f);
 #pragma unroll
           for (int a = 0; a < M; ++a) y = cfmaf(wc[m * M + a], xv[a], y);
-          sU[m * Tp + t] = fmaf(y.x, y.x, y.y * y.y);
+          pU[k * M + m] = fmaf(y.x, y.x, y.y * y.y);
         }
       }
     }
@@ -461,6 +476,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     // ---- pass A: the pending H[N-1,:] update of the last sweep (it > 0), then
     // sigma^2 = LH, 1/sigma^2 -> r, and the log-likelihood terms of the current parameters
     {
+      float Lr[M][N];
+      load_L(Lr);
       float llp = 0.f;
       bool bad = false;
 #pragma unroll
@@ -471,11 +488,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-            sH[(N - 1) * Tp + t] *= g;
+            pH[k * N + N - 1] *= g;
           }
           float h[N];
 #pragma unroll
-          for (int n = 0; n < N; ++n) h[n] = sH[n * Tp + t];
+          for (int n = 0; n < N; ++n) h[n] = pH[k * N + n];
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             float s2 = 0.f;
@@ -484,7 +501,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
             bad |= !(s2 > 0.f && s2 < INFINITY);
             const float rs = fast_rcp(s2);
             r[k][m] = rs;
-            if (have_ll) llp += fmaf(sU[m * Tp + t], rs, __logf(s2));
+            if (have_ll) llp += fmaf(pU[k * M + m], rs, __logf(s2));
           }
         }
       }
@@ -588,15 +605,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
     // the H[n-1,:] update of the previous source, then forms r for source n.
 #pragma unroll 1
     for (int n = 0; n < N; ++n) {
+      float* pHn = pH + n;                   // this thread's H[n, .] (slot k at k*N)
+      float Lr[M][N];
+      load_L(Lr);
       float Ln[M];
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        float v = Lr[m][0];
-#pragma unroll
-        for (int n2 = 1; n2 < N; ++n2)
-          if (n2 == n) v = Lr[m][n2];
-        Ln[m] = v;
-      }
+      for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
       float acc[MP];
 #pragma unroll
       for (int m = 0; m < MP; ++m) acc[m] = 0.f;
@@ -608,12 +622,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-            sH[(n - 1) * Tp + t] *= g;
+            pHn[k * N - 1] *= g;
           }
           float h[N];
 #pragma unroll
-          for (int n2 = 0; n2 < N; ++n2) h[n2] = sH[n2 * Tp + t];
-          const float hn = sH[n * Tp + t];
+          for (int n2 = 0; n2 < N; ++n2) h[n2] = pH[k * N + n2];
+          const float hn = pHn[k * N];
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             float s2 = 0.f;
@@ -621,7 +635,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
             for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
             const float rs = fast_rcp(s2);
             const float G = Ln[m] * hn * rs;
-            const float rr = fmaf(G, fmaf(sU[m * Tp + t], rs, -1.f), 1.f);
+            const float rr = fmaf(G, fmaf(pU[k * M + m], rs, -1.f), 1.f);
             r[k][m] = rr;
             acc[m] += rr;
           }
@@ -639,9 +653,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const float mean = tot[m] * invTf;
-#pragma unroll
-        for (int n2 = 0; n2 < N; ++n2)
-          if (n2 == n) Lr[m][n2] *= mean;
+        sL[m * N + n] = Ln[m] * mean;       // same value from every thread
         coef[m] = fast_rcp(mean) * (1.0f / (float)M);
       }
       FFCA_MARK(it, 5 + (n < 9 ? n : 9));
@@ -651,12 +663,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
 
   // ---- write back
   __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int m = 0; m < M; ++m)
-#pragma unroll
-      for (int n = 0; n < N; ++n) p.lam[(size_t)f * M * N + m * N + n] = Lr[m][n];
-  }
+  for (int i = tid; i < M * N; i += bd) p.lam[(size_t)f * M * N + i] = sL[i];
   for (int i = tid; i < M * M; i += bd) {
     p.P[(size_t)f * M * M + i] = sW[i];
     p.Bst[(size_t)f * M * M + i] = sB[i];
@@ -664,11 +671,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) fastfca_em_kernel(EmArgs p) {
   if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
   for (int n = 0; n < N; ++n) {
     float* vf = p.v + ((size_t)f * N + n) * T;
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      const int t = tid + k * bd;
-      if (t < T) vf[t] = sH[n * Tp + t];
-    }
+    for (int t = tid; t < T; t += bd) vf[t] = sH[(t % bd) * SH + (t / bd) * N + n];
   }
 }
 
