@@ -133,6 +133,56 @@ void fastfca_destroy(fastfca_ctx* ctx);
 /* Library version string. */
 const char* fastfca_version(void);
 
+/* ------------------------------------------------------------------------------------------
+ * Batches: many independent mixtures (mixed M, N, T) iterated together in one CUDA-graph
+ * launch.  Each (mixture, frequency) pair is one work item run by one CTA with the same code
+ * as the single-mixture path; items are grouped into classes by (M, N) and a frame bucket,
+ * each class is one persistent launch whose CTAs take items longest-first from an atomic
+ * counter, and all classes run concurrently on forked streams inside one captured graph.
+ * (Not in the paper: FastFCA processes frequencies independently, Sec. IV-G, so independent
+ * mixtures batch naturally.)
+ */
+typedef struct fastfca_batch fastfca_batch;
+
+/* Creates a batch of B FastFCA mixtures: cfgs[b] (model must be FASTFCA) and xs[b] (complex64
+ * [F][T][M], host or device; device arrays are borrowed).  Parameters start as in
+ * fastfca_create.  The initial schedule is the finest bucketing with one grid share per
+ * class; fastfca_batch_tune picks a measured one. */
+fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const void* const* xs, void* stream,
+                                    fastfca_batch** out);
+
+/* Replaces mixture b's parameters (layouts as fastfca_set_params; host or device). */
+fastfca_status fastfca_batch_set_params(fastfca_batch* batch, int32_t b, const void* P, const float* lam,
+                                        const float* v);
+
+/* Copies mixture b's parameters out (host or device; NULL skips).  Synchronises. */
+fastfca_status fastfca_batch_get_params(fastfca_batch* batch, int32_t b, void* P, float* lam, float* v);
+
+/* Runs n_iter IP+EM iterations (Algorithm 1) on every frequency of every mixture with one
+ * graph launch (the graph is captured on first use of each n_iter and reused).  Optional host
+ * outputs: ll_per_mixture[b] = sum_f l_f after the last iteration; seconds_per_mixture[b] =
+ * the span between the first start and the last end of mixture b's items inside the launch
+ * (%globaltimer).  With either output the call synchronises; otherwise it is asynchronous. */
+fastfca_status fastfca_batch_iterate(fastfca_batch* batch, int32_t n_iter, double* ll_per_mixture,
+                                     double* seconds_per_mixture);
+
+/* Autotuner: times every candidate schedule (frame bucketing: fine / coarse / one per (M, N);
+ * grid share factor 1, 2 or 4) on this batch with n_iter iterations, restores the parameters,
+ * and keeps the fastest.  *scheme and *factor (may be NULL) receive the choice. */
+fastfca_status fastfca_batch_tune(fastfca_batch* batch, int32_t n_iter, int32_t* scheme, double* factor);
+
+/* Sets a schedule directly (scheme 0 fine, 1 coarse, 2 one per (M, N); factor > 0). */
+fastfca_status fastfca_batch_schedule(fastfca_batch* batch, int32_t scheme, double factor);
+
+/* Wiener-filter separation of mixture b into c (complex64 [F][T][N][M], device). */
+fastfca_status fastfca_batch_separate(fastfca_batch* batch, int32_t b, void* c);
+
+/* Last error message of the batch (or of the last failed batch create when NULL). */
+const char* fastfca_batch_last_error(const fastfca_batch* batch);
+
+/* Frees everything the batch owns (never borrowed device mixtures). */
+void fastfca_batch_destroy(fastfca_batch* batch);
+
 /* Largest F*M*M that fastfca_separate_noalloc accepts (complex64 values of its static
  * scratch: 512 KiB of device memory). */
 #define FASTFCA_NOALLOC_MAX_FMM 65536

@@ -1,0 +1,569 @@
+// Batched FastFCA: many mixtures with mixed (M, N, T) in one CUDA-graph launch.
+//
+// Work unit: one frequency of one mixture (an EmItem), run start to finish by one CTA with the
+// same per-frequency code as the single-mixture path (em_frequency).  Items are grouped into
+// classes by (M, N) and a frame bucket that fixes the CTA size; every class runs as one
+// persistent launch whose CTAs take items from an atomic counter, longest first.  All class
+// launches sit on forked streams inside one captured CUDA graph, so one graph launch runs the
+// whole batch.  The schedule (bucketing of T into CTA sizes, CTAs per class) is chosen by a
+// small autotuner that times each candidate on the batch itself (fastfca_batch_tune).
+// %globaltimer stamps per item give each mixture's wall time inside the launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fastfca.h"
+#include "launch.cuh"
+
+namespace {
+
+struct Mix {
+  fastfca_config cfg{};
+  const float2* x = nullptr;
+  float2* x_owned = nullptr;
+  double2* P = nullptr;
+  float* lam = nullptr;
+  float* v = nullptr;
+  double2* Bst = nullptr;
+  double* detst = nullptr;
+  double* ll_last = nullptr;
+  int* flags = nullptr;
+  float2* winv = nullptr;
+  size_t item0 = 0;          // global index of this mixture's frequency 0
+  ffca::FastOps ops{};
+};
+
+struct Class {
+  int M = 0, N = 0, bd = 0, grid = 0;
+  std::vector<size_t> items;          // global item indices, longest first
+  ffca::EmItem* d_items = nullptr;
+  int* d_counter = nullptr;
+  ffca::FastOps ops{};
+};
+
+// Frame-bucket schemes the tuner chooses between.
+enum Scheme { kFine = 0, kCoarse = 1, kSingle = 2, kNumSchemes = 3 };
+
+int bucket_threads(int scheme, int T, int group_max_T) {
+  auto warps_for = [](int t) { return std::max(1, (t + 32 * ffca::kSlots - 1) / (32 * ffca::kSlots)); };
+  switch (scheme) {
+    case kFine: return 32 * warps_for(T);
+    case kCoarse: return T <= 1024 ? 128 : 256;
+    default: return 32 * warps_for(group_max_T);
+  }
+}
+
+}  // namespace
+
+struct fastfca_batch {
+  std::vector<Mix> mix;
+  std::vector<ffca::EmItem> items;     // host mirror, global order (mixture-major)
+  std::vector<Class> classes;
+  unsigned long long* d_stamps = nullptr;
+  int* d_err = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;       // one join event per side stream
+  cudaEvent_t fork = nullptr;
+  cudaStream_t capture = nullptr;    // graphs are captured here (never the legacy stream)
+  std::map<int, cudaGraphExec_t> graphs;
+  int scheme = kFine;
+  double grid_factor = 1.0;
+  int sms = 0;
+  fastfca_status sticky = FASTFCA_OK;
+  char msg[512] = "";
+};
+
+namespace {
+
+fastfca_status bfail(fastfca_batch* b, fastfca_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) {
+    snprintf(b->msg, sizeof b->msg, "%s", buf);
+    if (st == FASTFCA_ECUDA) b->sticky = st;
+  } else {
+    ffca::set_thread_error(buf);
+  }
+  return st;
+}
+
+#define BCK(b, expr, what)                                                             \
+  do {                                                                                 \
+    cudaError_t e__ = (expr);                                                          \
+    if (e__ != cudaSuccess) {                                                          \
+      cudaGetLastError();                                                              \
+      return bfail(b, e__ == cudaErrorMemoryAllocation ? FASTFCA_ENOMEM : FASTFCA_ECUDA, \
+                   "%s: %s", what, cudaGetErrorString(e__));                           \
+    }                                                                                  \
+  } while (0)
+
+bool is_dev(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (is_dev(src)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+}
+
+cudaError_t copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (is_dev(dst)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+}
+
+__global__ void batch_init_kernel(const float2* __restrict__ x, double2* __restrict__ P, float* __restrict__ lam,
+                                  float* __restrict__ v, int F, int T, int M, int N) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < (size_t)F * M * M) {
+    const size_t r = i % ((size_t)M * M);
+    P[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
+  }
+  if (i < (size_t)F * M * N) lam[i] = 1.0f;
+  if (i < (size_t)F * N * T) {
+    const size_t f = i / ((size_t)N * T), t = i % T;
+    float pw = 0.f;
+    for (int m = 0; m < M; ++m) {
+      const float2 a = x[(f * T + t) * M + m];
+      pw += a.x * a.x + a.y * a.y;
+    }
+    v[i] = fmaxf(pw / (float)(M * N), 1e-30f);
+  }
+}
+
+void free_graphs(fastfca_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+void free_classes(fastfca_batch* b) {
+  for (auto& c : b->classes) {
+    cudaFree(c.d_items);
+    cudaFree(c.d_counter);
+  }
+  b->classes.clear();
+}
+
+void free_batch(fastfca_batch* b) {
+  free_graphs(b);
+  free_classes(b);
+  for (auto& m : b->mix) {
+    cudaFree(m.x_owned);
+    cudaFree(m.P);
+    cudaFree(m.lam);
+    cudaFree(m.v);
+    cudaFree(m.Bst);
+    cudaFree(m.detst);
+    cudaFree(m.ll_last);
+    cudaFree(m.flags);
+    cudaFree(m.winv);
+  }
+  cudaFree(b->d_stamps);
+  cudaFree(b->d_err);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->ev) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->capture) cudaStreamDestroy(b->capture);
+}
+
+double item_cost(const ffca::EmItem& it, int M, int N) { return (double)it.T * (double)(M * M + M * N + 8); }
+
+// Builds the classes of a schedule: bucket the items, order each class longest first, size
+// each class's persistent grid by its share of the work and the occupancy of its kernel.
+fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
+  free_graphs(b);
+  free_classes(b);
+  std::map<std::pair<int, int>, int> group_max_T;
+  for (const auto& m : b->mix) {
+    auto key = std::make_pair(m.cfg.M, m.cfg.N);
+    group_max_T[key] = std::max(group_max_T[key], m.cfg.T);
+  }
+  std::map<std::tuple<int, int, int>, size_t> index;
+  for (size_t mi = 0; mi < b->mix.size(); ++mi) {
+    const Mix& m = b->mix[mi];
+    const int bd = bucket_threads(scheme, m.cfg.T, group_max_T[std::make_pair(m.cfg.M, m.cfg.N)]);
+    auto key = std::make_tuple(m.cfg.M, m.cfg.N, bd);
+    auto it = index.find(key);
+    if (it == index.end()) {
+      Class c;
+      c.M = m.cfg.M;
+      c.N = m.cfg.N;
+      c.bd = bd;
+      c.ops = m.ops;
+      index[key] = b->classes.size();
+      b->classes.push_back(c);
+      it = index.find(key);
+    }
+    Class& c = b->classes[it->second];
+    for (int f = 0; f < m.cfg.F; ++f) c.items.push_back(m.item0 + f);
+  }
+  double total = 0.0;
+  std::vector<double> work(b->classes.size(), 0.0);
+  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+    Class& c = b->classes[ci];
+    std::stable_sort(c.items.begin(), c.items.end(),
+                     [&](size_t a, size_t z) { return b->items[a].T > b->items[z].T; });
+    for (size_t id : c.items) work[ci] += item_cost(b->items[id], c.M, c.N);
+    total += work[ci];
+  }
+  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+    Class& c = b->classes[ci];
+    const int per_sm = std::max(1, c.ops.em_blocks_per_sm(c.bd));
+    const double share = total > 0 ? work[ci] / total : 1.0;
+    int grid = (int)std::lround(grid_factor * share * per_sm * b->sms);
+    grid = std::max(1, std::min<int>(grid, (int)c.items.size()));
+    c.grid = grid;
+    std::vector<ffca::EmItem> h;
+    h.reserve(c.items.size());
+    for (size_t id : c.items) h.push_back(b->items[id]);
+    BCK(b, cudaMalloc(&c.d_items, sizeof(ffca::EmItem) * h.size()), "batch item alloc");
+    BCK(b, cudaMemcpyAsync(c.d_items, h.data(), sizeof(ffca::EmItem) * h.size(), cudaMemcpyHostToDevice, b->stream),
+        "batch item upload");
+    BCK(b, cudaMalloc(&c.d_counter, sizeof(int)), "batch counter alloc");
+  }
+  while (b->side.size() < b->classes.size()) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    BCK(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "side stream");
+    BCK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side event");
+    b->side.push_back(s);
+    b->ev.push_back(e);
+  }
+  if (!b->fork) BCK(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+  b->scheme = scheme;
+  b->grid_factor = grid_factor;
+  BCK(b, cudaStreamSynchronize(b->stream), "batch schedule upload");
+  return FASTFCA_OK;
+}
+
+// Enqueues every class launch: fork from `origin` onto side streams, join back onto it.
+fastfca_status enqueue_all(fastfca_batch* b, int n_iter, cudaStream_t origin) {
+  cudaEvent_t fork = b->fork;
+  BCK(b, cudaEventRecord(fork, origin), "fork record");
+  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+    Class& c = b->classes[ci];
+    cudaStream_t s = b->side[ci];
+    BCK(b, cudaStreamWaitEvent(s, fork, 0), "fork wait");
+    BCK(b, cudaMemsetAsync(c.d_counter, 0, sizeof(int), s), "counter reset");
+    BCK(b, c.ops.em_persistent(c.d_items, (int)c.items.size(), n_iter, c.d_counter, b->d_err, c.bd, c.grid, s),
+        "persistent launch");
+    BCK(b, cudaEventRecord(b->ev[ci], s), "join record");
+    BCK(b, cudaStreamWaitEvent(origin, b->ev[ci], 0), "join wait");
+  }
+  return FASTFCA_OK;
+}
+
+fastfca_status graph_for(fastfca_batch* b, int n_iter, cudaGraphExec_t* out) {
+  auto it = b->graphs.find(n_iter);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return FASTFCA_OK;
+  }
+  cudaGraph_t g = nullptr;
+  if (!b->capture) BCK(b, cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
+  BCK(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed), "begin capture");
+  fastfca_status st = enqueue_all(b, n_iter, b->capture);
+  cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+  if (st != FASTFCA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  BCK(b, e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  BCK(b, e, "graph instantiate");
+  b->graphs[n_iter] = exec;
+  *out = exec;
+  return FASTFCA_OK;
+}
+
+fastfca_status check_err(fastfca_batch* b) {
+  int bits = 0;
+  BCK(b, cudaMemcpyAsync(&bits, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "status read");
+  BCK(b, cudaStreamSynchronize(b->stream), "batch synchronize");
+  if (!bits) return FASTFCA_OK;
+  BCK(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "status clear");
+  if (bits & ffca::kErrConfig) return bfail(b, FASTFCA_ECUDA, "batch launch configuration rejected (0x%x)", bits);
+  return bfail(b, FASTFCA_ENUMERIC, "numerical failure in a batch kernel (bits 0x%x)", bits);
+}
+
+}  // namespace
+
+extern "C" {
+
+fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const void* const* xs, void* stream,
+                                    fastfca_batch** out) {
+  if (!out) return bfail(nullptr, FASTFCA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (B < 1 || !cfgs || !xs) return bfail(nullptr, FASTFCA_EINVAL, "B >= 1, cfgs and xs are required");
+  fastfca_batch* b = new (std::nothrow) fastfca_batch();
+  if (!b) return bfail(nullptr, FASTFCA_ENOMEM, "host allocation failed");
+  b->stream = (cudaStream_t)stream;
+  auto bail = [&](fastfca_status st) {
+    ffca::set_thread_error(b->msg);
+    free_batch(b);
+    delete b;
+    return st;
+  };
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t n_items = 0;
+  b->mix.resize(B);
+  for (int i = 0; i < B; ++i) {
+    const fastfca_config c = cfgs[i];
+    Mix& m = b->mix[i];
+    m.cfg = c;
+    if (c.F < 1 || c.T < 1 || c.model != FASTFCA_MODEL_FASTFCA || !xs[i]) {
+      bfail(b, FASTFCA_EINVAL, "mixture %d: bad config or NULL x", i);
+      return bail(FASTFCA_EINVAL);
+    }
+    if (!ffca::fast_ops(c.M, c.N, &m.ops) || c.T > m.ops.max_T) {
+      bfail(b, FASTFCA_EUNSUPPORTED, "mixture %d: no kernel for M=%d N=%d T=%d", i, c.M, c.N, c.T);
+      return bail(FASTFCA_EUNSUPPORTED);
+    }
+    m.item0 = n_items;
+    n_items += c.F;
+  }
+  fastfca_status st;
+#define BCKC(expr, what)                                  \
+  do {                                                    \
+    cudaError_t e__ = (expr);                             \
+    if (e__ != cudaSuccess) {                             \
+      cudaGetLastError();                                 \
+      bfail(b, FASTFCA_ECUDA, "%s: %s", what, cudaGetErrorString(e__)); \
+      return bail(e__ == cudaErrorMemoryAllocation ? FASTFCA_ENOMEM : FASTFCA_ECUDA); \
+    }                                                     \
+  } while (0)
+  BCKC(cudaMalloc(&b->d_stamps, sizeof(unsigned long long) * 2 * n_items), "stamps alloc");
+  BCKC(cudaMemsetAsync(b->d_stamps, 0, sizeof(unsigned long long) * 2 * n_items, b->stream), "stamps clear");
+  BCKC(cudaMalloc(&b->d_err, sizeof(int)), "status alloc");
+  BCKC(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "status clear");
+  b->items.resize(n_items);
+  for (int i = 0; i < B; ++i) {
+    Mix& m = b->mix[i];
+    const fastfca_config& c = m.cfg;
+    const size_t FT = (size_t)c.F * c.T;
+    if (is_dev(xs[i])) {
+      m.x = static_cast<const float2*>(xs[i]);
+    } else {
+      BCKC(cudaMalloc(&m.x_owned, sizeof(float2) * FT * c.M), "x alloc");
+      BCKC(cudaMemcpyAsync(m.x_owned, xs[i], sizeof(float2) * FT * c.M, cudaMemcpyHostToDevice, b->stream), "x upload");
+      m.x = m.x_owned;
+    }
+    BCKC(cudaMalloc(&m.P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
+    BCKC(cudaMalloc(&m.lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    BCKC(cudaMalloc(&m.v, sizeof(float) * FT * c.N), "v alloc");
+    BCKC(cudaMalloc(&m.Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    BCKC(cudaMalloc(&m.detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    BCKC(cudaMalloc(&m.ll_last, sizeof(double) * (size_t)c.F), "ll alloc");
+    BCKC(cudaMalloc(&m.flags, sizeof(int) * (size_t)c.F), "flag alloc");
+    BCKC(cudaMalloc(&m.winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    BCKC(cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "flag clear");
+    size_t n = FT * c.N;
+    n = std::max(n, (size_t)c.F * c.M * c.M);
+    n = std::max(n, (size_t)c.F * c.M * c.N);
+    batch_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(m.x, m.P, m.lam, m.v, c.F, c.T, c.M, c.N);
+    BCKC(cudaGetLastError(), "init launch");
+    for (int f = 0; f < c.F; ++f) {
+      ffca::EmItem& it = b->items[m.item0 + f];
+      it.x = m.x + (size_t)f * c.T * c.M;
+      it.P = m.P + (size_t)f * c.M * c.M;
+      it.lam = m.lam + (size_t)f * c.M * c.N;
+      it.v = m.v + (size_t)f * c.N * c.T;
+      it.Bst = m.Bst + (size_t)f * c.M * c.M;
+      it.detst = m.detst + 2 * (size_t)f;
+      it.ll_hist = nullptr;
+      it.ll_last = m.ll_last + f;
+      it.clocks = nullptr;
+      it.valid_flag = m.flags + f;
+      it.stamp = b->d_stamps + 2 * (m.item0 + f);
+      it.T = c.T;
+      it.n_iter = 1;
+      it.b_valid = 0;
+    }
+  }
+  BCKC(cudaStreamSynchronize(b->stream), "create synchronize");
+#undef BCKC
+  st = build_classes(b, kFine, 1.0);
+  if (st != FASTFCA_OK) return bail(st);
+  *out = b;
+  return FASTFCA_OK;
+}
+
+void fastfca_batch_destroy(fastfca_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  free_batch(b);
+  delete b;
+}
+
+const char* fastfca_batch_last_error(const fastfca_batch* b) { return b ? b->msg : fastfca_last_error(nullptr); }
+
+fastfca_status fastfca_batch_set_params(fastfca_batch* b, int32_t i, const void* P, const float* lam, const float* v) {
+  if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
+  if (i < 0 || i >= (int)b->mix.size() || !P || !lam || !v) return bfail(b, FASTFCA_EINVAL, "bad mixture index or NULL");
+  Mix& m = b->mix[i];
+  const fastfca_config& c = m.cfg;
+  BCK(b, copy_in(m.P, P, sizeof(double2) * (size_t)c.F * c.M * c.M, b->stream), "P upload");
+  BCK(b, copy_in(m.lam, lam, sizeof(float) * (size_t)c.F * c.M * c.N, b->stream), "lam upload");
+  BCK(b, copy_in(m.v, v, sizeof(float) * (size_t)c.F * c.T * c.N, b->stream), "v upload");
+  BCK(b, cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "flag clear");
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_batch_get_params(fastfca_batch* b, int32_t i, void* P, float* lam, float* v) {
+  if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
+  if (i < 0 || i >= (int)b->mix.size()) return bfail(b, FASTFCA_EINVAL, "bad mixture index");
+  Mix& m = b->mix[i];
+  const fastfca_config& c = m.cfg;
+  if (P) BCK(b, copy_out(P, m.P, sizeof(double2) * (size_t)c.F * c.M * c.M, b->stream), "P download");
+  if (lam) BCK(b, copy_out(lam, m.lam, sizeof(float) * (size_t)c.F * c.M * c.N, b->stream), "lam download");
+  if (v) BCK(b, copy_out(v, m.v, sizeof(float) * (size_t)c.F * c.T * c.N, b->stream), "v download");
+  return check_err(b);
+}
+
+fastfca_status fastfca_batch_iterate(fastfca_batch* b, int32_t n_iter, double* ll_per_mixture,
+                                     double* seconds_per_mixture) {
+  if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
+  if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
+  cudaGraphExec_t exec = nullptr;
+  fastfca_status st = graph_for(b, n_iter, &exec);
+  if (st) return st;
+  BCK(b, cudaGraphLaunch(exec, b->stream), "graph launch");
+  if (!ll_per_mixture && !seconds_per_mixture) return FASTFCA_OK;
+  st = check_err(b);
+  if (st) return st;
+  if (ll_per_mixture) {
+    for (size_t i = 0; i < b->mix.size(); ++i) {
+      const Mix& m = b->mix[i];
+      std::vector<double> ll(m.cfg.F);
+      BCK(b, cudaMemcpy(ll.data(), m.ll_last, sizeof(double) * m.cfg.F, cudaMemcpyDeviceToHost), "ll download");
+      double s = 0.0;
+      for (double x : ll) s += x;
+      ll_per_mixture[i] = s;
+    }
+  }
+  if (seconds_per_mixture) {
+    std::vector<unsigned long long> st2(2 * b->items.size());
+    BCK(b, cudaMemcpy(st2.data(), b->d_stamps, sizeof(unsigned long long) * st2.size(), cudaMemcpyDeviceToHost),
+        "stamp download");
+    for (size_t i = 0; i < b->mix.size(); ++i) {
+      const Mix& m = b->mix[i];
+      unsigned long long lo = ~0ULL, hi = 0;
+      for (int f = 0; f < m.cfg.F; ++f) {
+        lo = std::min(lo, st2[2 * (m.item0 + f)]);
+        hi = std::max(hi, st2[2 * (m.item0 + f) + 1]);
+      }
+      seconds_per_mixture[i] = hi > lo ? (double)(hi - lo) * 1e-9 : 0.0;
+    }
+  }
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* chosen_scheme, double* chosen_factor) {
+  if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
+  if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
+  // snapshot the parameters: the probes iterate on them
+  struct Saved { double2* P; float* lam; float* v; };
+  std::vector<Saved> saved(b->mix.size());
+  for (size_t i = 0; i < b->mix.size(); ++i) {
+    Mix& m = b->mix[i];
+    const fastfca_config& c = m.cfg;
+    BCK(b, cudaMalloc(&saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M), "tune snapshot");
+    BCK(b, cudaMalloc(&saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N), "tune snapshot");
+    BCK(b, cudaMalloc(&saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N), "tune snapshot");
+    BCK(b, cudaMemcpyAsync(saved[i].P, m.P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "snap");
+    BCK(b, cudaMemcpyAsync(saved[i].lam, m.lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "snap");
+    BCK(b, cudaMemcpyAsync(saved[i].v, m.v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "snap");
+  }
+  auto restore = [&]() -> fastfca_status {
+    for (size_t i = 0; i < b->mix.size(); ++i) {
+      Mix& m = b->mix[i];
+      const fastfca_config& c = m.cfg;
+      BCK(b, cudaMemcpyAsync(m.P, saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      BCK(b, cudaMemcpyAsync(m.lam, saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      BCK(b, cudaMemcpyAsync(m.v, saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      BCK(b, cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "restore");
+    }
+    return FASTFCA_OK;
+  };
+  const double factors[] = {1.0, 2.0, 4.0};
+  float best_ms = 1e30f;
+  int best_scheme = kFine;
+  double best_factor = 1.0;
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0), "tune event");
+  BCK(b, cudaEventCreate(&e1), "tune event");
+  fastfca_status st = FASTFCA_OK;
+  for (int scheme = 0; scheme < kNumSchemes && st == FASTFCA_OK; ++scheme) {
+    for (double fac : factors) {
+      st = build_classes(b, scheme, fac);
+      if (st) break;
+      st = restore();
+      if (st) break;
+      cudaEventRecord(e0, b->stream);
+      st = enqueue_all(b, n_iter, b->stream);
+      if (st) break;
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = bfail(b, FASTFCA_ECUDA, "tune probe failed"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best_scheme = scheme; best_factor = fac; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == FASTFCA_OK) st = restore();
+  for (auto& s : saved) { cudaFree(s.P); cudaFree(s.lam); cudaFree(s.v); }
+  if (st) return st;
+  st = build_classes(b, best_scheme, best_factor);
+  if (st) return st;
+  if (chosen_scheme) *chosen_scheme = best_scheme;
+  if (chosen_factor) *chosen_factor = best_factor;
+  return check_err(b);
+}
+
+fastfca_status fastfca_batch_schedule(fastfca_batch* b, int32_t scheme, double grid_factor) {
+  if (!b) return FASTFCA_EINVAL;
+  if (scheme < 0 || scheme >= kNumSchemes || !(grid_factor > 0.0)) return bfail(b, FASTFCA_EINVAL, "bad schedule");
+  return build_classes(b, scheme, grid_factor);
+}
+
+fastfca_status fastfca_batch_separate(fastfca_batch* b, int32_t i, void* c) {
+  if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
+  if (i < 0 || i >= (int)b->mix.size() || !c) return bfail(b, FASTFCA_EINVAL, "bad mixture index or NULL c");
+  Mix& m = b->mix[i];
+  const fastfca_config& cf = m.cfg;
+  if (!is_dev(c)) return bfail(b, FASTFCA_EINVAL, "c must be a device pointer");
+  BCK(b, m.ops.winv(m.P, m.winv, cf.F, b->d_err, b->stream), "winv launch");
+  BCK(b, m.ops.mwf(m.x, m.P, m.winv, m.lam, m.v, static_cast<float2*>(c), cf.F, cf.T, b->stream), "filter launch");
+  return FASTFCA_OK;
+}
+
+}  // extern "C"

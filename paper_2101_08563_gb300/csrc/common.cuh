@@ -30,24 +30,33 @@ __device__ __forceinline__ float fast_rsqrt(float x) {
   return r;
 }
 
-// FP64 reciprocal of a positive real.  FP64 has a ~70-cycle dependent latency on this part,
-// so the seed comes from the FP32 reciprocal and one Newton-Raphson step r <- r (2 - d r)
-// squares its relative error (about 2^-22 -> 2^-44), far below the FP32 error of the sums
-// the IP works on.  Outside the FP32 normal range the seed is unusable: IEEE division then.
+// FP64 reciprocal and reciprocal square root of a positive normal number.  FP64 has a
+// ~70-cycle dependent latency on this part, so the seed comes from the FP32 approximation
+// and one Newton-Raphson step squares its relative error (about 2^-22 -> 2^-44), far below
+// the FP32 error of the sums the IP works on.  The argument is first scaled by a power of two
+// into [1, 2) (reciprocal) or [1, 4) (reciprocal square root) with integer operations on its
+// exponent field, so the FP32 seed is always in range and no slow path exists; the result
+// is scaled back the same way.  Callers pass positive normal values only.
+constexpr long long kExpUnit = 1LL << 52;                          // one step of the exponent field
+
 __device__ __forceinline__ double rcp_pos_f64(double d) {
-  const float df = (float)d;
-  if (!(df > 1e-36f && df < 1e36f)) return 1.0 / d;
-  const double r = (double)fast_rcp(df);
-  return fma(r, fma(-d, r, 1.0), r);
+  const long long b = __double_as_longlong(d);
+  const long long e = ((b >> 52) & 0x7ff) - 1023;                 // d = m * 2^e, m in [1, 2)
+  const long long shift = e * kExpUnit;
+  const double m = __longlong_as_double(b - shift);
+  const double r0 = (double)fast_rcp((float)m);
+  const double r1 = fma(r0, fma(-m, r0, 1.0), r0);                 // 1/m in (0.5, 1]
+  return __longlong_as_double(__double_as_longlong(r1) - shift);
 }
 
-// FP64 1/sqrt(s) for s > 0: FP32 seed, then one Newton step y <- y (1 + (1 - s y^2)/2)
-// (relative error about 2^-43).
 __device__ __forceinline__ double rsqrt_pos_f64(double s) {
-  const float sf = (float)s;
-  if (!(sf > 1e-36f && sf < 1e36f)) return 1.0 / sqrt(s);
-  const double y = (double)fast_rsqrt(sf);
-  return fma(0.5 * y, fma(-s * y, y, 1.0), y);
+  const long long b = __double_as_longlong(s);
+  const long long e = ((b >> 52) & 0x7ff) - 1023;
+  const long long k = e >> 1;                                      // s = m * 4^k, m in [1, 4)
+  const double m = __longlong_as_double(b - 2 * k * kExpUnit);
+  const double y0 = (double)fast_rsqrt((float)m);
+  const double y1 = fma(0.5 * y0, fma(-m * y0, y0, 1.0), y0);      // 1/sqrt(m) in (0.5, 1]
+  return __longlong_as_double(__double_as_longlong(y1) - k * kExpUnit);
 }
 
 // ---------------------------------------------------------------------- complex helpers

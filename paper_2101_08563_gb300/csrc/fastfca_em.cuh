@@ -61,7 +61,7 @@ struct EmArgs {
 #ifdef FFCA_PHASE_CLOCKS
 #define FFCA_MARK(it, slot)                                                       \
   do {                                                                            \
-    if (p.clocks && f == 0 && tid == 0 && (it) < 8) p.clocks[(it) * 16 + (slot)] = clock64(); \
+    if (q.clocks && tid == 0 && (it) < 8) q.clocks[(it) * 16 + (slot)] = clock64(); \
   } while (0)
 #else
 #define FFCA_MARK(it, slot) \
@@ -99,12 +99,15 @@ struct EmSmem {
   // sQ holds the M matrices Q_m; once per launch it is also the scratch of the pivoted
   // inverse of W^H (M*M source + M*2M augmented work).
   static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
+  // sWc holds M*M float2; rounded up to an even count so that sL (read as float4) starts on a
+  // 16-byte boundary for every M.
+  static constexpr int kWcPad = (M * M + 1) & ~1;
   static size_t bytes(int threads) {
     size_t b = 0;
     b += sizeof(double2) * M * M * 3;        // sW, sB, sWork
     b += sizeof(double2) * kQsz;             // sQ
     b += sizeof(double) * 4;                 // sDet (mantissa, exponent), spare
-    b += sizeof(float2) * M * M;             // sWc
+    b += sizeof(float2) * kWcPad;            // sWc (padded to 16 bytes)
     b += sizeof(float) * ((M * N + 3) & ~3); // sL
     b += sizeof(float) * 2 * kMaxWarps * kRedW;
     b += sizeof(float) * kMaxWarps;          // sLL
@@ -323,33 +326,44 @@ __device__ __forceinline__ void cta_rows_sum(const float* red, int nw, int lane,
   for (int i = 0; i < M; ++i) tot[i] = __shfl_sync(0xffffffffu, v, i);
 }
 
+// One frequency of one mixture: everything em_frequency needs, as per-frequency pointers.
+struct EmItem {
+  const float2* x;      // T x M
+  double2* P;           // M x M (W[a][m] at a*M + m)
+  float* lam;           // M x N
+  float* v;             // N rows of T frames
+  double2* Bst;         // M x M, W^{-H} carried between launches
+  double* detst;        // 2: |det W|^2 as (mantissa, exponent)
+  double* ll_hist;      // n_iter entries or null
+  double* ll_last;      // 1 entry or null
+  long long* clocks;    // phase timestamps (profiling builds) or null
+  int* valid_flag;      // if set: 1 when Bst/detst are current (read at start, set at end)
+  unsigned long long* stamp;   // if set: start and end %globaltimer of this item
+  int T, n_iter, b_valid;
+};
+
+// The whole IP+EM run of one frequency by one CTA (see the file comment).  `smem_raw` is the
+// CTA's dynamic shared memory (EmSmem<M, N>::bytes(blockDim.x)); T <= blockDim.x * kSlots.
 template <int M, int N>
-__global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
+__device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned char* smem_raw) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
   constexpr int MP = pow2_ceil(M);
   constexpr int NE = M * M;                   // packed Hermitian entries per Q_m
   static_assert(MP * (kMaxWarps) <= 32, "n-step reduction rows must fit one warp");
 
-  const int f = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bd = blockDim.x, nw = bd >> 5;
-  const int T = p.T;
+  const int T = q.T;
   const int Tp = bd * kSlots;
-  if (f >= p.F) return;
-  if (Tp < T || nw > kMaxWarps) {             // uniform over the CTA
-    if (tid == 0) atomicOr(p.err, kErrConfig);
-    return;
-  }
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* sW = reinterpret_cast<double2*>(smem_raw);
   double2* sB = sW + M * M;
   double2* sWork = sB + M * M;
   double2* sQ = sWork + M * M;
   double* sDet = reinterpret_cast<double*>(sQ + SM::kQsz);
   float2* sWc = reinterpret_cast<float2*>(sDet + 4);
-  float* sL = reinterpret_cast<float*>(sWc + M * M);
+  float* sL = reinterpret_cast<float*>(sWc + SM::kWcPad);
   float* sRed = sL + ((M * N + 3) & ~3);
   float* sLL = sRed + 2 * kMaxWarps * SM::kRedW;
   float* sH = sLL + kMaxWarps;
@@ -361,15 +375,15 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   float* pH = sH + tid * SH;
   float* pU = sU + tid * SU;
 
-  const float2* xf = p.x + (size_t)f * T * M;
+  const float2* xf = q.x;
   const double invT = 1.0 / (double)T;
   const float invTf = 1.0f / (float)T;
 
   // ---- load the parameters of frequency f
-  for (int i = tid; i < M * N; i += bd) sL[i] = p.lam[(size_t)f * M * N + i];
-  for (int i = tid; i < M * M; i += bd) sW[i] = p.P[(size_t)f * M * M + i];
+  for (int i = tid; i < M * N; i += bd) sL[i] = q.lam[i];
+  for (int i = tid; i < M * M; i += bd) sW[i] = q.P[i];
   for (int n = 0; n < N; ++n) {
-    const float* vf = p.v + ((size_t)f * N + n) * T;
+    const float* vf = q.v + (size_t)n * T;
     for (int t = tid; t < Tp; t += bd) {
       const int owner = t % bd, k = t / bd;
       sH[owner * SH + k * N + n] = (t < T) ? vf[t] : 1.0f;
@@ -378,10 +392,11 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   __syncthreads();
   // ---- B = W^{-H}, |det W|^2: carried over from the previous launch when valid, else
   // formed once by pivoted Gauss-Jordan on W^H (warp 0)
+  const int b_valid = q.valid_flag ? *reinterpret_cast<volatile int*>(q.valid_flag) : q.b_valid;
   if (warp == 0) {
-    if (p.b_valid) {
-      for (int e = lane; e < M * M; e += 32) sB[e] = p.Bst[(size_t)f * M * M + e];
-      if (lane == 0) { sDet[0] = p.detst[2 * f]; sDet[1] = p.detst[2 * f + 1]; }
+    if (b_valid) {
+      for (int e = lane; e < M * M; e += 32) sB[e] = q.Bst[e];
+      if (lane == 0) { sDet[0] = q.detst[0]; sDet[1] = q.detst[1]; }
     } else {
       for (int e = lane; e < M * M; e += 32) {
         const int i = e / M, j = e - (e / M) * M;
@@ -390,7 +405,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
       }
       __syncwarp();
       double mant, expo;
-      warp_inverse_pivot<M>(sQ, sQ + M * M, sB, mant, expo, lane, p.err);
+      warp_inverse_pivot<M>(sQ, sQ + M * M, sB, mant, expo, lane, err);
       if (lane == 0) { sDet[0] = mant; sDet[1] = expo; }
     }
     for (int e = lane; e < M * M; e += 32) {
@@ -406,10 +421,20 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   // (identical values), so each thread's later reads see the new column through its own
   // store, without another barrier.
   auto load_L = [&](float (&Lr)[M][N]) {
+    constexpr int Q4 = (M * N) / 4;
+    float tmp[M * N];
+    const float4* s4 = reinterpret_cast<const float4*>(sL);
+#pragma unroll
+    for (int i = 0; i < Q4; ++i) {
+      const float4 v4 = s4[i];
+      tmp[4 * i] = v4.x; tmp[4 * i + 1] = v4.y; tmp[4 * i + 2] = v4.z; tmp[4 * i + 3] = v4.w;
+    }
+#pragma unroll
+    for (int i = 4 * Q4; i < M * N; ++i) tmp[i] = sL[i];
 #pragma unroll
     for (int m = 0; m < M; ++m)
 #pragma unroll
-      for (int n = 0; n < N; ++n) Lr[m][n] = sL[m * N + n];
+      for (int n = 0; n < N; ++n) Lr[m][n] = tmp[m * N + n];
   };
 
   // per-slot registers: r[k][m] holds 1/sigma^2 during the Q pass and r_{mt} in the sweep
@@ -462,15 +487,15 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
 #pragma unroll
   for (int m = 0; m < M; ++m) coef[m] = 0.f;
 
-  if (p.n_iter == 0) pass_U();
+  if (q.n_iter == 0) pass_U();
 
   // The loop body is written once (n and the Q chunks are runtime loops) so that the
   // kernel's code stays small enough for the instruction cache; register arrays are indexed
   // with compile-time indices only, through selects.
 #pragma unroll 1
   for (int it = 0;; ++it) {
-    const bool have_ll = (it > 0) || (p.n_iter == 0);
-    const bool do_iter = it < p.n_iter;
+    const bool have_ll = (it > 0) || (q.n_iter == 0);
+    const bool do_iter = it < q.n_iter;
     FFCA_MARK(it, 0);
 
     // ---- pass A: the pending H[N-1,:] update of the last sweep (it > 0), then
@@ -505,7 +530,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
           }
         }
       }
-      if (bad) atomicOr(p.err, kErrSigma);
+      if (bad) atomicOr(err, kErrSigma);
       if (have_ll) {
         llp = warp_sum(llp);
         if (lane == 0) sLL[warp] = llp;
@@ -517,8 +542,8 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += (double)sLL[w];
         const double ll = ll_from_sum(s);
-        if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
-        if (p.ll_last) p.ll_last[f] = ll;
+        if (it > 0 && q.ll_hist) q.ll_hist[it - 1] = ll;
+        if (q.ll_last) q.ll_last[0] = ll;
       }
       break;
     }
@@ -582,18 +607,20 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
       if (c == 0 && have_ll && tid == 32 % bd) {
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += (double)sLL[w];
-        if (p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(s);
+        if (q.ll_hist) q.ll_hist[it - 1] = ll_from_sum(s);
       }
       par ^= 1;
     }
     __syncthreads();
     FFCA_MARK(it, 1);
 
-    // ---- IP (FP64): Q_m^{-1} for all m, then the column loop (warp 0)
-    if (warp == 0) warp_hpd_inverse_all<M>(sQ, lane, p.err);
+    // ---- IP (FP64): Q_m^{-1} for all m packed on warp 0's lanes, then the column loop.
+    // (One matrix per warp shortens the chain but issues ~2.5x the FP64 warp instructions,
+    // which the other CTAs on the SM then wait for: measured slower.)
+    if (warp == 0) warp_hpd_inverse_all<M>(sQ, lane, err);
     __syncwarp();
     FFCA_MARK(it, 2);
-    if (warp == 0) ip_columns<M>(sQ, sW, sB, sWc, sDet, lane, p.err);
+    if (warp == 0) ip_columns<M>(sQ, sW, sB, sWc, sDet, lane, err);
     __syncthreads();
     FFCA_MARK(it, 3);
 
@@ -663,15 +690,85 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
 
   // ---- write back
   __syncthreads();
-  for (int i = tid; i < M * N; i += bd) p.lam[(size_t)f * M * N + i] = sL[i];
+  for (int i = tid; i < M * N; i += bd) q.lam[i] = sL[i];
   for (int i = tid; i < M * M; i += bd) {
-    p.P[(size_t)f * M * M + i] = sW[i];
-    p.Bst[(size_t)f * M * M + i] = sB[i];
+    q.P[i] = sW[i];
+    q.Bst[i] = sB[i];
   }
-  if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
+  if (tid == 0) {
+    q.detst[0] = sDet[0];
+    q.detst[1] = sDet[1];
+    if (q.valid_flag) *q.valid_flag = 1;
+  }
   for (int n = 0; n < N; ++n) {
-    float* vf = p.v + ((size_t)f * N + n) * T;
+    float* vf = q.v + (size_t)n * T;
     for (int t = tid; t < T; t += bd) vf[t] = sH[(t % bd) * SH + (t / bd) * N + n];
+  }
+}
+
+
+template <int M, int N>
+__global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
+  const int f = blockIdx.x;
+  if (f >= p.F) return;
+  if (blockDim.x * kSlots < (unsigned)p.T || blockDim.x > (unsigned)kMaxThreads) {   // uniform
+    if (threadIdx.x == 0) atomicOr(p.err, kErrConfig);
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EmItem q;
+  q.x = p.x + (size_t)f * p.T * M;
+  q.P = p.P + (size_t)f * M * M;
+  q.lam = p.lam + (size_t)f * M * N;
+  q.v = p.v + (size_t)f * N * p.T;
+  q.Bst = p.Bst + (size_t)f * M * M;
+  q.detst = p.detst + 2 * (size_t)f;
+  q.ll_hist = p.ll_hist ? p.ll_hist + (size_t)f * p.ll_stride : nullptr;
+  q.ll_last = p.ll_last ? p.ll_last + f : nullptr;
+  q.clocks = (p.clocks && f == 0) ? p.clocks : nullptr;
+  q.valid_flag = nullptr;
+  q.stamp = nullptr;
+  q.T = p.T;
+  q.n_iter = p.n_iter;
+  q.b_valid = p.b_valid;
+  em_frequency<M, N>(q, p.err, smem_raw);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Persistent form for batches of mixtures: each CTA takes items (one frequency of one mixture
+// each, all of this kernel's (M, N)) from an atomic counter, in the order they are listed
+// (the host lists them longest-first), until the list is exhausted.  blockDim.x * kSlots must
+// cover every item's T.  No CTA waits on another.
+template <int M, int N>
+__global__ void __maxnreg__(kEmMaxRegs) fastfca_em_persistent_kernel(const EmItem* __restrict__ items,
+                                                                    int n_items, int n_iter,
+                                                                    int* counter, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_next;
+  for (;;) {
+    __syncthreads();                               // previous item's smem reads are done
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = s_next;
+    if (i >= n_items) return;
+    EmItem q = items[i];
+    q.n_iter = n_iter;
+    if (blockDim.x * kSlots < (unsigned)q.T) {    // uniform over the CTA
+      if (threadIdx.x == 0) atomicOr(err, kErrConfig);
+      continue;
+    }
+    const unsigned long long t0 = global_ns();
+    em_frequency<M, N>(q, err, smem_raw);
+    __syncthreads();
+    if (threadIdx.x == 0 && q.stamp) {
+      q.stamp[0] = t0;
+      q.stamp[1] = global_ns();
+    }
   }
 }
 

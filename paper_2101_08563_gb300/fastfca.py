@@ -42,6 +42,15 @@ _SIGNATURES = {
     "fastfca_version": (ctypes.c_char_p, []),
     "fastfca_separate_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 _P, _P, _P, _P, _P, _P]),
+    "fastfca_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]),
+    "fastfca_batch_set_params": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "fastfca_batch_get_params": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "fastfca_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "fastfca_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "fastfca_batch_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double]),
+    "fastfca_batch_separate": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "fastfca_batch_last_error": (ctypes.c_char_p, [_P]),
+    "fastfca_batch_destroy": (None, [_P]),
 }
 
 
@@ -236,3 +245,94 @@ def abi_symbols_from_header(path: str | None = None):
     txt = open(path).read()
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(fastfca_[a-z0-9_]+)\s*\(",
                                  txt, flags=re.M)))
+
+
+class Batch:
+    """Many independent FastFCA mixtures iterated together in one CUDA-graph launch.
+
+    xs: list of complex64 (F_b, T_b, M_b) arrays (host or CUDA); Ns: sources per mixture.
+    """
+
+    SCHEMES = {0: "fine", 1: "coarse", 2: "single"}
+
+    def __init__(self, xs, Ns, stream=None):
+        self.lib = load()
+        if len(xs) != len(Ns) or not xs:
+            raise ValueError("xs and Ns must be non-empty and of equal length")
+        self.B = len(xs)
+        self.shapes = []
+        cfgs = (Config * self.B)()
+        ptrs = (ctypes.c_void_p * self.B)()
+        self._xs = []
+        for i, (x, N) in enumerate(zip(xs, Ns)):
+            F, T, M = (int(s) for s in x.shape)
+            self.shapes.append((F, T, M, int(N)))
+            cfgs[i] = Config(F, T, M, int(N), MODEL_FASTFCA, 0)
+            p, keep = _ptr(x, np.complex64, (F, T, M), f"xs[{i}]")
+            ptrs[i] = p.value
+            self._xs.append(keep)
+        self.stream = _default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        st = self.lib.fastfca_batch_create(self.B, cfgs, ptrs, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        if st != 0:
+            raise FastFCAError(st, self.lib.fastfca_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise FastFCAError(st, self.lib.fastfca_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fastfca_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, b, P, lam, v):
+        F, T, M, N = self.shapes[b]
+        pP, kP = _ptr(P, np.complex128, (F, M, M), "P")
+        pl, kl = _ptr(lam, np.float32, (F, M, N), "lam")
+        pv, kv = _ptr(v, np.float32, (F, N, T), "v")
+        self._check(self.lib.fastfca_batch_set_params(self._h, b, pP, pl, pv))
+
+    def get_params(self, b):
+        F, T, M, N = self.shapes[b]
+        P = np.empty((F, M, M), np.complex128)
+        lam = np.empty((F, M, N), np.float32)
+        v = np.empty((F, N, T), np.float32)
+        self._check(self.lib.fastfca_batch_get_params(self._h, b, _ptr(P, np.complex128, P.shape, "P", True)[0],
+                                                      _ptr(lam, np.float32, lam.shape, "lam", True)[0],
+                                                      _ptr(v, np.float32, v.shape, "v", True)[0]))
+        return P, lam, v
+
+    def iterate(self, n_iter, stats=True):
+        """Returns (log-likelihood per mixture, seconds per mixture) when stats, else None."""
+        if not stats:
+            self._check(self.lib.fastfca_batch_iterate(self._h, int(n_iter), None, None))
+            return None
+        ll = np.empty(self.B, np.float64)
+        sec = np.empty(self.B, np.float64)
+        self._check(self.lib.fastfca_batch_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p),
+                                                   sec.ctypes.data_as(ctypes.c_void_p)))
+        return ll, sec
+
+    def tune(self, n_iter):
+        scheme = ctypes.c_int32()
+        factor = ctypes.c_double()
+        self._check(self.lib.fastfca_batch_tune(self._h, int(n_iter), ctypes.byref(scheme), ctypes.byref(factor)))
+        return self.SCHEMES[scheme.value], factor.value
+
+    def schedule(self, scheme, factor=1.0):
+        code = {v: k for k, v in self.SCHEMES.items()}[scheme] if isinstance(scheme, str) else int(scheme)
+        self._check(self.lib.fastfca_batch_schedule(self._h, code, ctypes.c_double(factor)))
+
+    def separate(self, b, out):
+        F, T, M, N = self.shapes[b]
+        p, keep = _ptr(out, np.complex64, (F, T, N, M), "c", True)
+        self._check(self.lib.fastfca_batch_separate(self._h, b, p))
+        return out
