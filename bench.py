@@ -172,6 +172,77 @@ def cpu_baseline():
             "sample": sample, "seconds": round(wall, 3)}
 
 
+# ----------------------------------------------------------------------------- batch workload
+BATCH_B, BATCH_F, BATCH_ITERS, BATCH_SEED = 64, 513, 20, 3000
+
+
+def batch_shapes():
+    """The mixed-shape batch: M in {2,3,4}, N in M+1..M+3, T uniform in [200, 2000]."""
+    rng = np.random.Generator(np.random.PCG64(BATCH_SEED))
+    out = []
+    for b in range(BATCH_B):
+        M = int(rng.integers(2, 5))
+        N = int(rng.integers(M + 1, M + 4))
+        T = int(rng.integers(200, 2001))
+        out.append((M, N, T))
+    return out
+
+
+def _gen_batch_item(args):
+    b, M, N, T = args
+    mix = synth.generate_mixture(M, N, BATCH_F, T, 8, seed=BATCH_SEED + b)
+    init = synth.random_init(mix.x, N, seed=BATCH_SEED + b)
+    return mix.x, init.P, init.lam, init.v
+
+
+def generate_batch():
+    import multiprocessing as mp
+    shapes = batch_shapes()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        data = pool.map(_gen_batch_item, [(b, M, N, T) for b, (M, N, T) in enumerate(shapes)])
+    return shapes, data
+
+
+def run_batch(shapes, data, dev, stream, clocks_ok=True):
+    import torch
+    from paper_2101_08563_gb300 import fastfca
+    xs = [torch.from_numpy(d[0]).to(dev) for d in data]
+    inits = [(torch.from_numpy(d[1]).to(dev), torch.from_numpy(d[2]).to(dev), torch.from_numpy(d[3]).to(dev))
+             for d in data]
+    bt = fastfca.Batch(xs, [N for _, N, _ in shapes], stream=stream.cuda_stream)
+
+    def reset():
+        for b, (P, lam, v) in enumerate(inits):
+            bt.set_params(b, P, lam, v)
+
+    reset()
+    scheme, factor = bt.tune(3)
+    for _ in range(3):
+        reset()
+        bt.iterate(BATCH_ITERS, stats=False)
+    torch.cuda.synchronize()
+    units = sum(BATCH_F * T for _, _, T in shapes) * BATCH_ITERS
+    times, secs = [], []
+    for _ in range(5):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.iterate(BATCH_ITERS, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        _, sec = bt.iterate(BATCH_ITERS, stats=True)     # per-mixture spans (stamps)
+        secs.append(sec)
+    bt.close()
+    sec = np.median(np.array(secs), axis=0)
+    ms = float(np.median(times))
+    return {"value": units / (ms * 1e-3), "unit": UNIT, "mixtures": BATCH_B, "iters": BATCH_ITERS,
+            "ms_per_launch": ms, "per_mixture_ms_p50": float(np.percentile(sec, 50) * 1e3),
+            "per_mixture_ms_p99": float(np.percentile(sec, 99) * 1e3),
+            "schedule": {"bucketing": scheme, "grid_factor": factor},
+            "config": "M in {2,3,4}, N in M+1..M+3, F=513, T uniform [200,2000], one CUDA-graph launch"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def load_peaks():
     try:
@@ -315,6 +386,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -367,8 +439,15 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()                   # spawned workers, before any CUDA work
+    batch_data = None
+    if rank == 0 and not args.no_batch:
+        batch_data = generate_batch()          # spawned workers, before any CUDA work
 
     r = run_gpu(args, rank, world, local_rank)
+    batch = None
+    if batch_data is not None:
+        import torch
+        batch = run_batch(*batch_data, torch.device("cuda", local_rank), torch.cuda.current_stream())
     if rank != 0:
         return
     peaks = load_peaks()
@@ -401,6 +480,8 @@ def main():
         "final_loglik": r["final_ll"],
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
+    if batch is not None:
+        out["batch"] = batch
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out))
