@@ -363,6 +363,42 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
+def run_profile_case(F, iters):
+    """The bench workload's first 8 frequencies tiled to F (so the launch has F CTAs of the
+    bench's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`."""
+    import torch
+    from paper_2101_08563_gb300 import build, fastfca
+    w = WORKLOAD
+    mix = synth.generate_mixture(w.M, w.N, 8, w.T, w.K, seed=w.seed)
+    x = np.tile(mix.x, (F // 8 + 1, 1, 1))[:F].copy()
+    init = synth.random_init(x, w.N, seed=w.seed)
+    build.build()
+    sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N)
+    sep.set_params(init.P, init.lam, init.v)
+    sep.iterate(2, return_ll=False)
+    sep.set_params(init.P, init.lam, init.v)
+    sep.iterate(iters, return_ll=False)
+    torch.cuda.synchronize()
+    sep.close()
+    print("profile case done")
+
+
+def em_traffic():
+    """DRAM bytes per bench launch of the IP+EM kernel from the committed ncu capture, or None
+    when the kernel source changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(prof))["fastfca_em_kernel"]
+        csrc = os.path.join(ROOT, "paper_2101_08563_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("fastfca_em.cuh", "common.cuh"))
+        if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -387,6 +423,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run the IP+EM kernel on the bench mixture's first frequencies tiled to "
+                         "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
+    ap.add_argument("--profile-F", type=int, default=608)
+    ap.add_argument("--profile-iters", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -399,6 +440,10 @@ def main():
               "K_nmf": w.K, "array": f"{w.array} {w.spacing * 100:.0f} cm",
               "step": "IP+EM x iters + Wiener separation, from the seeded init",
               "l2": "flushed between steps (512 MiB write, untimed)"}
+
+    if args.profile:
+        run_profile_case(args.profile_F, args.profile_iters)
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -454,13 +499,7 @@ def main():
     flops = algorithmic_flops_per_bin_iter(w.M, w.N) * w.F * w.T * w.iters
     em_avg_s = statistics.mean(r["em_ms"]) * 1e-3
     achieved = flops / em_avg_s / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("fastfca_em_kernel_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = em_traffic()
     out = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
