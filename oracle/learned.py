@@ -17,7 +17,8 @@ network: h1 = gelu(W1 phi + b1), h2 = gelu(W2 h1 + b2), o = W3 h2 + b3 (hidden 2
 per-frame powers: ln v_nt = c_n + b_n + sum_j k_nj q_{t+j-(K-1)/2}, q_t = p_t - mean_t p,
   zero outside [0, T) (a 1-D convolution over t with N output channels, shared weights k, c).
 loss of one frequency against a target (W*, L*, H*) from converged FastFCA:
-  w-hat = columns scaled to unit norm; l[m,n] = ln L - mean_m ln L (per n);
+  w-hat = columns scaled to unit norm, with row m of L divided by ||w_m||^2 so that the
+  covariances of the model are unchanged; l[m,n] = ln L - mean_m ln L (per n);
   h[n,t] = ln v + mean_m ln L[:, n]  (the scale shared by L[:, n] and H[n, :] removed);
   sigma = the channel permutation minimising sum_m (1 - |w-hat[:, sigma(m)]^H w-hat*[:, m]|^2);
   pi = the source permutation minimising sum_{m,n} (l[sigma(m), pi(n)] - l*[m, n])^2
@@ -117,9 +118,14 @@ def _w_unit(o, M):
 
 
 def canon_target(W, L, H):
-    """Scale-free target (w-hat*, l*, h*) from a converged (W, L, H) of one frequency."""
-    Wn = W / np.linalg.norm(W, axis=0, keepdims=True)
-    lnL = np.log(L)
+    """Scale-free target (w-hat*, l*, h*) from a converged (W, L, H) of one frequency.
+
+    Scaling column m of W by d scales the variance of w_m^H x by |d|^2, so with unit columns
+    row m of L is divided by ||w_m||^2: (w-hat, L', H) give the same covariances as (W, L, H).
+    """
+    norms = np.linalg.norm(W, axis=0)
+    Wn = W / norms[None, :]
+    lnL = np.log(L) - 2.0 * np.log(norms)[:, None]
     mean = lnL.mean(axis=0)
     return Wn, lnL - mean[None, :], np.log(H) + mean[:, None]
 

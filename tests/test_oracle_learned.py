@@ -68,3 +68,27 @@ def test_batch_gradients_by_finite_differences():
             flat[idx] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - g[name].reshape(-1)[idx]) <= 1e-5 + 1e-4 * abs(fd), (name, idx, fd, g[name].reshape(-1)[idx])
+
+
+def test_canonical_target_keeps_the_model_covariances(rng):
+    # W^{-H} diag(L h_t) W^{-1} must be the same for (W, L, H) and the scale-free target
+    M, N, T = 3, 4, 7
+    W = rand_complex(rng, M, M) + 2 * np.eye(M)
+    L = rng.uniform(0.2, 3.0, (M, N))
+    H = rng.uniform(0.2, 3.0, (N, T))
+    Wn, lt, ht = ol.canon_target(W, L, H)
+    assert np.allclose(np.linalg.norm(Wn, axis=0), 1.0)
+    assert np.allclose(lt.mean(axis=0), 0.0)
+
+    def covs(W_, L_, H_):
+        Wi = np.linalg.inv(W_)
+        return [Wi.conj().T @ np.diag(L_ @ H_[:, t]) @ Wi for t in range(T)]
+
+    for a, b in zip(covs(W, L, H), covs(Wn, np.exp(lt), np.exp(ht))):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+    # a column rescaling of W or a per-source rescaling of (L, H) leaves the target unchanged
+    d = rng.uniform(0.5, 2.0, M) * np.exp(1j * rng.uniform(0, 6.28, M))
+    s = rng.uniform(0.5, 2.0, N)
+    Wn2, lt2, ht2 = ol.canon_target(W * d[None, :], L * np.abs(d)[:, None] ** 2 * s[None, :], H / s[:, None])
+    assert np.allclose(np.abs(np.sum(Wn2.conj() * Wn, axis=0)), 1.0)
+    assert np.allclose(lt2, lt) and np.allclose(ht2, ht)
