@@ -74,15 +74,17 @@ typedef struct {
   int32_t M;      /* microphones: 2, 3 or 4 in this build */
   int32_t N;      /* sources: 2..8 in this build */
   int32_t model;  /* fastfca_model */
-  int32_t reserved;
+  int32_t seed;   /* seed of the default initial v (Philox4x32-10); any value */
 } fastfca_config;
 
 typedef struct fastfca_ctx fastfca_ctx;
 
 /* Creates a context for the mixture x (complex64 [F][T][M], host or device) on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The parameters start at W = I,
- * lambda = 1 and v = ||x_t||^2 / (M N) (FCA: R_n = I, h = the same v); callers normally
- * overwrite them with fastfca_set_params.  Sec. II defines the problem: estimate the source
+ * lambda = 1 and v[n][t] = ||x_t||^2 / (M N) * u, u ~ U[0.5, 1.5) drawn from Philox4x32-10
+ * keyed by cfg->seed with counter (f, n, t, 0x1d17) (FCA: R_n = I, h = the same v).  The random
+ * factor breaks the symmetry between sources that equal starting values would keep forever.
+ * Callers may overwrite the start with fastfca_set_params.  Sec. II defines the problem: estimate the source
  * images c given x and N.  Returns EINVAL for sizes out of range, EUNSUPPORTED for an (M, N)
  * without a kernel, ENOMEM/ECUDA on allocation or copy failure; *out is NULL then. */
 fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream,
@@ -211,6 +213,93 @@ void fastfca_batch_destroy(fastfca_batch* batch);
 fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t N, const void* x,
                                         const void* P, const float* lam, const float* v, void* c,
                                         void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned initialiser (not in the paper: its initialisation is mask-based, Sec. VII, and it
+ * leaves the choice of a better starting point open).  A small network maps statistics of
+ * each frequency of a mixture to a starting point (W, L, H) of Algorithm 1:
+ *
+ *   features phi (16 floats per frequency): the upper triangle of R / tr R, R = (1/T) sum_t
+ *     x_t x_t^H (the M diagonal reals, then (re, im) of each a < b pair), ln(tr R / M), the mean
+ *     and standard deviation over t of p_t = ln(||x_t||^2 / M), f / (F - 1), 1, zeros to 16;
+ *     q_t = p_t - mean_t p (T floats per frequency).
+ *   network: h1 = gelu(W1 phi + b1), h2 = gelu(W2 h1 + b2), o = W3 h2 + b3; hidden 256,
+ *     gelu(z) = z Phi(z).  o holds W (2M^2 reals, row-major complex), ln L (M N, m-major) and a
+ *     per-source bias b_n; o is padded to 40 columns.
+ *   per-frame powers: ln v[n][t] = c_n + b_n + sum_{j<9} k[n][j] q_{t+j-4} (zero outside [0, T)).
+ *   loss of one frequency against a converged (W*, L*, H*): W's columns to unit norm (row m
+ *     of L divided by ||w_m||^2, the same covariances), l = ln L - mean_m ln L,
+ *     h = ln v + mean_m ln L; the channel permutation sigma that best matches the unit
+ *     columns, then the source permutation pi that best matches l and mean_t h (first in
+ *     lexicographic order on ties);  loss = sum_m (1 - |u_sigma(m)^H u*_m|^2)
+ *     + sum_{m,n} (l[sigma(m)][pi(n)] - l*[m][n])^2 + (1/T) sum_{n,t} (h[pi(n)][t] - h*[n][t])^2,
+ *     averaged over the rows of a batch.
+ * Products run on BF16 tensor cores (operands rounded to BF16, FP32 accumulation); the rest in
+ * FP32.  Parameters are one flat FP32 vector: W1 [256][16], b1 [256], W2 [256][256], b2 [256],
+ * W3 [40][256], b3 [40], k [N][9], c [N].  This build supports M in {2, 3}, N <= 5 and
+ * 2 M^2 + M N + N <= 40.  A "row" is one frequency of one mixture.  Unless stated otherwise
+ * arrays are device memory and calls are asynchronous on the given stream.
+ * --------------------------------------------------------------------------------------- */
+typedef struct fastfca_net fastfca_net;
+
+/* Synthetic training mixtures from the model of Sec. IV (the same recipe as the tests' data):
+ * x[b][f][t] = sum_n sqrt(v_n(f,t)) chol(a_n a_n^H + 0.01 I) z, v_n(f,t) = sum_{k<K} B A with
+ * B, A ~ Exp(1), a_n the steering vector of a linear array (spacing metres, 16 kHz, 343 m/s)
+ * for a direction uniform in [0, pi), z ~ CN(0, I); all draws from Philox4x32-10 keyed by
+ * seed.  x: complex64 [B][F][T][M], device.  M <= 3, N <= 5. */
+fastfca_status fastfca_generate_mixtures(int32_t B, int32_t F, int32_t T, int32_t M, int32_t N, int32_t K,
+                                         double spacing, uint64_t seed, void* x, void* stream);
+
+/* Features of `rows` frequencies: x complex64 [rows][T][M] (row r is frequency r % F of its
+ * mixture) -> feats float32 [rows][16], q float32 [rows][T].  Device arrays. */
+fastfca_status fastfca_net_features(int32_t rows, int32_t F, int32_t T, int32_t M, const void* x, float* feats,
+                                    float* q, void* stream);
+
+/* Training targets from converged parameters (layouts of fastfca_set_params with F = rows):
+ * wt float32 [rows][M][M][2] (unit columns), lt float32 [rows][M][N], ht float32 [rows][N][T].
+ * Device arrays. */
+fastfca_status fastfca_net_targets(int32_t rows, int32_t T, int32_t M, int32_t N, const void* P, const float* lam,
+                                   const float* v, float* wt, float* lt, float* ht, void* stream);
+
+/* Creates a network for (M, N) with workspace for batches of up to max_rows rows of up to
+ * max_T frames (max_T (N + 1) 4 bytes <= 200 KiB).  Weights start uniform in +-sqrt(3/fan_in)
+ * (Philox4x32-10, seed), the last layer 100x smaller, with b3 holding W = I.  Adam moments
+ * start at zero.  EUNSUPPORTED outside the supported (M, N). */
+fastfca_status fastfca_net_create(int32_t M, int32_t N, int32_t max_rows, int32_t max_T, uint64_t seed, void* stream,
+                                  fastfca_net** out);
+
+/* Number of FP32 parameters of the flat vector. */
+int64_t fastfca_net_param_count(const fastfca_net* net);
+
+/* Copies the parameter vector out / in (host or device; synchronises). */
+fastfca_status fastfca_net_get_params(fastfca_net* net, float* out);
+fastfca_status fastfca_net_set_params(fastfca_net* net, const float* in);
+
+/* Network output o float32 [rows][40] (host or device; synchronises) for feats [rows][16]. */
+fastfca_status fastfca_net_forward(fastfca_net* net, int32_t rows, const float* feats, float* out);
+
+/* Batch loss and gradients: the mean loss goes to *loss (host; synchronises when not NULL),
+ * the gradient of every parameter (the flat layout) to grads (host or device; NULL keeps it
+ * in the network only). */
+fastfca_status fastfca_net_loss_grad(fastfca_net* net, int32_t rows, int32_t T, const float* feats, const float* q,
+                                     const float* wt, const float* lt, const float* ht, double* loss, float* grads);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) at learning rate lr on one batch; the mean loss
+ * before the step goes to *loss when not NULL (synchronises). */
+fastfca_status fastfca_net_train_step(fastfca_net* net, int32_t rows, int32_t T, const float* feats, const float* q,
+                                      const float* wt, const float* lt, const float* ht, float lr, double* loss);
+
+/* Starting point of Algorithm 1 for `rows` frequencies: P complex128 [rows][M][M],
+ * lam float32 [rows][M][N], v float32 [rows][N][T] (device; the layouts of
+ * fastfca_set_params with F = rows). */
+fastfca_status fastfca_net_predict(fastfca_net* net, int32_t rows, int32_t T, const float* feats, const float* q,
+                                   void* P, float* lam, float* v);
+
+/* Last error message of the network (or of the last failed call without one when NULL). */
+const char* fastfca_net_last_error(const fastfca_net* net);
+
+/* Frees the network. */
+void fastfca_net_destroy(fastfca_net* net);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,8 @@ loss of one frequency against a target (W*, L*, H*) from converged FastFCA:
   loss = sum_m (1 - |...|^2)_sigma + sum_{m,n} (l[sigma(m), pi(n)] - l*[m, n])^2
          + (1/T) sum_{n,t} (h[pi(n), t] - h*[n, t])^2.
 The batch loss is the mean over the frequencies of the batch.
+prediction (the starting point handed to Algorithm 1): W with unit columns (the loss fixes
+  only their directions, and l refers to unit columns), L = exp(ln L), v = exp(ln v).
 """
 from __future__ import annotations
 
@@ -238,3 +240,14 @@ def batch_loss_and_grads(params, conv, phis, qs, targets, M, N):
     g["k"] = dk / S
     g["c"] = dc / S
     return total / S, g, o
+
+
+def predict(params, conv, phi, q, M, N):
+    """Starting point (W (M, M), L (M, N), H (N, T)) of one frequency from its features."""
+    o, _ = forward(params, phi[None, :])
+    o = o[0]
+    Wn, _ = _w_unit(o, M)
+    base = 2 * M * M
+    lnL = o[base: base + M * N].reshape(M, N)
+    lnv = conv_logv(conv["k"], conv["c"], o[base + M * N: base + M * N + N], q)
+    return Wn, np.exp(lnL), np.exp(lnv)

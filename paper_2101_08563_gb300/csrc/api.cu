@@ -11,6 +11,7 @@
 
 #include "../../include/fastfca.h"
 #include "fca.cuh"
+#include "init.cuh"
 #include "launch.cuh"
 
 namespace {
@@ -136,26 +137,6 @@ __global__ void sum_over_f_kernel(const double* __restrict__ hist, int F, int st
   out[it] = s;
 }
 
-__global__ void init_fastfca_params_kernel(const float2* __restrict__ x, double2* __restrict__ P,
-                                           float* __restrict__ lam, float* __restrict__ v, int F,
-                                           int T, int M, int N) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < (size_t)F * M * M) {
-    const size_t r = i % ((size_t)M * M);
-    P[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
-  }
-  if (i < (size_t)F * M * N) lam[i] = 1.0f;
-  if (i < (size_t)F * N * T) {
-    const size_t f = i / ((size_t)N * T), t = i % T;
-    float pw = 0.f;
-    for (int m = 0; m < M; ++m) {
-      const float2 a = x[(f * T + t) * M + m];
-      pw += a.x * a.x + a.y * a.y;
-    }
-    v[i] = fmaxf(pw / (float)(M * N), 1e-30f);
-  }
-}
-
 __global__ void init_fca_params_kernel(double2* __restrict__ R, int F, int N, int M) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < (size_t)F * N * M * M) {
@@ -260,11 +241,9 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
     CKC(cudaMalloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
     CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
     CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
-    size_t n = FT(c) * c.N;
-    if ((size_t)c.F * c.M * c.M > n) n = (size_t)c.F * c.M * c.M;
-    if ((size_t)c.F * c.M * c.N > n) n = (size_t)c.F * c.M * c.N;
-    init_fastfca_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        ctx->x, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N);
+    const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
+    ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        ctx->x, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
     CKC(cudaGetLastError(), "init launch");
   } else {
     CKC(cudaMalloc(&ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M), "R alloc");
@@ -274,11 +253,9 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
     float* lamtmp = nullptr;
     CKC(cudaMalloc(&Ptmp, sizeof(double2) * (size_t)c.F * c.M * c.M), "tmp alloc");
     CKC(cudaMalloc(&lamtmp, sizeof(float) * (size_t)c.F * c.M * c.N), "tmp alloc");
-    size_t n = FT(c) * c.N;
-    if ((size_t)c.F * c.M * c.M > n) n = (size_t)c.F * c.M * c.M;
-    if ((size_t)c.F * c.M * c.N > n) n = (size_t)c.F * c.M * c.N;
-    init_fastfca_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        ctx->x, Ptmp, lamtmp, ctx->h, c.F, c.T, c.M, c.N);
+    const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
+    ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        ctx->x, Ptmp, lamtmp, ctx->h, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
     const size_t nr = (size_t)c.F * c.N * c.M * c.M;
     init_fca_params_kernel<<<(unsigned)((nr + threads - 1) / threads), threads, 0, ctx->stream>>>(ctx->R, c.F, c.N, c.M);
     cudaError_t e = cudaGetLastError();

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/fastfca.h"
+#include "init.cuh"
 #include "launch.cuh"
 
 namespace {
@@ -128,25 +129,6 @@ cudaError_t copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (is_dev(dst)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
   cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
   return e != cudaSuccess ? e : cudaStreamSynchronize(s);
-}
-
-__global__ void batch_init_kernel(const float2* __restrict__ x, double2* __restrict__ P, float* __restrict__ lam,
-                                  float* __restrict__ v, int F, int T, int M, int N) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < (size_t)F * M * M) {
-    const size_t r = i % ((size_t)M * M);
-    P[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
-  }
-  if (i < (size_t)F * M * N) lam[i] = 1.0f;
-  if (i < (size_t)F * N * T) {
-    const size_t f = i / ((size_t)N * T), t = i % T;
-    float pw = 0.f;
-    for (int m = 0; m < M; ++m) {
-      const float2 a = x[(f * T + t) * M + m];
-      pw += a.x * a.x + a.y * a.y;
-    }
-    v[i] = fmaxf(pw / (float)(M * N), 1e-30f);
-  }
 }
 
 void free_graphs(fastfca_batch* b) {
@@ -379,10 +361,9 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
     BCKC(cudaMalloc(&m.flags, sizeof(int) * (size_t)c.F), "flag alloc");
     BCKC(cudaMalloc(&m.winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
     BCKC(cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "flag clear");
-    size_t n = FT * c.N;
-    n = std::max(n, (size_t)c.F * c.M * c.M);
-    n = std::max(n, (size_t)c.F * c.M * c.N);
-    batch_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(m.x, m.P, m.lam, m.v, c.F, c.T, c.M, c.N);
+    const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
+    ffca::default_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(m.x, m.P, m.lam, m.v, c.F, c.T,
+                                                                                     c.M, c.N, (uint32_t)c.seed);
     BCKC(cudaGetLastError(), "init launch");
     for (int f = 0; f < c.F; ++f) {
       ffca::EmItem& it = b->items[m.item0 + f];

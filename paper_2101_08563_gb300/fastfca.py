@@ -51,6 +51,20 @@ _SIGNATURES = {
     "fastfca_batch_separate": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "fastfca_batch_last_error": (ctypes.c_char_p, [_P]),
     "fastfca_batch_destroy": (None, [_P]),
+    "fastfca_generate_mixtures": (ctypes.c_int, [ctypes.c_int32] * 6 + [ctypes.c_double, ctypes.c_uint64, _P, _P]),
+    "fastfca_net_features": (ctypes.c_int, [ctypes.c_int32] * 4 + [_P, _P, _P, _P]),
+    "fastfca_net_targets": (ctypes.c_int, [ctypes.c_int32] * 4 + [_P] * 7),
+    "fastfca_net_create": (ctypes.c_int, [ctypes.c_int32] * 4 + [ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+    "fastfca_net_param_count": (ctypes.c_int64, [_P]),
+    "fastfca_net_get_params": (ctypes.c_int, [_P, _P]),
+    "fastfca_net_set_params": (ctypes.c_int, [_P, _P]),
+    "fastfca_net_forward": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "fastfca_net_loss_grad": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32] + [_P] * 7),
+    "fastfca_net_train_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32] + [_P] * 5
+                               + [ctypes.c_float, _P]),
+    "fastfca_net_predict": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32] + [_P] * 5),
+    "fastfca_net_last_error": (ctypes.c_char_p, [_P]),
+    "fastfca_net_destroy": (None, [_P]),
 }
 
 
@@ -62,7 +76,7 @@ class FastFCAError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("F", ctypes.c_int32), ("T", ctypes.c_int32), ("M", ctypes.c_int32),
-                ("N", ctypes.c_int32), ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("N", ctypes.c_int32), ("model", ctypes.c_int32), ("seed", ctypes.c_int32)]
 
 
 _lib = None
@@ -128,10 +142,11 @@ class Separator:
     """One separation problem (one mixture) held by the library.
 
     x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" or "fca".
-    A CUDA x is borrowed (kept referenced here); a host x is copied by the library.
+    A CUDA x is borrowed (kept referenced here); a host x is copied by the library.  seed
+    selects the random factor of the default initial v (see fastfca_create).
     """
 
-    def __init__(self, x, N: int, model: str = "fastfca", stream=None):
+    def __init__(self, x, N: int, model: str = "fastfca", stream=None, seed: int = 0):
         self.lib = load()
         shape = tuple(x.shape)
         if len(shape) != 3:
@@ -139,7 +154,7 @@ class Separator:
         self.F, self.T, self.M = (int(s) for s in shape)
         self.N = int(N)
         self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA}[model]
-        cfg = Config(self.F, self.T, self.M, self.N, self.model, 0)
+        cfg = Config(self.F, self.T, self.M, self.N, self.model, int(seed) & 0x7fffffff)
         px, self._x = _ptr(x, np.complex64, shape, "x")
         self.stream = _default_stream() if stream is None else stream
         h = ctypes.c_void_p()
@@ -250,12 +265,13 @@ def abi_symbols_from_header(path: str | None = None):
 class Batch:
     """Many independent FastFCA mixtures iterated together in one CUDA-graph launch.
 
-    xs: list of complex64 (F_b, T_b, M_b) arrays (host or CUDA); Ns: sources per mixture.
+    xs: list of complex64 (F_b, T_b, M_b) arrays (host or CUDA); Ns: sources per mixture;
+    seeds: per-mixture seeds of the default initial v (default: the mixture index).
     """
 
     SCHEMES = {0: "fine", 1: "coarse", 2: "single"}
 
-    def __init__(self, xs, Ns, stream=None):
+    def __init__(self, xs, Ns, stream=None, seeds=None):
         self.lib = load()
         if len(xs) != len(Ns) or not xs:
             raise ValueError("xs and Ns must be non-empty and of equal length")
@@ -267,7 +283,8 @@ class Batch:
         for i, (x, N) in enumerate(zip(xs, Ns)):
             F, T, M = (int(s) for s in x.shape)
             self.shapes.append((F, T, M, int(N)))
-            cfgs[i] = Config(F, T, M, int(N), MODEL_FASTFCA, 0)
+            seed = i if seeds is None else int(seeds[i]) & 0x7fffffff
+            cfgs[i] = Config(F, T, M, int(N), MODEL_FASTFCA, seed)
             p, keep = _ptr(x, np.complex64, (F, T, M), f"xs[{i}]")
             ptrs[i] = p.value
             self._xs.append(keep)
