@@ -244,6 +244,31 @@ def run_batch(shapes, data, dev, stream, clocks_ok=True):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def run_learned(n_train):
+    """The learned initialiser end to end on the GPU: n_train generated mixtures of the
+    learned-initialiser workload with 200-iteration FastFCA targets, 6 epochs of training, and
+    the comparison with the default start on 512 held-out mixtures (batched as one context)."""
+    import torch
+    from paper_2101_08563_gb300 import learned as L
+    w = synth.WORKLOADS["learned"]
+    data, t_data = L.make_training_set(n_train, w.F, w.T, w.M, w.N, w.K, w.spacing, seed=w.seed, iters=w.iters)
+    n_eval = 512
+    net = L.InitNet(w.M, w.N, max_rows=n_eval * w.F, max_T=w.T, seed=w.seed + 1)
+    loss0 = L.mean_loss(net, data)
+    hist, t_train = L.train(net, data, epochs=6, batch=2048, lr=1e-3, seed=w.seed)
+    loss1 = L.mean_loss(net, data)
+    del data
+    torch.cuda.empty_cache()
+    res = L.evaluate(net, n_eval, w.F, w.T, w.M, w.N, w.K, w.spacing, seed=(0xFFFF << 32) + w.seed, iters=w.iters)
+    net.close()
+    res.update({"workload": w.name, "train_mixtures": n_train, "target_iters": w.iters,
+                "train_data_seconds": t_data, "train_seconds": t_train, "epochs": 6, "batch_rows": 2048,
+                "loss_untrained": loss0, "loss_trained": loss1,
+                "held_out": "512 mixtures, generator key disjoint from the training keys",
+                "reference_ll": "default start after 200 iterations (GPU FastFCA, oracle-parity tested)"})
+    return res
+
+
 def load_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -423,6 +448,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-mixtures", type=int, default=20000)
     ap.add_argument("--profile", action="store_true",
                     help="only run the IP+EM kernel on the bench mixture's first frequencies tiled to "
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
@@ -493,6 +520,9 @@ def main():
     if batch_data is not None:
         import torch
         batch = run_batch(*batch_data, torch.device("cuda", local_rank), torch.cuda.current_stream())
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = run_learned(args.learned_mixtures)
     if rank != 0:
         return
     peaks = load_peaks()
@@ -521,6 +551,8 @@ def main():
     }
     if batch is not None:
         out["batch"] = batch
+    if learned is not None:
+        out["learned_init"] = learned
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out))

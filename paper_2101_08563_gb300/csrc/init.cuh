@@ -6,6 +6,7 @@
 // alike, and they stay identical forever.
 #pragma once
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace ffca {
 

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace ffca {
 namespace learn {

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 HARNESS = r"""
 #include <cstdio>
-#include "common.cuh"
+#include "philox.cuh"
 int main() {
   using namespace ffca;
   const U4 in[3] = {{0u, 0u, 0u, 0u}, {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu},
