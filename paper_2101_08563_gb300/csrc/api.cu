@@ -16,8 +16,8 @@
 
 namespace {
 
-constexpr int kMaxM = 4;
-constexpr int kMaxN = 8;
+constexpr int kMaxM = 8;
+constexpr int kMaxN = 16;
 
 thread_local char g_create_error[512] = "";
 
@@ -195,10 +195,10 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
   ffca::FastOps ops{};
   ffca::FcaOps fops{};
   if (c.model == FASTFCA_MODEL_FASTFCA) {
-    if (!ffca::fast_ops(c.M, c.N, &ops))
-      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FastFCA kernel for M=%d N=%d (M in 2..%d, N in 2..%d)", c.M, c.N, kMaxM, kMaxN);
-    if (c.T > ops.max_T)
-      return fail(nullptr, FASTFCA_EUNSUPPORTED, "T=%d exceeds the %d frames one CTA holds", c.T, ops.max_T);
+    if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops))
+      return fail(nullptr, FASTFCA_EUNSUPPORTED,
+                  "no FastFCA kernel for M=%d N=%d T=%d (M in 2..%d, N in 1..%d, T within eight CTAs' "
+                  "shared memory)", c.M, c.N, c.T, kMaxM, kMaxN);
   } else {
     if (!ffca::fca_ops(c.M, c.N, &fops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FCA kernel for M=%d N=%d", c.M, c.N);
@@ -351,6 +351,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     a.err = ctx->err;
     a.F = c.F;
     a.T = c.T;
+    a.N = c.N;
     a.n_iter = n_iter;
     a.ll_stride = n_iter;
     CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA EM launch");
@@ -394,6 +395,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
     a.err = ctx->err;
     a.F = c.F;
     a.T = c.T;
+    a.N = c.N;
     a.n_iter = 0;
     a.ll_stride = 0;
     CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA log-likelihood launch");
@@ -437,7 +439,7 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   cudaError_t e;
   if (c.model == FASTFCA_MODEL_FASTFCA) {
     e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
-    if (e == cudaSuccess) e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, c.T, ctx->stream);
+    if (e == cudaSuccess) e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, c.T, c.N, ctx->stream);
   } else {
     e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
   }

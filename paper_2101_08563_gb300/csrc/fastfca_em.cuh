@@ -53,6 +53,7 @@ struct EmArgs {
   int b_valid;          // Bst/detst hold W^{-H} and |det W|^2 of the current P
   int* err;             // status bits (ErrBits)
   int F, T, n_iter, ll_stride;
+  int N;                // sources (read by the cluster kernel; the others take N as a template)
   long long* clocks;    // phase timestamps of frequency 0 (only with FFCA_PHASE_CLOCKS)
 };
 

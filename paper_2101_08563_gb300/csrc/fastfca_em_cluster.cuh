@@ -1,0 +1,589 @@
+// FastFCA IP+EM (Algorithm 1) for large bins: one thread-block cluster owns one frequency.
+//
+// The frequency-resident kernel (fastfca_em.cuh) keeps a frequency's per-frame state in one
+// CTA and its per-frame ratios in registers; that stops at M = 4, N = 8, T = 2048.  Here the
+// T frames of a frequency are split over the C CTAs of a cluster (C in {1, 2, 4, 8}, CTA rank
+// c owns frames [c Tc, min((c+1) Tc, T)), Tc = ceil(T / C)), and every per-frame array lives
+// in that CTA's shared memory: H (N x Tc), U = |W^H x|^2, sigma^2 and r (M x Tc each).  M is a
+// template parameter (M <= 8); N is a runtime parameter (N <= 16).  The steps and their
+// order are those of the frequency-resident kernel (see its file comment for the equations):
+//
+//   pass A   pending H[N-1,:] update, sigma^2 = L H, 1/sigma^2, log-likelihood terms
+//   Q pass   Q_m = (1/T) sum_t x x^H / sigma^2_m  (Eq. 33): lanes own Hermitian entries,
+//            warps own frames, so no warp reduction is needed
+//   IP       Q_m^{-1} (HPD Gauss-Jordan, FP64), the CTAs of the cluster splitting the M
+//            matrices; then the column loop of Eq. 34-35 on B = W^{-H} by four warps (FP64)
+//   U pass   U = |W^H x|^2 (Eq. 37)
+//   n-loop   for each source: r = 1 + G (U / sigma^2 - 1), L[:,n] *= mean_t r, then
+//            H[n,:] *= (1/M) sum_m r / mean_t r in the next pass (Gauss-Seidel), with sigma^2
+//            updated by the change of that source's term: sigma^2_m += L'H' - LH
+//
+// Every reduction over t (Q, log-likelihood, the n-loop means) is summed per warp, then per
+// CTA in warp order, then over the cluster in rank order through distributed shared memory,
+// so all CTAs of a cluster hold bit-identical W, B, L and agree on every decision.  Exchange
+// buffers are double-buffered, so one cluster barrier per reduction suffices (a buffer is
+// rewritten only after every CTA has passed the following barrier, i.e. finished reading).
+#pragma once
+#include "fastfca_em.cuh"
+
+namespace ffca {
+
+constexpr int kCThreads = 256;               // threads per CTA
+constexpr int kCWarps = kCThreads / 32;
+constexpr int kCMaxN = 16;                   // sources
+constexpr int kCMaxCluster = 8;              // portable cluster size
+constexpr int kCIpThreads = 128;             // the four FP64 warps of the IP (one per SMSP)
+
+// ------------------------------------------------------------------ cluster primitives
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned dyn_smem_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
+// Barrier over every thread of every CTA of the cluster; release/acquire order the shared
+// memory accesses (local and distributed) made before it against those made after it.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of `p` (this CTA's shared memory) in the shared memory of CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, unsigned rank) {
+  const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  return remote;
+}
+
+__device__ __forceinline__ double ld_dsmem_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ double2 ld_dsmem_f64x2(uint32_t addr) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Barrier of the four IP warps (threads 0..127) only.
+__device__ __forceinline__ void ip_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// ------------------------------------------------------------------ shared-memory layout
+template <int M>
+struct ClusterSmem {
+  static constexpr int NE = M * M;                        // packed Hermitian entries of Q_m
+  static constexpr int V = M * NE;                        // reals of all Q_m
+  static constexpr int kXV = V + 1;                       // exchange: Q entries + log-lik
+  static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
+  static constexpr int kWcPad = (M * M + 1) & ~1;
+  // byte offsets (all multiples of 16)
+  static constexpr size_t oW = 0;                                         // double2 M*M
+  static constexpr size_t oB = oW + 16 * M * M;                           // double2 M*M
+  static constexpr size_t oQ = oB + 16 * M * M;                           // double2 kQsz
+  static constexpr size_t oV = oQ + 16 * (size_t)kQsz;                    // double2 8 (w_raw)
+  static constexpr size_t oBeta = oV + 16 * 8;                            // double2 8
+  static constexpr size_t oDet = oBeta + 16 * 8;                          // double 4
+  static constexpr size_t oX = oDet + 32;                                 // double 2 x kXV
+  static constexpr size_t oWc = oX + ((8 * 2 * (size_t)kXV + 15) & ~(size_t)15);   // float2 kWcPad
+  static constexpr size_t oL = oWc + 8 * (size_t)kWcPad;                  // float M*kCMaxN
+  static constexpr size_t oRed = oL + 4 * (size_t)M * kCMaxN;             // float kCWarps*8
+  static constexpr size_t oLL = oRed + 4 * kCWarps * 8;                   // float kCWarps
+  static constexpr size_t oQw = oLL + 4 * kCWarps;                        // float kCWarps*V
+  static constexpr size_t oFrames = oQw + 4 * (size_t)kCWarps * V;        // per-frame arrays
+  // per-frame arrays, each row padded to Tcp = Tc rounded up to 4 floats
+  __host__ __device__ static int tcp(int Tc) { return (Tc + 3) & ~3; }
+  __host__ __device__ static size_t bytes(int N, int Tc) { return oFrames + 4 * (size_t)tcp(Tc) * (N + 3 * M); }
+};
+
+// ------------------------------------------------------------------ FP64 pieces of the IP
+// In-place inverses of the Q_m (HPD, row-major, M*M each, at Q + m*M*M) for the m with
+// m % C == crank, by the four IP warps: slot i of the owned entries goes to thread
+// i % 128 (warp (i % 128) / 32), so every FP64 warp instruction of a step does up to 32 entries and
+// the four warps sit on the four sub-partitions.  Gauss-Jordan without pivoting (the pivots
+// of an HPD matrix are positive Schur complements); a non-positive pivot sets kErrQPivot.
+template <int M>
+__device__ void cluster_hpd_inverses(double2* Q, int crank, int C, int tid, int* err) {
+  constexpr int E = M * M;
+  constexpr int kMaxSlots = (M * E + kCIpThreads - 1) / kCIpThreads;   // all M matrices when C = 1
+  const int owned = (crank < M) ? (M - 1 - crank) / C + 1 : 0;
+  const int total = owned * E;
+  for (int k = 0; k < M; ++k) {
+    double2 nv[kMaxSlots];
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < kMaxSlots; ++s) {
+      const int i = tid + s * kCIpThreads;
+      if (i < total) {
+        const int mo = i / E, e = i - mo * E;
+        double2* A = Q + (crank + mo * C) * E;
+        const int r = e / M, cc = e - r * M;
+        const double d = A[k * M + k].x;
+        const float df = (float)d;
+        bad |= !(df > 0.f && df < INFINITY);
+        const double rd = rcp_pos_f64((df > 0.f && df < INFINITY) ? d : 1.0);
+        const double2 aij = A[e], aik = A[r * M + k], akj = A[k * M + cc];
+        const double2 base = (r != k && cc != k) ? aij : make_double2(0.0, 0.0);
+        const double2 c1 = (r != k) ? aik : make_double2(-1.0, 0.0);
+        const double2 c2 = (cc != k) ? akj : make_double2(1.0, 0.0);
+        const double2 t = make_double2(c1.x * rd, c1.y * rd);
+        nv[s] = make_double2(fma(t.y, c2.y, fma(-t.x, c2.x, base.x)), fma(-t.y, c2.x, fma(-t.x, c2.y, base.y)));
+      }
+    }
+    ip_bar();
+#pragma unroll
+    for (int s = 0; s < kMaxSlots; ++s) {
+      const int i = tid + s * kCIpThreads;
+      if (i < total) {
+        const int mo = i / E, e = i - mo * E;
+        Q[(crank + mo * C) * E + e] = nv[s];
+      }
+    }
+    ip_bar();
+    if (bad) atomicOr(err, kErrQPivot);
+  }
+}
+
+// The IP column loop (Eq. 34-35) by the four IP warps, for any M <= 8.  Qi holds Q_m^{-1}.
+// Thread (w, lane) with lane = (rl * 8 + c) * 2 + part covers row r = 2 w + rl, column c,
+// real (part 0) or imaginary (part 1) part; sums over c are xor-shuffles over lane bits 1-3.
+// Per column m:  w_raw = Q_m^{-1} b_m;  beta = w_raw^H B;  s = Re beta_m;  w_m = w_raw/sqrt(s);
+// b_k -= (beta_k / s) b_m (k != m), b_m /= sqrt(s);  |det W|^2 *= s.  Updates sW, sB, sWc
+// and sDet; all four warps leave with the results visible to each other.
+template <int M>
+__device__ void cluster_ip_columns(const double2* Qi, double2* sW, double2* sB, float2* sWc, double* sDet,
+                                   double2* sV, double2* sBeta, int tid, int* err) {
+  const int w = tid >> 5, lane = tid & 31;
+  const int part = lane & 1, c = (lane >> 1) & 7, rl = lane >> 4;
+  const int r = 2 * w + rl;
+  const bool act = r < M && c < M;
+  double mant = sDet[0], expo = sDet[1];
+  for (int m = 0; m < M; ++m) {
+    const double2* Q = Qi + m * M * M;
+    // w_raw[r] = sum_c Qinv[r][c] b_m[c]
+    double pw = 0.0;
+    if (act) {
+      const double2 q = Q[r * M + c];
+      const double2 bb = sB[c * M + m];
+      pw = fma(q.x, part ? bb.y : bb.x, q.y * (part ? bb.x : -bb.y));
+    }
+#pragma unroll
+    for (int off = 2; off <= 8; off <<= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
+    if (act && c == 0) reinterpret_cast<double*>(sV)[2 * r + part] = pw;
+    ip_bar();
+    // beta_k = sum_i conj(w_raw[i]) B[i][k]     (row index r plays k, c plays i)
+    double pb = 0.0;
+    if (act) {
+      const double2 wi = sV[c];
+      const double2 bk = sB[c * M + r];
+      pb = part ? fma(wi.x, bk.y, -wi.y * bk.x) : fma(wi.x, bk.x, wi.y * bk.y);
+    }
+#pragma unroll
+    for (int off = 2; off <= 8; off <<= 1) pb += __shfl_xor_sync(0xffffffffu, pb, off);
+    if (act && c == 0) reinterpret_cast<double*>(sBeta)[2 * r + part] = pb;
+    ip_bar();
+    const double s = sBeta[m].x;
+    const float sf = (float)s;
+    const bool ok = sf > 0.f && sf < INFINITY;
+    const double sc = rsqrt_pos_f64(ok ? s : 1.0);
+    const double sc2 = sc * sc;
+    // B update on row i = r, column k = c; w_m[i] = w_raw[i] sqrt(s)^-1
+    double nb = 0.0;
+    if (act) {
+      const double2 bki = sB[r * M + c];
+      const double2 bmi = sB[r * M + m];
+      if (c == m) {
+        nb = (part ? bmi.y : bmi.x) * sc;
+      } else {
+        const double2 be = sBeta[c];
+        const double cr = be.x * sc2, ci = be.y * sc2;
+        nb = part ? fma(-ci, bmi.x, fma(-cr, bmi.y, bki.y)) : fma(ci, bmi.y, fma(-cr, bmi.x, bki.x));
+      }
+    }
+    const double wv = act ? reinterpret_cast<const double*>(sV)[2 * r + part] * sc : 0.0;
+    __syncwarp();                         // row r's reads above precede its writes below
+    if (act) reinterpret_cast<double*>(sB)[2 * (r * M + c) + part] = nb;
+    if (act && c == 0) {
+      reinterpret_cast<double*>(sW)[2 * (r * M + m) + part] = wv;
+      reinterpret_cast<float*>(sWc)[2 * (m * M + r) + part] = part ? (float)-wv : (float)wv;
+    }
+    if (!ok && tid == 0) atomicOr(err, kErrIpNorm);
+    mant *= ok ? s : 1.0;
+    renorm(mant, expo);
+    ip_bar();
+  }
+  if (tid == 0) { sDet[0] = mant; sDet[1] = expo; }
+}
+
+// Packed Hermitian entry e of x x^H (the order of xxh_packed): e < M is |x_e|^2, then for
+// each pair a < b (row-major) Re(x_a conj x_b) and Im(x_a conj x_b).  kind 0 diagonal,
+// 1 real part, 2 imaginary part.
+template <int M>
+__device__ __forceinline__ void decode_entry(int e, int& a, int& b, int& kind) {
+  if (e < M) { a = e; b = e; kind = 0; return; }
+  int idx = (e - M) >> 1;
+  kind = 1 + ((e - M) & 1);
+  a = 0;
+  while (idx >= M - 1 - a) { idx -= M - 1 - a; ++a; }
+  b = a + 1 + idx;
+}
+
+// ------------------------------------------------------------------ the kernel
+// Grid: F * C CTAs of kCThreads threads in clusters of C (rank c of cluster f owns frames
+// [c Tc, ...) of frequency f); dynamic shared memory ClusterSmem<M>::bytes(N, Tc).
+template <int M>
+__global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs p) {
+  using SM = ClusterSmem<M>;
+  constexpr int NE = SM::NE, V = SM::V, XV = SM::kXV;
+  constexpr int EPL = (NE + 31) / 32;
+  constexpr int MP = pow2_ceil(M);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = (int)cluster_size(), crank = (int)cluster_rank();
+  const int f = blockIdx.x / C;
+  const int T = p.T, N = p.N;
+  const int Tc = (T + C - 1) / C;
+  const int Tcp = SM::tcp(Tc);
+  // the same outcome in every CTA: no CTA is left waiting at a cluster barrier
+  if (N < 1 || N > kCMaxN || blockDim.x != kCThreads || f >= p.F || (C - 1) * Tc >= T ||
+      dyn_smem_size() < SM::bytes(N, Tc)) {
+    if (tid == 0) atomicOr(p.err, kErrConfig);
+    return;
+  }
+  double2* sW = reinterpret_cast<double2*>(smem + SM::oW);
+  double2* sB = reinterpret_cast<double2*>(smem + SM::oB);
+  double2* sQ = reinterpret_cast<double2*>(smem + SM::oQ);
+  double2* sV = reinterpret_cast<double2*>(smem + SM::oV);
+  double2* sBeta = reinterpret_cast<double2*>(smem + SM::oBeta);
+  double* sDet = reinterpret_cast<double*>(smem + SM::oDet);
+  double* sX = reinterpret_cast<double*>(smem + SM::oX);
+  float2* sWc = reinterpret_cast<float2*>(smem + SM::oWc);
+  float* sL = reinterpret_cast<float*>(smem + SM::oL);
+  float* sRed = reinterpret_cast<float*>(smem + SM::oRed);
+  float* sLL = reinterpret_cast<float*>(smem + SM::oLL);
+  float* sQw = reinterpret_cast<float*>(smem + SM::oQw);
+  float* sH = reinterpret_cast<float*>(smem + SM::oFrames);   // [n][j]
+  float* sU = sH + (size_t)N * Tcp;                             // [m][j]
+  float* sS = sU + (size_t)M * Tcp;                             // sigma^2 [m][j]
+  float* sR = sS + (size_t)M * Tcp;                             // 1/sigma^2 or r [m][j]
+
+  const int t0 = crank * Tc;
+  const int Tl = min(Tc, T - t0);
+  const float2* xf = p.x + ((size_t)f * T + t0) * M;
+  double2* Pf = p.P + (size_t)f * M * M;
+  float* lamf = p.lam + (size_t)f * M * N;
+  float* vf = p.v + (size_t)f * N * T;
+  const double invT = 1.0 / (double)T;
+  const float invTf = 1.0f / (float)T;
+
+  // ---- load the parameters (L and W replicated, H for this CTA's frames)
+  for (int i = tid; i < M * N; i += kCThreads) sL[i] = lamf[i];
+  for (int i = tid; i < M * M; i += kCThreads) sW[i] = Pf[i];
+  for (int n = 0; n < N; ++n)
+    for (int j = tid; j < Tl; j += kCThreads) sH[n * Tcp + j] = vf[(size_t)n * T + t0 + j];
+  __syncthreads();
+  if (warp == 0) {
+    if (p.b_valid) {
+      for (int e = lane; e < M * M; e += 32) sB[e] = p.Bst[(size_t)f * M * M + e];
+      if (lane == 0) { sDet[0] = p.detst[2 * f]; sDet[1] = p.detst[2 * f + 1]; }
+    } else {
+      for (int e = lane; e < M * M; e += 32) {
+        const int i = e / M, j = e - (e / M) * M;
+        const double2 w = sW[j * M + i];
+        sQ[e] = make_double2(w.x, -w.y);                        // W^H
+      }
+      __syncwarp();
+      double mant, expo;
+      warp_inverse_pivot<M>(sQ, sQ + M * M, sB, mant, expo, lane, p.err);
+      if (lane == 0) { sDet[0] = mant; sDet[1] = expo; }
+    }
+    for (int e = lane; e < M * M; e += 32) {
+      const int a = e / M, m = e - (e / M) * M;
+      const double2 w = sW[a * M + m];
+      sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    }
+  }
+  __syncthreads();
+
+  auto load_x = [&](int j, float2 (&xv)[M]) {
+    const float2* src = xf + (size_t)j * M;
+    if constexpr (M % 2 == 0) {
+#pragma unroll
+      for (int a = 0; a < M; a += 2) {
+        const float4 q4 = __ldg(reinterpret_cast<const float4*>(src + a));
+        xv[a] = make_float2(q4.x, q4.y);
+        xv[a + 1] = make_float2(q4.z, q4.w);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
+    }
+  };
+
+  // U = |W^H x|^2 for this CTA's frames
+  auto pass_U = [&]() {
+    for (int j = tid; j < Tl; j += kCThreads) {
+      float2 xv[M];
+      load_x(j, xv);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xv[a], y);
+        sU[m * Tcp + j] = fmaf(y.x, y.x, y.y * y.y);
+      }
+    }
+  };
+
+  auto ll_from_sum = [&](double s) {
+    const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
+    return (double)T * logdet - s - (double)M * (double)T * kLnPi;
+  };
+
+  // sum over the cluster, in rank order, of the value at this CTA's shared address `local`
+  auto cluster_sum = [&](const double* local) {
+    double s = 0.0;
+    for (int c = 0; c < C; ++c) s += ld_dsmem_f64(dsmem_addr(local, (unsigned)c));
+    return s;
+  };
+
+  // lane -> Hermitian entries of the Q pass
+  int ea[EPL], eb[EPL], ek[EPL];
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) {
+    const int e = lane + 32 * q;
+    if (e < NE) decode_entry<M>(e, ea[q], eb[q], ek[q]);
+    else { ea[q] = 0; eb[q] = 0; ek[q] = 3; }
+  }
+
+  float coef[M], Lold[M], Lnew[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) { coef[m] = 0.f; Lold[m] = 0.f; Lnew[m] = 0.f; }
+  int par = 0;
+
+  if (p.n_iter == 0) {
+    pass_U();
+    __syncthreads();
+  }
+
+#pragma unroll 1
+  for (int it = 0;; ++it) {
+    const bool have_ll = (it > 0) || (p.n_iter == 0);
+    const bool do_iter = it < p.n_iter;
+
+    // ---- pass A: pending H[N-1,:] update, sigma^2 = L H, 1/sigma^2, log-likelihood terms
+    {
+      float llp = 0.f;
+      bool bad = false;
+      for (int j = tid; j < Tl; j += kCThreads) {
+        if (it > 0) {
+          float g = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
+          sH[(N - 1) * Tcp + j] *= g;
+        }
+        float h[kCMaxN];
+#pragma unroll
+        for (int n = 0; n < kCMaxN; ++n) {
+          const float hv = sH[(n < N ? n : 0) * Tcp + j];     // index kept inside the array
+          h[n] = (n < N) ? hv : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float s2 = 0.f;
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n)
+            if (n < N) s2 = fmaf(sL[m * N + (n < N ? n : 0)], h[n], s2);
+          bad |= !(s2 > 0.f && s2 < INFINITY);
+          const float rs = fast_rcp(s2);
+          sS[m * Tcp + j] = s2;
+          sR[m * Tcp + j] = rs;
+          if (have_ll) llp += fmaf(sU[m * Tcp + j], rs, __logf(s2));
+        }
+      }
+      if (bad) atomicOr(p.err, kErrSigma);
+      llp = warp_sum(llp);
+      if (lane == 0) sLL[warp] = llp;
+    }
+    double* xb = sX + par * XV;
+    if (!do_iter) {
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kCWarps; ++w) s += (double)sLL[w];
+        xb[V] = s;
+      }
+      cluster_sync();
+      if (crank == 0 && tid == 0) {
+        const double ll = ll_from_sum(cluster_sum(xb + V));
+        if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+        if (p.ll_last) p.ll_last[f] = ll;
+      }
+      break;
+    }
+
+    // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33): warp w takes frames j = w mod 8,
+    // lane l the entries l + 32 q, for every m
+    {
+      float acc[M][EPL];
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < EPL; ++q) acc[m][q] = 0.f;
+      for (int j = warp; j < Tl; j += kCWarps) {
+        const float2* xt = xf + (size_t)j * M;
+        float ev[EPL];
+#pragma unroll
+        for (int q = 0; q < EPL; ++q) {
+          if (ek[q] == 3) { ev[q] = 0.f; continue; }
+          const float2 xa = __ldg(xt + ea[q]), xc = __ldg(xt + eb[q]);
+          ev[q] = (ek[q] == 0) ? fmaf(xa.x, xa.x, xa.y * xa.y)
+                  : (ek[q] == 1) ? fmaf(xa.x, xc.x, xa.y * xc.y) : fmaf(xa.y, xc.x, -xa.x * xc.y);
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float w = sR[m * Tcp + j];
+#pragma unroll
+          for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < EPL; ++q)
+          if (lane + 32 * q < NE) sQw[warp * V + m * NE + lane + 32 * q] = acc[m][q];
+    }
+    __syncthreads();
+    for (int i = tid; i < V; i += kCThreads) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kCWarps; ++w) s += (double)sQw[w * V + i];
+      xb[i] = s;
+    }
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kCWarps; ++w) s += (double)sLL[w];
+      xb[V] = s;
+    }
+    cluster_sync();
+    for (int i = tid; i < V; i += kCThreads) {
+      const double qd = cluster_sum(xb + i) * invT;
+      const int m = i / NE, e = i - m * NE;
+      int a, b, kind;
+      decode_entry<M>(e, a, b, kind);
+      double2* Qm = sQ + m * M * M;
+      if (kind == 0) Qm[a * M + a] = make_double2(qd, 0.0);
+      else if (kind == 1) { Qm[a * M + b].x = qd; Qm[b * M + a].x = qd; }
+      else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
+    }
+    if (have_ll && crank == 0 && tid == 0 && p.ll_hist)
+      p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(cluster_sum(xb + V));
+    par ^= 1;
+    __syncthreads();
+
+    // ---- IP (FP64): this CTA's share of the Q_m^{-1}, gathered over the cluster, then the
+    // column loop (every CTA, identical inputs, identical results)
+    if (tid < kCIpThreads) cluster_hpd_inverses<M>(sQ, crank, C, tid, p.err);
+    cluster_sync();
+    if (C > 1) {
+      for (int i = tid; i < M * M * M; i += kCThreads) {
+        const int owner = (i / (M * M)) % C;
+        if (owner != crank) sQ[i] = ld_dsmem_f64x2(dsmem_addr(sQ + i, (unsigned)owner));
+      }
+    }
+    __syncthreads();
+    if (tid < kCIpThreads) cluster_ip_columns<M>(sQ, sW, sB, sWc, sDet, sV, sBeta, tid, p.err);
+    __syncthreads();
+
+    // ---- U = |W^H x|^2 (Eq. 37); each thread later reads only its own frames
+    pass_U();
+
+    // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's
+    // H update and its change of sigma^2
+#pragma unroll 1
+    for (int n = 0; n < N; ++n) {
+      float Ln[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
+      float acc[MP];
+#pragma unroll
+      for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+      for (int j = tid; j < Tl; j += kCThreads) {
+        if (n > 0) {
+          float g = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
+          const float hold = sH[(n - 1) * Tcp + j];
+          const float hnew = hold * g;
+          sH[(n - 1) * Tcp + j] = hnew;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            // sigma^2 <- sigma^2 - L H + L' H' (one rounding: fma), never below the new term
+            const float s2 = fmaf(Lnew[m], hnew, fmaf(-Lold[m], hold, sS[m * Tcp + j]));
+            sS[m * Tcp + j] = fmaxf(s2, Lnew[m] * hnew);
+          }
+        }
+        const float hn = sH[n * Tcp + j];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float s2 = sS[m * Tcp + j];
+          const float rs = fast_rcp(s2);
+          const float G = Ln[m] * hn * rs;
+          const float rr = fmaf(G, fmaf(sU[m * Tcp + j], rs, -1.f), 1.f);
+          sR[m * Tcp + j] = rr;
+          acc[m] += rr;
+        }
+      }
+      warp_reduce_scatter<MP>(acc, lane);
+      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) sRed[warp * 8 + (lane * MP) / 32] = acc[0];
+      __syncthreads();
+      double* xn = sX + par * XV;
+      if (tid < M) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCWarps; ++w) s += (double)sRed[w * 8 + tid];
+        xn[tid] = s;
+      }
+      cluster_sync();
+      const double tot_l = (lane < M) ? cluster_sum(xn + lane) : 0.0;
+      par ^= 1;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float mean = (float)__shfl_sync(0xffffffffu, tot_l, m) * invTf;
+        Lold[m] = Ln[m];
+        Lnew[m] = Ln[m] * mean;
+        sL[m * N + n] = Lnew[m];           // the same value from every thread
+        coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+      }
+    }
+  }
+
+  // ---- write back: this CTA's frames of H; rank 0 the per-frequency parameters
+  __syncthreads();
+  for (int n = 0; n < N; ++n)
+    for (int j = tid; j < Tl; j += kCThreads) vf[(size_t)n * T + t0 + j] = sH[n * Tcp + j];
+  if (crank == 0) {
+    for (int i = tid; i < M * N; i += kCThreads) lamf[i] = sL[i];
+    for (int i = tid; i < M * M; i += kCThreads) {
+      Pf[i] = sW[i];
+      p.Bst[(size_t)f * M * M + i] = sB[i];
+    }
+    if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
+  }
+  cluster_sync();          // no CTA exits while a peer may still read its shared memory
+}
+
+}  // namespace ffca

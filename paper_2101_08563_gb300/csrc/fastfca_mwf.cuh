@@ -109,4 +109,72 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
   }
 }
 
+// Wide form of the filter for large bins (any M <= 8, runtime N <= kMwfWMaxN): phase 1 forms
+// y = W^H x_t and the gains g_mn(t) of kMwfWFrames frames in shared memory, one thread per
+// (frame, m); phase 2 writes the CTA's output span (frames t0.. t0+nt, all n, all a) in memory
+// order, one complex value per thread and step, so the stores coalesce.
+constexpr int kMwfWFrames = 32;
+constexpr int kMwfWThreads = 256;
+constexpr int kMwfWMaxN = 16;
+
+template <int M>
+__global__ void __launch_bounds__(kMwfWThreads) fastfca_mwf_wide_kernel(
+    const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
+    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int N) {
+  __shared__ float2 sWc[M * M];                  // conj(W[a][m]) at [m*M + a]
+  __shared__ float2 sWi[M * M];                  // W^{-H}[a][m] at [a*M + m]
+  __shared__ float sL[M * kMwfWMaxN];
+  __shared__ float2 sY[kMwfWFrames][M];
+  __shared__ float sG[kMwfWFrames][kMwfWMaxN][M];
+  const int f = blockIdx.x, tid = threadIdx.x;
+  const int t0 = blockIdx.y * kMwfWFrames;
+  if (f >= F || t0 >= T || N > kMwfWMaxN) return;
+  const int nt = min(kMwfWFrames, T - t0);
+  for (int e = tid; e < M * M; e += kMwfWThreads) {
+    const int a = e / M, m = e - (e / M) * M;
+    const double2 w = P[(size_t)f * M * M + e];
+    sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    sWi[e] = WmH[(size_t)f * M * M + e];
+  }
+  for (int e = tid; e < M * N; e += kMwfWThreads) sL[e] = lam[(size_t)f * M * N + e];
+  __syncthreads();
+  if (tid < nt * M) {
+    const int tl = tid / M, m = tid - (tid / M) * M;
+    const int t = t0 + tl;
+    const float2* xt = x + ((size_t)f * T + t) * M;
+    float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xt[a], y);
+    sY[tl][m] = y;
+    float h[kMwfWMaxN];
+    float s2 = 0.f;
+#pragma unroll
+    for (int n = 0; n < kMwfWMaxN; ++n) {
+      const int nn = (n < N) ? n : 0;                  // index kept inside the arrays
+      const float hv = v[((size_t)f * N + nn) * T + t], lv = sL[m * N + nn];
+      h[n] = (n < N) ? hv : 0.f;
+      s2 = fmaf((n < N) ? lv : 0.f, h[n], s2);
+    }
+    const float rs = 1.0f / s2;
+#pragma unroll
+    for (int n = 0; n < kMwfWMaxN; ++n)
+      if (n < N) sG[tl][n][m] = sL[m * N + n] * h[n] * rs;
+  }
+  __syncthreads();
+  const int total = nt * N * M;
+  float2* dst = c + ((size_t)f * T + t0) * N * M;
+  for (int o = tid; o < total; o += kMwfWThreads) {
+    const int tl = o / (N * M), rem = o - tl * (N * M);
+    const int n = rem / M, a = rem - (rem / M) * M;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const float g = sG[tl][n][m];
+      const float2 z = make_float2(g * sY[tl][m].x, g * sY[tl][m].y);
+      acc = cfmaf(sWi[a * M + m], z, acc);
+    }
+    dst[o] = acc;
+  }
+}
+
 }  // namespace ffca

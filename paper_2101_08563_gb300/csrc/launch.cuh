@@ -1,6 +1,7 @@
 // Host-side launchers for one (M, N) specialisation of the FastFCA kernels.
 #pragma once
 #include "fastfca_em.cuh"
+#include "fastfca_em_cluster.cuh"
 #include "fastfca_mwf.cuh"
 
 namespace ffca {
@@ -9,13 +10,14 @@ struct FastOps {
   cudaError_t (*em)(const EmArgs& a, cudaStream_t s);
   cudaError_t (*winv)(const double2* P, float2* WmH, int F, int* err, cudaStream_t s);
   cudaError_t (*mwf)(const float2* x, const double2* P, const float2* WmH, const float* lam,
-                     const float* v, float2* c, int F, int T, cudaStream_t s);
+                     const float* v, float2* c, int F, int T, int N, cudaStream_t s);
   // persistent batch form: items in device memory, `bd` threads per CTA, `grid` CTAs
   cudaError_t (*em_persistent)(const EmItem* items, int n_items, int n_iter, int* counter, int* err, int bd,
                                int grid, cudaStream_t s);
   size_t (*em_smem)(int bd);
   int (*em_blocks_per_sm)(int bd);
   int max_T;
+  bool cluster;          // the cluster kernel (any T it fits, runtime N); no batch form
 };
 
 // Threads for a frequency of T frames: whole warps, kSlots frames each.
@@ -74,7 +76,7 @@ cudaError_t launch_winv(const double2* P, float2* WmH, int F, int* err, cudaStre
 
 template <int M, int N>
 cudaError_t launch_mwf(const float2* x, const double2* P, const float2* WmH, const float* lam,
-                       const float* v, float2* c, int F, int T, cudaStream_t s) {
+                       const float* v, float2* c, int F, int T, int /*N*/, cudaStream_t s) {
   dim3 grid(F, (T + kMwfThreads - 1) / kMwfThreads);
   fastfca_mwf_kernel<M, N><<<grid, kMwfThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T);
   return cudaGetLastError();
@@ -90,6 +92,75 @@ FastOps make_fast_ops() {
   o.em_smem = &em_smem_bytes<M, N>;
   o.em_blocks_per_sm = &em_blocks_per_sm<M, N>;
   o.max_T = kMaxThreads * kSlots;
+  o.cluster = false;
+  return o;
+}
+
+// ---------------------------------------------------------------- cluster kernel (large bins)
+// Shared memory available to one CTA, alone on an SM or as one of two.
+constexpr size_t kSmemOnePerSm = 227 * 1024;
+constexpr size_t kSmemTwoPerSm = 113 * 1024;
+
+// Cluster size C for T frames and N sources: the smallest C in {1, 2, 4, 8} (with C <= T)
+// whose CTAs fit two per SM, else the smallest that fits one per SM.  False if none fits.
+template <int M>
+bool cluster_shape(int T, int N, int* C, size_t* smem) {
+  if (N < 1 || N > kCMaxN || T < 1) return false;
+  for (size_t cap : {kSmemTwoPerSm, kSmemOnePerSm}) {
+    for (int c = 1; c <= kCMaxCluster; c *= 2) {
+      const int Tc = (T + c - 1) / c;
+      if ((c - 1) * Tc >= T) break;                  // every CTA must own a frame
+      const size_t b = ClusterSmem<M>::bytes(N, Tc);
+      if (b <= cap) { *C = c; *smem = b; return true; }
+    }
+  }
+  return false;
+}
+
+template <int M>
+cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
+  int C = 0;
+  size_t smem = 0;
+  if (!cluster_shape<M>(a.T, a.N, &C, &smem)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_cluster_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.F * C), 1, 1);
+  cfg.blockDim = dim3(kCThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M>, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
+                            float2* c, int F, int T, int N, cudaStream_t s) {
+  if (N < 1 || N > kMwfWMaxN) return cudaErrorInvalidValue;
+  dim3 grid(F, (T + kMwfWFrames - 1) / kMwfWFrames);
+  fastfca_mwf_wide_kernel<M><<<grid, kMwfWThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T, N);
+  return cudaGetLastError();
+}
+
+template <int M>
+FastOps make_cluster_ops() {
+  FastOps o{};
+  o.em = &launch_em_cluster<M>;
+  o.winv = &launch_winv<M>;
+  o.mwf = &launch_mwf_wide<M>;
+  o.em_persistent = nullptr;
+  o.em_smem = nullptr;
+  o.em_blocks_per_sm = nullptr;
+  o.max_T = 0;                     // set by cluster_ops for the N at hand
+  o.cluster = true;
   return o;
 }
 
@@ -100,6 +171,8 @@ void set_thread_error(const char* msg);
 bool fast_ops_m2(int N, FastOps* o);
 bool fast_ops_m3(int N, FastOps* o);
 bool fast_ops_m4(int N, FastOps* o);
+// Cluster-kernel ops for M in 2..8 and N in 1..kCMaxN when T frames fit (fastfca_cluster_*.cu).
+bool cluster_ops(int M, int N, int T, FastOps* o);
 
 inline bool fast_ops(int M, int N, FastOps* o) {
   switch (M) {
@@ -108,6 +181,14 @@ inline bool fast_ops(int M, int N, FastOps* o) {
     case 4: return fast_ops_m4(N, o);
     default: return false;
   }
+}
+
+// The kernels for one FastFCA problem: the frequency-resident kernel where it applies
+// (M <= 4, N <= 8, T <= 2048), else the cluster kernel (M <= 8, N <= 16, T up to what eight
+// CTAs hold).
+inline bool fast_ops_for(int M, int N, int T, FastOps* o) {
+  if (fast_ops(M, N, o) && T <= o->max_T) return true;
+  return cluster_ops(M, N, T, o);
 }
 
 }  // namespace ffca

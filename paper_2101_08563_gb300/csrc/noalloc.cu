@@ -53,7 +53,8 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
                                                    const float* v, void* c, void* stream) {
   if (F < 1 || T < 1 || M < 1 || N < 1) return noalloc_fail(FASTFCA_EINVAL, "F, T, M, N must be positive");
   ffca::FastOps ops{};
-  if (!ffca::fast_ops(M, N, &ops)) return noalloc_fail(FASTFCA_EUNSUPPORTED, "no kernel for this (M, N)");
+  if (!ffca::fast_ops(M, N, &ops) && !ffca::cluster_ops(M, N, T, &ops))
+    return noalloc_fail(FASTFCA_EUNSUPPORTED, "no kernel for this (M, N)");
   if ((long long)F * M * M > kNoAllocMaxWinv) {
     char msg[256];
     snprintf(msg, sizeof msg, "F*M*M = %lld exceeds the %d complex values of the static scratch",
@@ -91,7 +92,7 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
   cudaError_t e = ops.winv(static_cast<const double2*>(P), winv, F, status, s);
   if (e == cudaSuccess)
     e = ops.mwf(static_cast<const float2*>(x), static_cast<const double2*>(P), winv, lam, v,
-                static_cast<float2*>(c), F, T, s);
+                static_cast<float2*>(c), F, T, N, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(FASTFCA_ECUDA, cudaGetErrorString(e));

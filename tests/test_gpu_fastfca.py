@@ -174,12 +174,12 @@ def test_host_buffers_match_device_buffers(ff):
 
 
 def test_errors_are_reported(ff):
-    x = torch.zeros((2, 10, 5), dtype=torch.complex64, device="cuda")
+    x = torch.zeros((2, 10, 9), dtype=torch.complex64, device="cuda")
     with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
-        ff.Separator(x, 3)                    # M = 5 has no kernel
-    x = torch.zeros((2, 5000, 2), dtype=torch.complex64, device="cuda")
+        ff.Separator(x, 3)                    # M = 9 has no kernel
+    x = torch.zeros((1, 60000, 2), dtype=torch.complex64, device="cuda")
     with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
-        ff.Separator(x, 3)                    # T beyond one CTA
+        ff.Separator(x, 3)                    # T beyond what eight CTAs hold
     mix = synth.generate_mixture(2, 3, 3, 64, 4, seed=1)
     init = synth.random_init(mix.x, 3, seed=1)
     sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 3)
