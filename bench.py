@@ -388,13 +388,14 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
-def run_profile_case(F, iters):
-    """The bench workload's first 8 frequencies tiled to F (so the launch has F CTAs of the
-    bench's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`."""
+def run_profile_case(F, iters, workload="fca_cmp"):
+    """A workload's first 8 frequencies tiled to F (so the launch has F frequencies of the
+    workload's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`."""
     import torch
     from paper_2101_08563_gb300 import build, fastfca
-    w = WORKLOAD
-    mix = synth.generate_mixture(w.M, w.N, 8, w.T, w.K, seed=w.seed)
+    w = synth.WORKLOADS[workload]
+    mix = synth.generate_mixture(w.M, w.N, 8, w.T, w.K, seed=w.seed, array=w.array, spacing=w.spacing,
+                                 keep_images=False)
     x = np.tile(mix.x, (F // 8 + 1, 1, 1))[:F].copy()
     init = synth.random_init(x, w.N, seed=w.seed)
     build.build()
@@ -455,6 +456,7 @@ def main():
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
     ap.add_argument("--profile-F", type=int, default=608)
     ap.add_argument("--profile-iters", type=int, default=5)
+    ap.add_argument("--profile-workload", default="fca_cmp", choices=["fca_cmp", "large"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -469,7 +471,7 @@ def main():
               "l2": "flushed between steps (512 MiB write, untimed)"}
 
     if args.profile:
-        run_profile_case(args.profile_F, args.profile_iters)
+        run_profile_case(args.profile_F, args.profile_iters, args.profile_workload)
         return
 
     if args.impl == "reference":

@@ -73,6 +73,12 @@ __device__ __forceinline__ double ld_dsmem_f64(uint32_t addr) {
   return v;
 }
 
+__device__ __forceinline__ float ld_dsmem_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ double2 ld_dsmem_f64x2(uint32_t addr) {
   double2 v;
   asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
@@ -87,7 +93,7 @@ template <int M>
 struct ClusterSmem {
   static constexpr int NE = M * M;                        // packed Hermitian entries of Q_m
   static constexpr int V = M * NE;                        // reals of all Q_m
-  static constexpr int kXV = V + 1;                       // exchange: Q entries + log-lik
+  static constexpr int kXV = (V > kCWarps * 8 ? V : kCWarps * 8) + 4;   // float exchange row
   static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
   static constexpr int kWcPad = (M * M + 1) & ~1;
   // byte offsets (all multiples of 16)
@@ -97,8 +103,9 @@ struct ClusterSmem {
   static constexpr size_t oV = oQ + 16 * (size_t)kQsz;                    // double2 8 (w_raw)
   static constexpr size_t oBeta = oV + 16 * 8;                            // double2 8
   static constexpr size_t oDet = oBeta + 16 * 8;                          // double 4
-  static constexpr size_t oX = oDet + 32;                                 // double 2 x kXV
-  static constexpr size_t oWc = oX + ((8 * 2 * (size_t)kXV + 15) & ~(size_t)15);   // float2 kWcPad
+  static constexpr size_t oXll = oDet + 32;                               // double 2 (log-lik)
+  static constexpr size_t oX = oXll + 16;                                 // float 2 x kXV
+  static constexpr size_t oWc = oX + ((4 * 2 * (size_t)kXV + 15) & ~(size_t)15);   // float2 kWcPad
   static constexpr size_t oL = oWc + 8 * (size_t)kWcPad;                  // float M*kCMaxN
   static constexpr size_t oRed = oL + 4 * (size_t)M * kCMaxN;             // float kCWarps*8
   static constexpr size_t oLL = oRed + 4 * kCWarps * 8;                   // float kCWarps
@@ -111,22 +118,24 @@ struct ClusterSmem {
 
 // ------------------------------------------------------------------ FP64 pieces of the IP
 // In-place inverses of the Q_m (HPD, row-major, M*M each, at Q + m*M*M) for the m with
-// m % C == crank, by the four IP warps: slot i of the owned entries goes to thread
-// i % 128 (warp (i % 128) / 32), so every FP64 warp instruction of a step does up to 32 entries and
-// the four warps sit on the four sub-partitions.  Gauss-Jordan without pivoting (the pivots
-// of an HPD matrix are positive Schur complements); a non-positive pivot sets kErrQPivot.
+// m % C == crank, by the four IP warps.  Entry i of the owned entries goes to warp i % 4,
+// lane (i / 4) % 32, slot i / 128: the four warps sit on the four sub-partitions, and an FP64
+// warp instruction costs the same whatever its lane count, so spreading the entries over the
+// warps shortens each step.  Gauss-Jordan without pivoting (the pivots of an HPD matrix are
+// positive Schur complements); a non-positive pivot sets kErrQPivot.
 template <int M>
 __device__ void cluster_hpd_inverses(double2* Q, int crank, int C, int tid, int* err) {
   constexpr int E = M * M;
   constexpr int kMaxSlots = (M * E + kCIpThreads - 1) / kCIpThreads;   // all M matrices when C = 1
   const int owned = (crank < M) ? (M - 1 - crank) / C + 1 : 0;
   const int total = owned * E;
+  const int me = (tid & 31) * 4 + (tid >> 5);        // this thread's entry within a slot
   for (int k = 0; k < M; ++k) {
     double2 nv[kMaxSlots];
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < kMaxSlots; ++s) {
-      const int i = tid + s * kCIpThreads;
+      const int i = me + s * kCIpThreads;
       if (i < total) {
         const int mo = i / E, e = i - mo * E;
         double2* A = Q + (crank + mo * C) * E;
@@ -146,7 +155,7 @@ __device__ void cluster_hpd_inverses(double2* Q, int crank, int C, int tid, int*
     ip_bar();
 #pragma unroll
     for (int s = 0; s < kMaxSlots; ++s) {
-      const int i = tid + s * kCIpThreads;
+      const int i = me + s * kCIpThreads;
       if (i < total) {
         const int mo = i / E, e = i - mo * E;
         Q[(crank + mo * C) * E + e] = nv[s];
@@ -228,6 +237,19 @@ __device__ void cluster_ip_columns(const double2* Qi, double2* sW, double2* sB, 
   if (tid == 0) { sDet[0] = mant; sDet[1] = expo; }
 }
 
+// Phase timestamps (clock64) of frequency 0, rank 0, thread 0, for the first 8 iterations,
+// 32 slots each; compiled in only with -DFFCA_PHASE_CLOCKS (profiling builds).
+#ifdef FFCA_PHASE_CLOCKS
+#define FFCA_CMARK(it, slot)                                                                   \
+  do {                                                                                         \
+    if (p.clocks && f == 0 && crank == 0 && tid == 0 && (it) < 8) p.clocks[(it) * 32 + (slot)] = clock64(); \
+  } while (0)
+#else
+#define FFCA_CMARK(it, slot) \
+  do {                       \
+  } while (0)
+#endif
+
 // Packed Hermitian entry e of x x^H (the order of xxh_packed): e < M is |x_e|^2, then for
 // each pair a < b (row-major) Re(x_a conj x_b) and Im(x_a conj x_b).  kind 0 diagonal,
 // 1 real part, 2 imaginary part.
@@ -269,7 +291,8 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   double2* sV = reinterpret_cast<double2*>(smem + SM::oV);
   double2* sBeta = reinterpret_cast<double2*>(smem + SM::oBeta);
   double* sDet = reinterpret_cast<double*>(smem + SM::oDet);
-  double* sX = reinterpret_cast<double*>(smem + SM::oX);
+  double* sXll = reinterpret_cast<double*>(smem + SM::oXll);
+  float* sX = reinterpret_cast<float*>(smem + SM::oX);
   float2* sWc = reinterpret_cast<float2*>(smem + SM::oWc);
   float* sL = reinterpret_cast<float*>(smem + SM::oL);
   float* sRed = reinterpret_cast<float*>(smem + SM::oRed);
@@ -333,17 +356,24 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     }
   };
 
-  // U = |W^H x|^2 for this CTA's frames
+  // U = |W^H x|^2 for this CTA's frames, two frames per thread at a time (loads overlap)
   auto pass_U = [&]() {
-    for (int j = tid; j < Tl; j += kCThreads) {
-      float2 xv[M];
+    for (int j = tid; j < Tl; j += 2 * kCThreads) {
+      const int j2 = j + kCThreads;
+      float2 xv[M], xw[M];
       load_x(j, xv);
+      if (j2 < Tl) load_x(j2, xw);
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        float2 y = make_float2(0.f, 0.f);
+        float2 y = make_float2(0.f, 0.f), z = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xv[a], y);
+        for (int a = 0; a < M; ++a) {
+          const float2 wc = sWc[m * M + a];
+          y = cfmaf(wc, xv[a], y);
+          z = cfmaf(wc, xw[a], z);
+        }
         sU[m * Tcp + j] = fmaf(y.x, y.x, y.y * y.y);
+        if (j2 < Tl) sU[m * Tcp + j2] = fmaf(z.x, z.x, z.y * z.y);
       }
     }
   };
@@ -353,10 +383,15 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     return (double)T * logdet - s - (double)M * (double)T * kLnPi;
   };
 
-  // sum over the cluster, in rank order, of the value at this CTA's shared address `local`
+  // sums over the cluster, in rank order, of the value at this CTA's shared address `local`
   auto cluster_sum = [&](const double* local) {
     double s = 0.0;
     for (int c = 0; c < C; ++c) s += ld_dsmem_f64(dsmem_addr(local, (unsigned)c));
+    return s;
+  };
+  auto cluster_sum_f = [&](const float* local) {
+    float s = 0.f;
+    for (int c = 0; c < C; ++c) s += ld_dsmem_f32(dsmem_addr(local, (unsigned)c));
     return s;
   };
 
@@ -383,6 +418,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   for (int it = 0;; ++it) {
     const bool have_ll = (it > 0) || (p.n_iter == 0);
     const bool do_iter = it < p.n_iter;
+    FFCA_CMARK(it, 0);
 
     // ---- pass A: pending H[N-1,:] update, sigma^2 = L H, 1/sigma^2, log-likelihood terms
     {
@@ -418,46 +454,70 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       llp = warp_sum(llp);
       if (lane == 0) sLL[warp] = llp;
     }
-    double* xb = sX + par * XV;
+    __syncthreads();          // the Q pass reads 1/sigma^2 of frames other threads wrote
+    FFCA_CMARK(it, 1);
+    float* xb = sX + par * XV;
+    double* xll = sXll + par;
     if (!do_iter) {
       __syncthreads();
       if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < kCWarps; ++w) s += (double)sLL[w];
-        xb[V] = s;
+        *xll = s;
       }
       cluster_sync();
       if (crank == 0 && tid == 0) {
-        const double ll = ll_from_sum(cluster_sum(xb + V));
+        const double ll = ll_from_sum(cluster_sum(xll));
         if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
         if (p.ll_last) p.ll_last[f] = ll;
       }
       break;
     }
 
-    // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33): warp w takes frames j = w mod 8,
-    // lane l the entries l + 32 q, for every m
+    // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33).  Warp w takes a contiguous block of
+    // frames; one load instruction brings 4 frames x 8 channels (lane 8 f + a holds x_a of
+    // frame f), a batch of 32 frames is loaded before any of it is used, and lane l forms
+    // the Hermitian entries l + 32 q of every frame from shuffled channels, for every m
     {
       float acc[M][EPL];
 #pragma unroll
       for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int q = 0; q < EPL; ++q) acc[m][q] = 0.f;
-      for (int j = warp; j < Tl; j += kCWarps) {
-        const float2* xt = xf + (size_t)j * M;
-        float ev[EPL];
+      const int per = (Tl + kCWarps - 1) / kCWarps;
+      const int fb = warp * per, fe = min(fb + per, Tl);
+      const int lf = lane >> 3, la = lane & 7;
+      for (int base = fb; base < fe; base += 32) {
+        float2 xr[8];
 #pragma unroll
-        for (int q = 0; q < EPL; ++q) {
-          if (ek[q] == 3) { ev[q] = 0.f; continue; }
-          const float2 xa = __ldg(xt + ea[q]), xc = __ldg(xt + eb[q]);
-          ev[q] = (ek[q] == 0) ? fmaf(xa.x, xa.x, xa.y * xa.y)
-                  : (ek[q] == 1) ? fmaf(xa.x, xc.x, xa.y * xc.y) : fmaf(xa.y, xc.x, -xa.x * xc.y);
+        for (int k = 0; k < 8; ++k) {
+          const int fr = base + 4 * k + lf;
+          xr[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const float w = sR[m * Tcp + j];
+        for (int k = 0; k < 8; ++k) {
 #pragma unroll
-          for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+          for (int fi = 0; fi < 4; ++fi) {
+            const int fr = base + 4 * k + fi;          // warp-uniform
+            if (fr >= fe) break;
+            float ev[EPL];
+#pragma unroll
+            for (int q = 0; q < EPL; ++q) {
+              const float ax = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + ea[q]);
+              const float ay = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + ea[q]);
+              const float bx = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + eb[q]);
+              const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + eb[q]);
+              ev[q] = (ek[q] == 3) ? 0.f
+                      : (ek[q] == 0) ? fmaf(ax, ax, ay * ay)
+                      : (ek[q] == 1) ? fmaf(ax, bx, ay * by) : fmaf(ay, bx, -ax * by);
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              const float w = sR[m * Tcp + fr];
+#pragma unroll
+              for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+            }
+          }
         }
       }
 #pragma unroll
@@ -467,20 +527,21 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
           if (lane + 32 * q < NE) sQw[warp * V + m * NE + lane + 32 * q] = acc[m][q];
     }
     __syncthreads();
+    // FP32 sums over warps (in warp order) and CTAs (in rank order), one conversion per entry
     for (int i = tid; i < V; i += kCThreads) {
-      double s = 0.0;
+      float s = 0.f;
 #pragma unroll
-      for (int w = 0; w < kCWarps; ++w) s += (double)sQw[w * V + i];
+      for (int w = 0; w < kCWarps; ++w) s += sQw[w * V + i];
       xb[i] = s;
     }
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < kCWarps; ++w) s += (double)sLL[w];
-      xb[V] = s;
+      *xll = s;
     }
     cluster_sync();
     for (int i = tid; i < V; i += kCThreads) {
-      const double qd = cluster_sum(xb + i) * invT;
+      const double qd = (double)cluster_sum_f(xb + i) * invT;
       const int m = i / NE, e = i - m * NE;
       int a, b, kind;
       decode_entry<M>(e, a, b, kind);
@@ -490,26 +551,49 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
     }
     if (have_ll && crank == 0 && tid == 0 && p.ll_hist)
-      p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(cluster_sum(xb + V));
+      p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(cluster_sum(xll));
     par ^= 1;
     __syncthreads();
+    FFCA_CMARK(it, 2);
 
     // ---- IP (FP64): this CTA's share of the Q_m^{-1}, gathered over the cluster, then the
     // column loop (every CTA, identical inputs, identical results)
+    // ---- IP (FP64): each CTA inverts its share of the Q_m; rank 0 gathers them and runs
+    // the column loop; the other CTAs then copy W, B = W^{-H}, conj(W)^T and |det W|^2
     if (tid < kCIpThreads) cluster_hpd_inverses<M>(sQ, crank, C, tid, p.err);
     cluster_sync();
+    FFCA_CMARK(it, 3);
+    if (crank == 0) {
+      if (C > 1) {
+        for (int i = tid; i < M * M * M; i += kCThreads) {
+          const int owner = (i / (M * M)) % C;
+          if (owner != 0) sQ[i] = ld_dsmem_f64x2(dsmem_addr(sQ + i, (unsigned)owner));
+        }
+        __syncthreads();
+      }
+      if (tid < kCIpThreads) cluster_ip_columns<M>(sQ, sW, sB, sWc, sDet, sV, sBeta, tid, p.err);
+    }
     if (C > 1) {
-      for (int i = tid; i < M * M * M; i += kCThreads) {
-        const int owner = (i / (M * M)) % C;
-        if (owner != crank) sQ[i] = ld_dsmem_f64x2(dsmem_addr(sQ + i, (unsigned)owner));
+      cluster_sync();
+      if (crank != 0) {
+        for (int i = tid; i < M * M; i += kCThreads) {
+          sW[i] = ld_dsmem_f64x2(dsmem_addr(sW + i, 0u));
+          sB[i] = ld_dsmem_f64x2(dsmem_addr(sB + i, 0u));
+        }
+        double2* wc2 = reinterpret_cast<double2*>(sWc);       // kWcPad float2 = kWcPad/2 x 16 B
+        for (int i = tid; i < SM::kWcPad / 2; i += kCThreads) wc2[i] = ld_dsmem_f64x2(dsmem_addr(wc2 + i, 0u));
+        if (tid == 0) {
+          sDet[0] = ld_dsmem_f64(dsmem_addr(sDet, 0u));
+          sDet[1] = ld_dsmem_f64(dsmem_addr(sDet + 1, 0u));
+        }
       }
     }
     __syncthreads();
-    if (tid < kCIpThreads) cluster_ip_columns<M>(sQ, sW, sB, sWc, sDet, sV, sBeta, tid, p.err);
-    __syncthreads();
 
+    FFCA_CMARK(it, 4);
     // ---- U = |W^H x|^2 (Eq. 37); each thread later reads only its own frames
     pass_U();
+    FFCA_CMARK(it, 5);
 
     // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's
     // H update and its change of sigma^2
@@ -547,27 +631,35 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
           acc[m] += rr;
         }
       }
+      // per-warp sums go straight to the exchange row (warp w, value m at w*8 + m); after the
+      // barrier lane (m, q) adds the rows of warps 2q, 2q+1 of every CTA (rank order), and
+      // two shuffles finish: the same order in every warp of every CTA
       warp_reduce_scatter<MP>(acc, lane);
-      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) sRed[warp * 8 + (lane * MP) / 32] = acc[0];
-      __syncthreads();
-      double* xn = sX + par * XV;
-      if (tid < M) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kCWarps; ++w) s += (double)sRed[w * 8 + tid];
-        xn[tid] = s;
-      }
+      float* xn = sX + par * XV;
+      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) xn[warp * 8 + (lane * MP) / 32] = acc[0];
       cluster_sync();
-      const double tot_l = (lane < M) ? cluster_sum(xn + lane) : 0.0;
+      float tot_l = 0.f;
+      {
+        const int m = lane >> 2, q = lane & 3;
+        if (m < M) {
+          for (int c = 0; c < C; ++c) {
+            tot_l += ld_dsmem_f32(dsmem_addr(xn + (2 * q) * 8 + m, (unsigned)c));
+            tot_l += ld_dsmem_f32(dsmem_addr(xn + (2 * q + 1) * 8 + m, (unsigned)c));
+          }
+        }
+        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 1);
+        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 2);
+      }
       par ^= 1;
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        const float mean = (float)__shfl_sync(0xffffffffu, tot_l, m) * invTf;
+        const float mean = __shfl_sync(0xffffffffu, tot_l, 4 * m) * invTf;
         Lold[m] = Ln[m];
         Lnew[m] = Ln[m] * mean;
         sL[m * N + n] = Lnew[m];           // the same value from every thread
         coef[m] = fast_rcp(mean) * (1.0f / (float)M);
       }
+      FFCA_CMARK(it, 6 + (n < 25 ? n : 25));
     }
   }
 
