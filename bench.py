@@ -269,6 +269,48 @@ def run_learned(n_train):
     return res
 
 
+def precision_report():
+    """Error of every output of the CUDA path against the FP64 oracle from the same start:
+    the whole small workload (M=2, N=3, F=257, T=250, 20 iterations) and four frequencies of
+    the bench workload (100 iterations).  Images c and log-likelihood per iteration are
+    compared directly; the parameters through W (fixed scale: the IP normalises it) and the
+    scale-free sigma^2 = LH and per-source powers L[:, n] H[n, :]."""
+    import torch
+    from oracle import fastfca as off
+    from paper_2101_08563_gb300 import fastfca
+    out = {}
+    for name, freqs in (("small", None), ("fca_cmp", [3, 130, 257, 511])):
+        w = synth.WORKLOADS[name]
+        mix = synth.workload_mixture(w)
+        init = synth.random_init(mix.x, w.N, seed=w.seed)
+        fs = list(range(w.F)) if freqs is None else freqs
+        x = np.ascontiguousarray(mix.x[fs])
+        sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N)
+        sep.set_params(np.ascontiguousarray(init.P[fs]), np.ascontiguousarray(init.lam[fs]),
+                       np.ascontiguousarray(init.v[fs]))
+        ll = sep.iterate(w.iters)
+        c = sep.separate()
+        P, lam, v = sep.get_params()
+        sep.close()
+        ref = off.run(x, init.P[fs], init.lam[fs], init.v[fs], iters=w.iters)
+        ll_ref = ref["ll"].sum(axis=0)
+        cr = np.stack([off.separate_fast(x[i], ref["W"][i], ref["L"][i], ref["H"][i]) for i in range(len(fs))])
+        s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
+        s2r = np.einsum("fmn,fnt->fmt", ref["L"], ref["H"])
+        pw = lam.astype(np.float64)[:, :, :, None] * v.astype(np.float64)[:, None, :, :]
+        pwr = ref["L"][:, :, :, None] * ref["H"][:, None, :, :]
+        out[name] = {
+            "frequencies": "all" if freqs is None else freqs, "iters": w.iters,
+            "loglik_rel_err_max": float(np.max(np.abs(ll - ll_ref) / np.abs(ll_ref))),
+            "images_rel_err": float(np.linalg.norm(c - cr) / np.linalg.norm(cr)),
+            "W_rel_err": float(np.max(np.abs(P - ref["W"])) / np.max(np.abs(ref["W"]))),
+            "sigma2_rel_err_max": float(np.max(np.abs(s2 - s2r) / s2r)),
+            "source_power_rel_err_median": float(np.median(np.abs(pw - pwr) / pwr)),
+            "tolerance": {"loglik": 1e-5, "images": 1e-4},
+        }
+    return out
+
+
 def load_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -450,6 +492,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--learned-mixtures", type=int, default=20000)
     ap.add_argument("--profile", action="store_true",
                     help="only run the IP+EM kernel on the bench mixture's first frequencies tiled to "
@@ -525,6 +568,9 @@ def main():
     learned = None
     if rank == 0 and not args.no_learned:
         learned = run_learned(args.learned_mixtures)
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = precision_report()
     if rank != 0:
         return
     peaks = load_peaks()
@@ -555,6 +601,8 @@ def main():
         out["batch"] = batch
     if learned is not None:
         out["learned_init"] = learned
+    if precision is not None:
+        out["precision"] = precision
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out))
