@@ -269,6 +269,54 @@ def run_learned(n_train):
     return res
 
 
+def run_large(peaks):
+    """The large single instance (M=8 circular, N=12, F=1025, T=4000, K=16, 50 iterations)
+    on the cluster kernel: IP+EM launch throughput (event-timed, L2 flushed between steps)
+    and the Wiener separation's HBM bandwidth (x and v read, 3.15 GB of images written)."""
+    import torch
+    from paper_2101_08563_gb300 import fastfca
+    w = synth.WORKLOADS["large"]
+    mix = synth.workload_mixture(w)
+    init = synth.random_init(mix.x, w.N, seed=w.seed)
+    x = torch.from_numpy(mix.x).cuda()
+    P0, lam0, v0 = (torch.from_numpy(a).cuda() for a in (init.P, init.lam, init.v))
+    c = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sep = fastfca.Separator(x, w.N)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    em_ms, mwf_ms = [], []
+    for rep in range(4):
+        sep.set_params(P0, lam0, v0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev[0].record()
+        sep.iterate(w.iters, return_ll=False)
+        ev[1].record()
+        sep.separate(c)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if rep > 0:                                   # the first is a warm-up
+            em_ms.append(ev[0].elapsed_time(ev[1]))
+            mwf_ms.append(ev[1].elapsed_time(ev[2]))
+    sep.close()
+    em = statistics.mean(em_ms)
+    mwf = statistics.mean(mwf_ms)
+    flops = algorithmic_flops_per_bin_iter(w.M, w.N) * w.F * w.T * w.iters
+    mwf_bytes = x.numel() * 8 + v0.numel() * 4 + c.numel() * 8
+    hbm = peaks.get("hbm_gbs")
+    return {
+        "workload": w.name, "metric": METRIC, "value": w.F * w.T * w.iters / (em * 1e-3), "unit": UNIT,
+        "iters": w.iters, "em_launch_ms": em, "kernel": "fastfca_em_cluster_kernel<8> (clusters of 8 CTAs)",
+        "roofline": {"bound": "alu", "achieved": flops / (em * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flops / (em * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "flops_per_bin_iter": algorithmic_flops_per_bin_iter(w.M, w.N)},
+        "separation": {"kernel": "fastfca_mwf_wide_kernel<8>", "ms": mwf, "bytes": mwf_bytes,
+                       "achieved_gbs": mwf_bytes / (mwf * 1e-3) / 1e9,
+                       "frac_of_measured_hbm": (mwf_bytes / (mwf * 1e-3) / 1e9 / hbm) if hbm else None},
+        "l2": "flushed before each step (512 MiB write, untimed)",
+    }
+
+
 def precision_report():
     """Error of every output of the CUDA path against the FP64 oracle from the same start:
     the whole small workload (M=2, N=3, F=257, T=250, 20 iterations) and four frequencies of
@@ -493,6 +541,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--learned-mixtures", type=int, default=20000)
     ap.add_argument("--profile", action="store_true",
                     help="only run the IP+EM kernel on the bench mixture's first frequencies tiled to "
@@ -571,6 +620,9 @@ def main():
     precision = None
     if rank == 0 and world == 1 and not args.no_precision:
         precision = precision_report()
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        large = run_large(load_peaks())
     if rank != 0:
         return
     peaks = load_peaks()
@@ -603,6 +655,8 @@ def main():
         out["learned_init"] = learned
     if precision is not None:
         out["precision"] = precision
+    if large is not None:
+        out["large"] = large
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out))

@@ -109,71 +109,78 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
   }
 }
 
-// Wide form of the filter for large bins (any M <= 8, runtime N <= kMwfWMaxN): phase 1 forms
-// y = W^H x_t and the gains g_mn(t) of kMwfWFrames frames in shared memory, one thread per
-// (frame, m); phase 2 writes the CTA's output span (frames t0.. t0+nt, all n, all a) in memory
-// order, one complex value per thread and step, so the stores coalesce.
+// Wide form of the filter for large bins (any M <= 8, runtime N <= kMwfWMaxN).  A CTA of
+// M x 32 threads takes kMwfWFrames frames.  Phase 1 (thread per (frame, m)) forms
+// z_nm(t) = g_nm(t) y_m(t) for every source in shared memory.  Phase 2 gives thread
+// (task slot s, row a) = (tid / M, tid % M) the fixed row a of W^{-H}, held in registers, and
+// walks the tasks (frame, n) s, s + 32, ...: each output c_tn[a] = sum_m W^{-H}[a][m] z_nm(t)
+// reads only the M values of z of its task (shared by the M threads of the task), and
+// consecutive threads write consecutive complex values of the output span (coalesced).
+// Rows of sZ are padded to M + 1 values so that the tasks of a warp fall in distinct banks.
 constexpr int kMwfWFrames = 32;
-constexpr int kMwfWThreads = 256;
 constexpr int kMwfWMaxN = 16;
 
 template <int M>
-__global__ void __launch_bounds__(kMwfWThreads) fastfca_mwf_wide_kernel(
+__global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
     const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
     const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int N) {
-  __shared__ float2 sWc[M * M];                  // conj(W[a][m]) at [m*M + a]
-  __shared__ float2 sWi[M * M];                  // W^{-H}[a][m] at [a*M + m]
+  constexpr int kThreads = M * 32;
+  __shared__ float2 sWc[M * M];                                   // conj(W[a][m]) at [m*M + a]
   __shared__ float sL[M * kMwfWMaxN];
-  __shared__ float2 sY[kMwfWFrames][M];
-  __shared__ float sG[kMwfWFrames][kMwfWMaxN][M];
+  __shared__ float2 sZ[kMwfWFrames * kMwfWMaxN * (M + 1)];        // [(tl*N + n)][m], padded
   const int f = blockIdx.x, tid = threadIdx.x;
   const int t0 = blockIdx.y * kMwfWFrames;
   if (f >= F || t0 >= T || N > kMwfWMaxN) return;
   const int nt = min(kMwfWFrames, T - t0);
-  for (int e = tid; e < M * M; e += kMwfWThreads) {
+  for (int e = tid; e < M * M; e += kThreads) {
     const int a = e / M, m = e - (e / M) * M;
     const double2 w = P[(size_t)f * M * M + e];
     sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
-    sWi[e] = WmH[(size_t)f * M * M + e];
   }
-  for (int e = tid; e < M * N; e += kMwfWThreads) sL[e] = lam[(size_t)f * M * N + e];
+  for (int e = tid; e < M * N; e += kThreads) sL[e] = lam[(size_t)f * M * N + e];
+  // this thread's row of W^{-H}
+  const int a_row = tid % M, slot = tid / M;
+  float2 wi[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) wi[m] = WmH[(size_t)f * M * M + a_row * M + m];
   __syncthreads();
-  if (tid < nt * M) {
+  // phase 1: thread (tl, m) for tl < nt (32 frames x M rows = the CTA)
+  {
     const int tl = tid / M, m = tid - (tid / M) * M;
-    const int t = t0 + tl;
-    const float2* xt = x + ((size_t)f * T + t) * M;
-    float2 y = make_float2(0.f, 0.f);
+    if (tl < nt) {
+      const int t = t0 + tl;
+      const float2* xt = x + ((size_t)f * T + t) * M;
+      float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xt[a], y);
-    sY[tl][m] = y;
-    float h[kMwfWMaxN];
-    float s2 = 0.f;
+      for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xt[a], y);
+      float h[kMwfWMaxN];
+      float s2 = 0.f;
 #pragma unroll
-    for (int n = 0; n < kMwfWMaxN; ++n) {
-      const int nn = (n < N) ? n : 0;                  // index kept inside the arrays
-      const float hv = v[((size_t)f * N + nn) * T + t], lv = sL[m * N + nn];
-      h[n] = (n < N) ? hv : 0.f;
-      s2 = fmaf((n < N) ? lv : 0.f, h[n], s2);
+      for (int n = 0; n < kMwfWMaxN; ++n) {
+        const int nn = (n < N) ? n : 0;                  // index kept inside the arrays
+        const float hv = v[((size_t)f * N + nn) * T + t], lv = sL[m * N + nn];
+        h[n] = (n < N) ? hv : 0.f;
+        s2 = fmaf((n < N) ? lv : 0.f, h[n], s2);
+      }
+      const float rs = 1.0f / s2;
+#pragma unroll
+      for (int n = 0; n < kMwfWMaxN; ++n)
+        if (n < N) {
+          const float g = sL[m * N + n] * h[n] * rs;
+          sZ[(tl * N + n) * (M + 1) + m] = make_float2(g * y.x, g * y.y);
+        }
     }
-    const float rs = 1.0f / s2;
-#pragma unroll
-    for (int n = 0; n < kMwfWMaxN; ++n)
-      if (n < N) sG[tl][n][m] = sL[m * N + n] * h[n] * rs;
   }
   __syncthreads();
-  const int total = nt * N * M;
+  // phase 2: outputs in memory order, task-major (task = tl*N + n), row a minor
+  const int tasks = nt * N;
   float2* dst = c + ((size_t)f * T + t0) * N * M;
-  for (int o = tid; o < total; o += kMwfWThreads) {
-    const int tl = o / (N * M), rem = o - tl * (N * M);
-    const int n = rem / M, a = rem - (rem / M) * M;
+  for (int task = slot; task < tasks; task += 32) {
+    const float2* z = sZ + task * (M + 1);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const float g = sG[tl][n][m];
-      const float2 z = make_float2(g * sY[tl][m].x, g * sY[tl][m].y);
-      acc = cfmaf(sWi[a * M + m], z, acc);
-    }
-    dst[o] = acc;
+    for (int m = 0; m < M; ++m) acc = cfmaf(wi[m], z[m], acc);
+    dst[(size_t)task * M + a_row] = acc;
   }
 }
 

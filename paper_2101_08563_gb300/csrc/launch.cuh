@@ -146,7 +146,7 @@ cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH
                             float2* c, int F, int T, int N, cudaStream_t s) {
   if (N < 1 || N > kMwfWMaxN) return cudaErrorInvalidValue;
   dim3 grid(F, (T + kMwfWFrames - 1) / kMwfWFrames);
-  fastfca_mwf_wide_kernel<M><<<grid, kMwfWThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T, N);
+  fastfca_mwf_wide_kernel<M><<<grid, M * 32, 0, s>>>(x, P, WmH, lam, v, c, F, T, N);
   return cudaGetLastError();
 }
 
