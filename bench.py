@@ -269,6 +269,22 @@ def run_learned(n_train):
     return res
 
 
+def separation_roofline(w, sep_ms, peaks):
+    """The Wiener separation (W^{-H} per frequency + Eq. 39 filter) of one step as an HBM-bound
+    kernel: algorithmic bytes x (8 M) + v (4 N) read and c (8 N M) written per bin, over its
+    event-timed span inside the step (it follows the IP+EM launch, so x and v may still be
+    partly in L2)."""
+    per_bin = 8 * w.M + 4 * w.N + 8 * w.N * w.M
+    bytes_ = per_bin * w.F * w.T
+    ms = statistics.mean(sep_ms)
+    hbm = peaks.get("hbm_gbs")
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "winv_kernel + fastfca_mwf_kernel", "achieved": gbs,
+            "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
+            "bytes_per_bin": per_bin, "ms": ms,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
 def run_large(peaks):
     """The large single instance (M=8 circular, N=12, F=1025, T=4000, K=16, 50 iterations)
     on the cluster kernel: IP+EM launch throughput (event-timed, L2 flushed between steps)
@@ -417,6 +433,7 @@ def run_gpu(args, rank, world, local_rank):
     clock_info = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     em_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
+    sep_ms = [m.elapsed_time(e) for m, e in zip(mids, ends)]
     tot_ms = sum(step_ms)
     tot_ms = allreduce_max(tot_ms, world, dev)
     # the set_params copies are outside the event spans; one step is iterate + separate
@@ -442,39 +459,51 @@ def run_gpu(args, rank, world, local_rank):
     fca_ms = f0.elapsed_time(f1)
     fsep.close()
 
-    # end-to-end through the public API with host buffers (pinned), copies inside the span
+    # end-to-end through the public API with host buffers (pinned), copies inside the span:
+    # every step uploads its mixture and start, runs the iterations (reading back the
+    # log-likelihood per iteration) and downloads the images.  Two long-lived contexts on two
+    # streams take the steps in turn, so one step's copies overlap the other's kernels.
     x_h = torch.from_numpy(mix.x).pin_memory()
     P_h = torch.from_numpy(init.P).pin_memory()
     lam_h = torch.from_numpy(init.lam).pin_memory()
     v_h = torch.from_numpy(init.v).pin_memory()
-    c_h = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
+    c_hs = [torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64).pin_memory() for _ in range(2)]
+    ll_hs = [torch.empty(w.iters, dtype=torch.float64).pin_memory() for _ in range(2)]
+    e2e_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    ctxs = [fastfca.Separator(x_h, w.N, stream=st.cuda_stream) for st in e2e_streams]
+    e2e_steps = max(4, min(args.steps, 10))
 
-    def e2e_step():
-        s = fastfca.Separator(x_h, w.N, stream=stream.cuda_stream)
+    def e2e_step(i):
+        s = ctxs[i % 2]
+        s.sync()                         # this context's previous step has landed on the host
+        s.set_mixture(x_h)
         s.set_params(P_h, lam_h, v_h)
-        ll = s.iterate(w.iters, return_ll=True)
-        s.separate(c_h)
-        s.close()
-        return ll
+        s.iterate_async(w.iters, ll_hs[i % 2])
+        s.separate_async(c_hs[i % 2])
+        return ll_hs[i % 2]
 
-    e2e_step()
-    torch.cuda.synchronize()
+    e2e_step(0)
+    e2e_step(1)
+    for s_ in ctxs:
+        s_.sync()
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ll = e2e_step()
-    torch.cuda.synchronize()
+    for i in range(e2e_steps):
+        ll = e2e_step(i)
+    for s_ in ctxs:
+        s_.sync()
     e2e_s = time.perf_counter() - t0
     e2e_s = allreduce_max(e2e_s, world, dev)
     h2d = mix.x.nbytes + init.P.nbytes + init.lam.nbytes + init.v.nbytes
-    d2h = c_h.numel() * 8 + w.iters * 8
+    d2h = c_hs[0].numel() * 8 + w.iters * 8
+    for s_ in ctxs:
+        s_.close()
     sep.close()
     return {
-        "value": value, "ms_per_step": tot_ms / args.steps, "em_ms": em_ms, "step_ms": step_ms,
+        "value": value, "ms_per_step": tot_ms / args.steps, "em_ms": em_ms, "step_ms": step_ms, "sep_ms": sep_ms,
         "clocks": clock_info, "fca_ms": fca_ms, "fca_iters": fca_iters,
         "e2e_value": world * units * e2e_steps / e2e_s, "h2d": h2d, "d2h": d2h,
-        "final_ll": float(ll[-1]),
+        "final_ll": float(ll[-1].item() if hasattr(ll[-1], "item") else ll[-1]),
     }
 
 
@@ -640,6 +669,7 @@ def main():
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "fastfca_em_kernel", "flops_per_bin_iter": algorithmic_flops_per_bin_iter(w.M, w.N),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
+        "roofline_separation": separation_roofline(w, r["sep_ms"], peaks),
         "clocks": r["clocks"],
         "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},

@@ -107,10 +107,13 @@ fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h);
 
 /* Runs n_iter iterations of the model's algorithm on every frequency: FastFCA IP+EM
  * (Algorithm 1, Sec. IV-E) or FCA EM (Eq. 12-13).  n_iter >= 1.  If ll_per_iter is not
- * NULL it receives (host) the total log-likelihood sum_f l_f after each iteration,
+ * NULL (host or device, n_iter doubles) it receives the total log-likelihood sum_f l_f
+ * after each iteration,
  * l_f = T ln|det W_f|^2 - sum_{m,t} (|y_mt|^2 / sigma^2_mt + ln sigma^2_mt) - M T ln(pi)
- * (Eq. 31 negated, with its constant); the call then synchronises.  Otherwise it is
- * asynchronous. */
+ * (Eq. 31 negated, with its constant).  Stream-ordered and asynchronous: a host
+ * ll_per_iter (pinned for a truly asynchronous copy) is complete once the context's stream
+ * has passed the call, e.g. after fastfca_sync, which also reports the kernels' numerical
+ * status (ENUMERIC). */
 fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_iter);
 
 /* Log-likelihood of the current parameters: *ll_total (host, may be NULL) = sum_f l_f and
@@ -119,8 +122,19 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
 
 /* Source images by the multichannel Wiener filter of the current parameters: FastFCA
  * Eq. 39 (c = W^{-H} diag(g_n) W^H x), FCA Eq. 7 (c = h_n R_n X^{-1} x).  c is complex64
- * [F][T][N][M], host or device, caller-allocated.  Asynchronous for a device c. */
+ * [F][T][N][M], host or device, caller-allocated.  Stream-ordered and asynchronous for both:
+ * a host c (pinned for a truly asynchronous copy) holds the images once the context's
+ * stream has passed the call, e.g. after fastfca_sync, which also reports any kernel
+ * status of the filter. */
 fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c);
+
+/* Replaces the mixture of a context with another of the same shape (complex64 [F][T][M],
+ * host or device), for running many mixtures through one context without reallocating.
+ * The data is copied, stream-ordered, into a buffer the context owns (allocated on the
+ * first call when the context was created on a borrowed device mixture); the caller may
+ * reuse x once the stream has passed the copy.  The parameters are left as they are.
+ * Sec. II: the input of the method is the mixture x and N. */
+fastfca_status fastfca_set_mixture(fastfca_ctx* ctx, const void* x);
 
 /* Waits for the context's stream and reports kernel-side numerical errors. */
 fastfca_status fastfca_sync(fastfca_ctx* ctx);

@@ -128,6 +128,13 @@ fastfca_status collect_device_status(fastfca_ctx* c) {
               bits);
 }
 
+// W^{-H} for the filter from the FP64 inverse the IP keeps (B = W^{-H}, maintained by
+// rank-one updates), rounded to complex64: replaces a fresh pivoted inversion when B is current.
+__global__ void bst_to_winv_kernel(const double2* __restrict__ B, float2* __restrict__ WmH, size_t n) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) WmH[i] = make_float2((float)B[i].x, (float)B[i].y);
+}
+
 __global__ void sum_over_f_kernel(const double* __restrict__ hist, int F, int stride, int n, double* __restrict__ out) {
   // one thread per column (iteration), fixed summation order over f
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,8 +380,10 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
   if (!ll_per_iter) return FASTFCA_OK;
   sum_over_f_kernel<<<(n_iter + 127) / 128, 128, 0, ctx->stream>>>(ctx->ll_hist, c.F, n_iter, n_iter, ctx->ll_sum);
   CK(ctx, cudaGetLastError(), "ll sum launch");
-  CK(ctx, cudaMemcpyAsync(ll_per_iter, ctx->ll_sum, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, ctx->stream), "ll download");
-  return collect_device_status(ctx);
+  // stream-ordered download; kernel status is collected by the next synchronising call
+  CK(ctx, cudaMemcpyAsync(ll_per_iter, ctx->ll_sum, sizeof(double) * n_iter, cudaMemcpyDefault, ctx->stream),
+     "ll download");
+  return FASTFCA_OK;
 }
 
 fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per_f) {
@@ -438,7 +447,13 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   }
   cudaError_t e;
   if (c.model == FASTFCA_MODEL_FASTFCA) {
-    e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
+    if (ctx->b_valid) {
+      const size_t n = (size_t)c.F * c.M * c.M;
+      bst_to_winv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->Bst, ctx->winv, n);
+      e = cudaGetLastError();
+    } else {
+      e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
+    }
     if (e == cudaSuccess) e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, c.T, c.N, ctx->stream);
   } else {
     e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
@@ -448,11 +463,23 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
     return cuda_fail(ctx, e, "separate launch");
   }
   if (!dev) {
+    // stream-ordered download and release of the staging buffer: no synchronisation here,
+    // kernel status is collected by the next synchronising call
     e = cudaMemcpyAsync(c_out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     cudaFreeAsync(tmp, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "c download");
-    return collect_device_status(ctx);
   }
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_set_mixture(fastfca_ctx* ctx, const void* x) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (!x) return fail(ctx, FASTFCA_EINVAL, "x is required");
+  const size_t bytes = sizeof(float2) * FT(ctx->cfg) * ctx->cfg.M;
+  if (!ctx->x_owned) CK(ctx, cudaMalloc(&ctx->x_owned, bytes), "x alloc");
+  CK(ctx, cudaMemcpyAsync(ctx->x_owned, x, bytes, cudaMemcpyDefault, ctx->stream), "x upload");
+  ctx->x = ctx->x_owned;
   return FASTFCA_OK;
 }
 

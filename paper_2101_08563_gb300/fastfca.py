@@ -36,6 +36,7 @@ _SIGNATURES = {
     "fastfca_iterate": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "fastfca_loglik": (ctypes.c_int, [_P, _P, _P]),
     "fastfca_separate": (ctypes.c_int, [_P, _P]),
+    "fastfca_set_mixture": (ctypes.c_int, [_P, _P]),
     "fastfca_sync": (ctypes.c_int, [_P]),
     "fastfca_last_error": (ctypes.c_char_p, [_P]),
     "fastfca_destroy": (None, [_P]),
@@ -225,13 +226,23 @@ class Separator:
 
     # ------------------------------------------------------------------ algorithm
     def iterate(self, n_iter: int, return_ll: bool = True):
-        """n_iter iterations; returns the total log-likelihood after each (np.float64) or None."""
+        """n_iter iterations; returns the total log-likelihood after each (np.float64), after
+        synchronising (numerical failures raise here), or None without waiting."""
         if return_ll:
             ll = np.empty(n_iter, np.float64)
             self._check(self.lib.fastfca_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p)))
+            self.sync()
             return ll
         self._check(self.lib.fastfca_iterate(self._h, int(n_iter), None))
         return None
+
+    def iterate_async(self, n_iter: int, ll_out=None):
+        """Stream-ordered iterations; ll_out (host or CUDA float64 (n_iter,), pinned host for an
+        asynchronous copy) receives the log-likelihood per iteration once the stream has passed
+        the call (see sync)."""
+        p = _ptr(ll_out, np.float64, (int(n_iter),), "ll_out", True)[0] if ll_out is not None else None
+        self._check(self.lib.fastfca_iterate(self._h, int(n_iter), p))
+        return ll_out
 
     def loglik(self, per_f: bool = False):
         tot = np.zeros(1, np.float64)
@@ -241,13 +252,30 @@ class Separator:
         return (float(tot[0]), pf) if per_f else float(tot[0])
 
     def separate(self, out=None):
-        """Source images complex64 (F, T, N, M); into `out` (host or CUDA) when given."""
+        """Source images complex64 (F, T, N, M); into `out` (host or CUDA) when given.  A host
+        result is complete on return (the call synchronises); a CUDA one is stream-ordered."""
         shape = (self.F, self.T, self.N, self.M)
         if out is None:
             out = np.empty(shape, np.complex64)
+        self.separate_async(out)
+        if not (torch is not None and isinstance(out, torch.Tensor) and out.is_cuda):
+            self.sync()
+        return out
+
+    def separate_async(self, out):
+        """Stream-ordered separation into `out` (host or CUDA, caller-allocated); a host buffer
+        is complete once the context's stream has passed the call (see sync)."""
+        shape = (self.F, self.T, self.N, self.M)
         p, keep = _ptr(out, np.complex64, shape, "c", True)
         self._check(self.lib.fastfca_separate(self._h, p))
         return out
+
+    def set_mixture(self, x):
+        """Replaces the mixture (same shape; host or CUDA), copied stream-ordered into a
+        buffer the library owns."""
+        p, keep = _ptr(x, np.complex64, (self.F, self.T, self.M), "x")
+        self._check(self.lib.fastfca_set_mixture(self._h, p))
+        self._x = keep
 
     def sync(self):
         self._check(self.lib.fastfca_sync(self._h))

@@ -207,3 +207,27 @@ def test_fewer_frames_than_mics_is_rejected_numerically(ff):
     with pytest.raises(ff.FastFCAError, match="ENUMERIC"):
         sep.iterate(1)
     sep.close()
+
+
+def test_set_mixture_and_async_host_separation(ff):
+    """A context reused through fastfca_set_mixture gives what a fresh context gives, and the
+    stream-ordered separation into a pinned host buffer equals the device result after sync."""
+    a = synth.generate_mixture(3, 4, 6, 300, 4, seed=21)
+    b = synth.generate_mixture(3, 4, 6, 300, 4, seed=22)
+    ib = synth.random_init(b.x, 4, seed=22)
+    fresh = ff.Separator(torch.from_numpy(b.x).cuda(), 4)
+    fresh.set_params(ib.P, ib.lam, ib.v)
+    ll_f = fresh.iterate(5)
+    c_f = fresh.separate(torch.empty((6, 300, 4, 3), dtype=torch.complex64, device="cuda"))
+    reused = ff.Separator(torch.from_numpy(a.x).cuda(), 4)      # borrowed device mixture
+    reused.iterate(2)
+    reused.set_mixture(torch.from_numpy(b.x).pin_memory())       # host copy into an owned buffer
+    reused.set_params(ib.P, ib.lam, ib.v)
+    ll_r = reused.iterate(5)
+    c_h = torch.empty((6, 300, 4, 3), dtype=torch.complex64).pin_memory()
+    reused.separate_async(c_h)
+    reused.sync()
+    assert np.array_equal(ll_f, ll_r)
+    assert torch.equal(c_f.cpu(), c_h)
+    fresh.close()
+    reused.close()
