@@ -121,7 +121,8 @@ fastfca_status collect_device_status(fastfca_ctx* c) {
   CK(c, cudaStreamSynchronize(c->stream), "stream synchronize");
   if (bits == 0) return FASTFCA_OK;
   CK(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "status clear");
-  if (bits & ffca::kErrConfig) return fail(c, FASTFCA_ECUDA, "kernel launch configuration rejected (bits 0x%x)", bits);
+  if (bits & (ffca::kErrConfig | ffca::kErrClusterWait))
+    return fail(c, FASTFCA_ECUDA, "kernel launch configuration rejected or a cluster exchange timed out (bits 0x%x)", bits);
   c->sticky = FASTFCA_ENUMERIC;
   return fail(c, FASTFCA_ENUMERIC,
               "numerical failure in a kernel (bits 0x%x: 1 sigma^2, 2 IP norm, 4 Q not PD, 8 W singular, 16 FCA not PD)",

@@ -85,6 +85,40 @@ __device__ __forceinline__ double2 ld_dsmem_f64x2(uint32_t addr) {
   return v;
 }
 
+// mbarrier + st.async: a CTA pushes values into a peer's shared memory and the peer's
+// transaction barrier counts the bytes; the peer waits on its own barrier only.
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(m)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(m)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"((uint32_t)__cvta_generic_to_shared(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr),
+               "r"(__float_as_uint(v)), "r"(remote_mbar)
+               : "memory");
+}
+
+// Status bit: a cluster exchange waited longer than its limit (the kernel continues; the
+// host reports the launch as failed).
+constexpr int kErrClusterWait = 64;
+constexpr int kMbarSpinLimit = 1 << 20;
+
 // Barrier of the four IP warps (threads 0..127) only.
 __device__ __forceinline__ void ip_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -110,7 +144,9 @@ struct ClusterSmem {
   static constexpr size_t oRed = oL + 4 * (size_t)M * kCMaxN;             // float kCWarps*8
   static constexpr size_t oLL = oRed + 4 * kCWarps * 8;                   // float kCWarps
   static constexpr size_t oQw = oLL + 4 * kCWarps;                        // float kCWarps*V
-  static constexpr size_t oFrames = oQw + 4 * (size_t)kCWarps * V;        // per-frame arrays
+  static constexpr size_t oPush = oQw + 4 * (size_t)kCWarps * V;         // float 2 x C x kCWarps x 8
+  static constexpr size_t oMbar = oPush + 4 * 2 * kCMaxCluster * kCWarps * 8;   // uint64 2
+  static constexpr size_t oFrames = oMbar + 16;                           // per-frame arrays
   // per-frame arrays, each row padded to Tcp = Tc rounded up to 4 floats
   __host__ __device__ static int tcp(int Tc) { return (Tc + 3) & ~3; }
   __host__ __device__ static size_t bytes(int N, int Tc) { return oFrames + 4 * (size_t)tcp(Tc) * (N + 3 * M); }
@@ -298,6 +334,8 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   float* sRed = reinterpret_cast<float*>(smem + SM::oRed);
   float* sLL = reinterpret_cast<float*>(smem + SM::oLL);
   float* sQw = reinterpret_cast<float*>(smem + SM::oQw);
+  float* sPush = reinterpret_cast<float*>(smem + SM::oPush);       // [parity][rank][warp][8]
+  uint64_t* sMbar = reinterpret_cast<uint64_t*>(smem + SM::oMbar);  // [parity]
   float* sH = reinterpret_cast<float*>(smem + SM::oFrames);   // [n][j]
   float* sU = sH + (size_t)N * Tcp;                             // [m][j]
   float* sS = sU + (size_t)M * Tcp;                             // sigma^2 [m][j]
@@ -311,6 +349,17 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   float* vf = p.v + (size_t)f * N * T;
   const double invT = 1.0 / (double)T;
   const float invTf = 1.0f / (float)T;
+
+  // transaction barriers of the n-loop exchange: each phase expects one value per (CTA, warp,
+  // m); armed here for the first two uses, re-armed after each use
+  const unsigned push_bytes = (unsigned)(C * kCWarps * M * sizeof(float));
+  if (tid == 0) {
+    mbar_init(&sMbar[0], 1);
+    mbar_init(&sMbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&sMbar[0], push_bytes);
+    mbar_expect_tx(&sMbar[1], push_bytes);
+  }
 
   // ---- load the parameters (L and W replicated, H for this CTA's frames)
   for (int i = tid; i < M * N; i += kCThreads) sL[i] = lamf[i];
@@ -404,6 +453,8 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     else { ea[q] = 0; eb[q] = 0; ek[q] = 3; }
   }
 
+  unsigned nphase[2] = {0u, 0u};
+  int npar = 0;
   float coef[M], Lold[M], Lnew[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) { coef[m] = 0.f; Lold[m] = 0.f; Lnew[m] = 0.f; }
@@ -540,9 +591,11 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       *xll = s;
     }
     cluster_sync();
+    // only the Q_m this CTA inverts are combined here (rank c owns m = c mod C)
     for (int i = tid; i < V; i += kCThreads) {
-      const double qd = (double)cluster_sum_f(xb + i) * invT;
       const int m = i / NE, e = i - m * NE;
+      if (m % C != crank) continue;
+      const double qd = (double)cluster_sum_f(xb + i) * invT;
       int a, b, kind;
       decode_entry<M>(e, a, b, kind);
       double2* Qm = sQ + m * M * M;
@@ -631,26 +684,39 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
           acc[m] += rr;
         }
       }
-      // per-warp sums go straight to the exchange row (warp w, value m at w*8 + m); after the
-      // barrier lane (m, q) adds the rows of warps 2q, 2q+1 of every CTA (rank order), and
-      // two shuffles finish: the same order in every warp of every CTA
+      // per-warp sums are pushed (st.async) into every CTA's receive row [rank][warp][m] of
+      // this parity, counted by that CTA's transaction barrier; each CTA waits on its own
+      // barrier, then lane (m, q) adds warps 2q, 2q+1 of every rank in rank order and two
+      // shuffles finish: the same order in every warp of every CTA.  A parity's row is
+      // rewritten only after every warp here has pushed the next exchange, i.e. read this one.
       warp_reduce_scatter<MP>(acc, lane);
-      float* xn = sX + par * XV;
-      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) xn[warp * 8 + (lane * MP) / 32] = acc[0];
-      cluster_sync();
+      float* rb = sPush + npar * (kCMaxCluster * kCWarps * 8);
+      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) {
+        float* slot = rb + (crank * kCWarps + warp) * 8 + (lane * MP) / 32;
+        for (int c = 0; c < C; ++c)
+          st_async_f32(dsmem_addr(slot, (unsigned)c), acc[0], dsmem_addr(&sMbar[npar], (unsigned)c));
+      }
+      {
+        int spins = 0;
+        while (!mbar_try_wait(&sMbar[npar], nphase[npar]) && ++spins < kMbarSpinLimit) {
+        }
+        if (spins >= kMbarSpinLimit && lane == 0) atomicOr(p.err, kErrClusterWait);
+      }
+      nphase[npar] ^= 1u;
       float tot_l = 0.f;
       {
         const int m = lane >> 2, q = lane & 3;
         if (m < M) {
           for (int c = 0; c < C; ++c) {
-            tot_l += ld_dsmem_f32(dsmem_addr(xn + (2 * q) * 8 + m, (unsigned)c));
-            tot_l += ld_dsmem_f32(dsmem_addr(xn + (2 * q + 1) * 8 + m, (unsigned)c));
+            tot_l += rb[(c * kCWarps + 2 * q) * 8 + m];
+            tot_l += rb[(c * kCWarps + 2 * q + 1) * 8 + m];
           }
         }
         tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 1);
         tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 2);
       }
-      par ^= 1;
+      if (tid == 0) mbar_expect_tx(&sMbar[npar], push_bytes);   // arm this parity's next use
+      npar ^= 1;
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const float mean = __shfl_sync(0xffffffffu, tot_l, 4 * m) * invTf;
