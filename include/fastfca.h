@@ -60,7 +60,7 @@ typedef enum {
   FASTFCA_ENOMEM = 2,        /* a device allocation failed */
   FASTFCA_ECUDA = 3,         /* a CUDA call or kernel launch failed */
   FASTFCA_ENUMERIC = 4,      /* non-finite or non-positive quantity met by a kernel */
-  FASTFCA_EUNSUPPORTED = 5   /* valid request for which this build has no kernel */
+  FASTFCA_EUNSUPPORTED = 5   /* valid request for which the library has no kernel */
 } fastfca_status;
 
 typedef enum {
@@ -70,9 +70,9 @@ typedef enum {
 
 typedef struct {
   int32_t F;      /* frequency bins, >= 1 */
-  int32_t T;      /* frames, >= 1 (FastFCA: <= 2048 in this build) */
-  int32_t M;      /* microphones: 2, 3 or 4 in this build */
-  int32_t N;      /* sources: 2..8 in this build */
+  int32_t T;      /* frames, >= 1 (FastFCA: up to what eight CTAs' shared memory holds, ~11k at M=8, N=12) */
+  int32_t M;      /* microphones: FastFCA 2..8, FCA 2..4 */
+  int32_t N;      /* sources: FastFCA 1..16, FCA 2..8 */
   int32_t model;  /* fastfca_model */
   int32_t seed;   /* seed of the default initial v (Philox4x32-10); any value */
 } fastfca_config;
@@ -250,7 +250,7 @@ fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t
  *     averaged over the rows of a batch.
  * Products run on BF16 tensor cores (operands rounded to BF16, FP32 accumulation); the rest in
  * FP32.  Parameters are one flat FP32 vector: W1 [256][16], b1 [256], W2 [256][256], b2 [256],
- * W3 [40][256], b3 [40], k [N][9], c [N].  This build supports M in {2, 3}, N <= 5 and
+ * W3 [40][256], b3 [40], k [N][9], c [N].  The network supports M in {2, 3}, N <= 5 and
  * 2 M^2 + M N + N <= 40.  A "row" is one frequency of one mixture.  Unless stated otherwise
  * arrays are device memory and calls are asynchronous on the given stream.
  * --------------------------------------------------------------------------------------- */

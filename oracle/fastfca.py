@@ -17,7 +17,7 @@ index i is dropped, as in Sec. III-IV; the frame index j runs over T frames, so 
 * ``loglik``             Eq. 31 (negated, with its additive constant -M J ln(pi) restored)
 * ``mwf``/``separate``   Eq. 39: F_jn = W^{-H} diag(L[:, n] H[n, j] / sigma^2_{:, j}) W^H
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 * Inside the n-loop the updates are Gauss-Seidel: G_n uses L and H as already updated for
   n' < n; L[:, n] divides by the old H[n, :]; H[n, :] divides by the new L[:, n].
 * Eq. 34 uses W with columns 1..m-1 already updated in this sweep.
