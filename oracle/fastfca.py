@@ -14,6 +14,8 @@ index i is dropped, as in Sec. III-IV; the frame index j runs over T frames, so 
 * ``decorrelated_power`` Eq. 37: U_{mj} = w_m^H X^_j w_m
 * ``nmf_em_step``        Algorithm 1, the body of the n-loop (G_n, Phi_n, L[:, n], H[n, :])
 * ``iterate``            Algorithm 1, one pass of the repeat loop
+* ``nmf_mm_step``        Algorithm 2, the L and H lines (MM for IS-NMF)
+* ``iterate_mm``         Algorithm 2, one pass of the repeat loop
 * ``loglik``             Eq. 31 (negated, with its additive constant -M J ln(pi) restored)
 * ``mwf``/``separate``   Eq. 39: F_jn = W^{-H} diag(L[:, n] H[n, j] / sigma^2_{:, j}) W^H
 
@@ -23,6 +25,8 @@ Readings where the paper is silent:
 * Eq. 34 uses W with columns 1..m-1 already updated in this sweep.
 * The square root of Eq. 35 takes the real part of w^H Q w (real for Hermitian Q).
 * No floors are applied to sigma^2, L or H (the paper has none).
+* Algorithm 2 lists the L line before the H line: H is updated with sigma^2 = LH recomputed
+  from the new L.
 """
 from __future__ import annotations
 
@@ -87,6 +91,16 @@ def nmf_em_step(U: np.ndarray, L: np.ndarray, H: np.ndarray, n: int):
     return L, H
 
 
+def nmf_mm_step(U: np.ndarray, L: np.ndarray, H: np.ndarray):
+    """Algorithm 2, the L and H lines: multiplicative MM updates of IS-NMF U ~ LH with the
+    exponent 1/2.  Returns new (L, H)."""
+    S = sigma2(L, H)
+    L = L * np.sqrt(((U * S ** -2) @ H.T) / ((S ** -1) @ H.T))     # L (.) {[U (.) (LH)^-2] H^T / (LH)^-1 H^T}^1/2
+    S = sigma2(L, H)                                                # with the new L
+    H = H * np.sqrt((L.T @ (U * S ** -2)) / (L.T @ (S ** -1)))     # H (.) {L^T [U (.) (LH)^-2] / L^T (LH)^-1}^1/2
+    return L, H
+
+
 def ip_sweep(Xhat: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray) -> np.ndarray:
     """Algorithm 1, the m-loop: Q_m from the current L, H, then Eq. 34-35 for m = 1..M."""
     M = W.shape[0]
@@ -107,6 +121,15 @@ def iterate(Xhat: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray):
     N = L.shape[1]
     for n in range(N):
         L, H = nmf_em_step(U, L, H, n)
+    return W, L, H
+
+
+def iterate_mm(Xhat: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray):
+    """Algorithm 2, one pass of the repeat loop for one frequency bin (shapes as ``iterate``):
+    the same IP sweep and U, then the MM updates of L and H."""
+    W = ip_sweep(Xhat, W, L, H)
+    U = decorrelated_power(Xhat, W)
+    L, H = nmf_mm_step(U, L, H)
     return W, L, H
 
 
@@ -155,14 +178,16 @@ def separate_fast(x: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray) ->
 
 # ----------------------------------------------------------------------------- whole problem
 def run(x: np.ndarray, P: np.ndarray, lam: np.ndarray, v: np.ndarray, iters: int,
-        freqs=None, with_ll: bool = True):
-    """Algorithm 1 for every frequency bin (or the listed ones), ``iters`` repeats each.
+        freqs=None, with_ll: bool = True, algorithm: str = "em"):
+    """Algorithm 1 ("em", IP+EM) or Algorithm 2 ("mm", IP+MM) for every frequency bin (or the
+    listed ones), ``iters`` repeats each.
 
     x (F, T, M) complex; P (F, M, M); lam (F, M, N); v (F, N, T).
     Returns dict with W, L, H (float64/complex128 copies for the processed bins) and
     ll[f_index, it] = log-likelihood after iteration it (when with_ll)."""
     F = x.shape[0]
     freqs = list(range(F)) if freqs is None else list(freqs)
+    step = {"em": iterate, "mm": iterate_mm}[algorithm]
     Ws, Ls, Hs, lls = [], [], [], []
     for f in freqs:
         Xhat = Xhat_from_x(x[f])
@@ -171,7 +196,7 @@ def run(x: np.ndarray, P: np.ndarray, lam: np.ndarray, v: np.ndarray, iters: int
         H = np.asarray(v[f], dtype=np.float64).copy()
         ll_f = []
         for _ in range(iters):
-            W, L, H = iterate(Xhat, W, L, H)
+            W, L, H = step(Xhat, W, L, H)
             if with_ll:
                 ll_f.append(loglik(Xhat, W, L, H))
         Ws.append(W)

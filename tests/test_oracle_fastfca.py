@@ -15,6 +15,7 @@ import scipy.stats
 
 from oracle import fastfca as ff
 from oracle import fca
+from paper_2101_08563_gb300 import synth  # noqa: E402
 from tests.conftest import rand_complex, rand_hpd
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -355,3 +356,77 @@ def test_golden_trajectory_regression():
     p = synth.random_init(mix.x, g["N"], seed=g["seed"])
     out = ff.run(mix.x, p.P, p.lam, p.v, iters=g["iters"])
     assert np.allclose(out["ll"], np.array(g["ll"]), rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------- Algorithm 2 (IP+MM)
+def _is_cost(U, L, H):
+    S = L @ H
+    return float(np.sum(U / S + np.log(S)))
+
+
+def test_mm_update_minimises_the_written_out_majoriser(rng):
+    """The L and H lines of Algorithm 2 are the exact minimisers of the IS-NMF auxiliary
+    function: Jensen's bound on U/sigma^2 with weights lam_n = L~ H~_n / sigma~^2 and the
+    tangent bound on ln sigma^2.  Each entry's 1-D majoriser is minimised numerically here."""
+    from scipy.optimize import minimize_scalar
+    M, N, J = 2, 3, 7
+    U = rng.uniform(0.2, 3.0, (M, J))
+    L0 = rng.uniform(0.3, 2.0, (M, N))
+    H0 = rng.uniform(0.3, 2.0, (N, J))
+    L1, H1 = ff.nmf_mm_step(U, L0, H0)
+    S0 = L0 @ H0
+    for m in range(M):
+        for n in range(N):
+            lam = L0[m, n] * H0[n] / S0[m]
+            f = lambda l: np.sum(lam ** 2 * U[m] / (l * H0[n]) + l * H0[n] / S0[m])
+            best = minimize_scalar(f, bounds=(1e-6, 100.0), method="bounded", options={"xatol": 1e-12})
+            assert abs(best.x - L1[m, n]) <= 1e-6 * L1[m, n]
+    S1 = L1 @ H0                               # H uses sigma^2 from the new L
+    for n in range(N):
+        for j in range(J):
+            lam = L1[:, n] * H0[n, j] / S1[:, j]
+            f = lambda h: np.sum(lam ** 2 * U[:, j] / (L1[:, n] * h) + L1[:, n] * h / S1[:, j])
+            best = minimize_scalar(f, bounds=(1e-6, 100.0), method="bounded", options={"xatol": 1e-12})
+            assert abs(best.x - H1[n, j]) <= 1e-6 * H1[n, j]
+
+
+def test_mm_step_never_increases_the_is_cost(rng):
+    for _ in range(20):
+        M, N, J = int(rng.integers(2, 5)), int(rng.integers(1, 6)), int(rng.integers(3, 30))
+        U = rng.uniform(0.01, 5.0, (M, J))
+        L = rng.uniform(0.05, 3.0, (M, N))
+        H = rng.uniform(0.05, 3.0, (N, J))
+        c0 = _is_cost(U, L, H)
+        L1, H1 = ff.nmf_mm_step(U, L, H)
+        assert _is_cost(U, L1, H1) <= c0 + 1e-12 * abs(c0)
+
+
+def test_mm_fixed_points_are_stationary_points_of_the_is_cost(rng):
+    """Run the MM updates to convergence (W = I is IS-NMF, footnote of Sec. IV-E); the
+    finite-difference gradient of the IS cost then vanishes at the limit."""
+    M, N, J = 2, 2, 6
+    U = rng.uniform(0.2, 3.0, (M, J))
+    L = rng.uniform(0.5, 1.5, (M, N))
+    H = rng.uniform(0.5, 1.5, (N, J))
+    for _ in range(20000):
+        L, H = ff.nmf_mm_step(U, L, H)
+    eps = 1e-6
+    for A in (L, H):
+        for idx in np.ndindex(A.shape):
+            old = A[idx]
+            A[idx] = old * (1 + eps)
+            cp = _is_cost(U, L, H)
+            A[idx] = old * (1 - eps)
+            cm = _is_cost(U, L, H)
+            A[idx] = old
+            # d cost / d ln A  (scale-free): zero at a stationary point
+            assert abs(cp - cm) / (2 * eps) <= 1e-6 * abs(_is_cost(U, L, H))
+
+
+def test_ip_mm_log_likelihood_is_monotone():
+    mix = synth.generate_mixture(3, 4, 3, 150, 4, seed=33)
+    init = synth.random_init(mix.x, 4, seed=33)
+    ref = ff.run(mix.x, init.P, init.lam, init.v, iters=25, algorithm="mm")
+    for f in range(3):
+        ll = ref["ll"][f]
+        assert np.all(np.diff(ll) >= -1e-9 * np.abs(ll[1:]))
