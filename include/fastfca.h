@@ -64,8 +64,10 @@ typedef enum {
 } fastfca_status;
 
 typedef enum {
-  FASTFCA_MODEL_FASTFCA = 0, /* joint-diagonalisation model, Sec. IV */
-  FASTFCA_MODEL_FCA = 1      /* full-rank FCA, Sec. III (comparison model) */
+  FASTFCA_MODEL_FASTFCA = 0,    /* joint-diagonalisation model, Sec. IV, IP+EM (Algorithm 1) */
+  FASTFCA_MODEL_FCA = 1,        /* full-rank FCA, Sec. III (comparison model) */
+  FASTFCA_MODEL_FASTFCA_MM = 2  /* the FastFCA model fitted by IP+MM (Algorithm 2); same
+                                   parameters and calls as FASTFCA; M 2..4, N 2..8, T <= 2048 */
 } fastfca_model;
 
 typedef struct {

@@ -108,6 +108,9 @@ cudaError_t from_device(void* dst, const void* src, size_t bytes, cudaStream_t s
 
 size_t FT(const fastfca_config& c) { return (size_t)c.F * c.T; }
 
+// The FastFCA model, fitted by IP+EM (Algorithm 1) or IP+MM (Algorithm 2): the same parameters.
+bool fastfca_family(int model) { return model == FASTFCA_MODEL_FASTFCA || model == FASTFCA_MODEL_FASTFCA_MM; }
+
 fastfca_status check_ready(fastfca_ctx* c) {
   if (!c) return FASTFCA_EINVAL;
   if (c->sticky == FASTFCA_ECUDA) return c->sticky;
@@ -198,15 +201,17 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
   const fastfca_config c = *cfg;
   if (c.F < 1 || c.T < 1 || c.M < 1 || c.N < 1)
     return fail(nullptr, FASTFCA_EINVAL, "F, T, M, N must be positive (got %d %d %d %d)", c.F, c.T, c.M, c.N);
-  if (c.model != FASTFCA_MODEL_FASTFCA && c.model != FASTFCA_MODEL_FCA)
+  if (!fastfca_family(c.model) && c.model != FASTFCA_MODEL_FCA)
     return fail(nullptr, FASTFCA_EINVAL, "unknown model %d", c.model);
   ffca::FastOps ops{};
   ffca::FcaOps fops{};
-  if (c.model == FASTFCA_MODEL_FASTFCA) {
+  if (fastfca_family(c.model)) {
     if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED,
                   "no FastFCA kernel for M=%d N=%d T=%d (M in 2..%d, N in 1..%d, T within eight CTAs' "
                   "shared memory)", c.M, c.N, c.T, kMaxM, kMaxN);
+    if (c.model == FASTFCA_MODEL_FASTFCA_MM && !ops.em_mm)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "IP+MM (Algorithm 2) runs on M in 2..4, N in 2..8, T <= 2048");
   } else {
     if (!ffca::fca_ops(c.M, c.N, &fops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FCA kernel for M=%d N=%d", c.M, c.N);
@@ -242,7 +247,7 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
   CKC(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "status clear");
   CKC(cudaMalloc(&ctx->ll_last, sizeof(double) * c.F), "ll alloc");
   const int threads = 256;
-  if (c.model == FASTFCA_MODEL_FASTFCA) {
+  if (fastfca_family(c.model)) {
     CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
     CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
     CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "v alloc");
@@ -290,7 +295,7 @@ void fastfca_destroy(fastfca_ctx* ctx) {
 fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* lam, const float* v) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (ctx->cfg.model != FASTFCA_MODEL_FASTFCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
   if (!P || !lam || !v) return fail(ctx, FASTFCA_EINVAL, "P, lam and v are required");
   const fastfca_config& c = ctx->cfg;
   CK(ctx, to_device(ctx->P, P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P upload");
@@ -304,7 +309,7 @@ fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* 
 fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* v) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (ctx->cfg.model != FASTFCA_MODEL_FASTFCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
   const fastfca_config& c = ctx->cfg;
   if (P) CK(ctx, from_device(P, ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P download");
   if (lam) CK(ctx, from_device(lam, ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam download");
@@ -345,7 +350,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     if (st) return st;
     hist = ctx->ll_hist;
   }
-  if (c.model == FASTFCA_MODEL_FASTFCA) {
+  if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
     a.P = ctx->P;
@@ -362,7 +367,8 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     a.N = c.N;
     a.n_iter = n_iter;
     a.ll_stride = n_iter;
-    CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA EM launch");
+    CK(ctx, (c.model == FASTFCA_MODEL_FASTFCA_MM ? ctx->ops.em_mm : ctx->ops.em)(a, ctx->stream),
+       "FastFCA IP+EM/IP+MM launch");
     ctx->b_valid = 1;
   } else {
     ffca::FcaArgs a{};
@@ -391,7 +397,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
   fastfca_status st = check_ready(ctx);
   if (st) return st;
   const fastfca_config& c = ctx->cfg;
-  if (c.model == FASTFCA_MODEL_FASTFCA) {
+  if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
     a.P = ctx->P;
@@ -447,7 +453,7 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
     dst = tmp;
   }
   cudaError_t e;
-  if (c.model == FASTFCA_MODEL_FASTFCA) {
+  if (fastfca_family(c.model)) {
     if (ctx->b_valid) {
       const size_t n = (size_t)c.F * c.M * c.M;
       bst_to_winv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->Bst, ctx->winv, n);

@@ -24,6 +24,12 @@
 //   H[n,t] <- (1/M) sum_m Phi/L'[m,n] = H[n,t] * (1/M) sum_m r_{mt} / mean_t r_{mt}
 // (the same numbers as Algorithm 1 with one reciprocal per (m,t) instead of three).
 //
+// IP+MM (Algorithm 2, the MM template flag): the same IP and U, then L and H by the
+// multiplicative MM updates of IS-NMF with exponent 1/2, all sources at once: one pass over
+// the frames accumulates [U (.) (LH)^-2] H^T and (LH)^-1 H^T (in chunks of sources, reduced
+// over the CTA) for L; a second pass forms, per frame, sigma^2 from the new L and updates
+// every H[n, t].  Two barriers per iteration instead of one per source.
+//
 // IP in FP64 (Eq. 34-35).  With B = W^{-H} (columns b_m), (W^H Q_m)^{-1} e_m = Q_m^{-1} b_m,
 // so Eq. 34 is w = Q_m^{-1} b_m and Eq. 35 divides by sqrt(s), s = b_m^H Q_m^{-1} b_m.  The
 // M inverses Q_m^{-1} do not depend on W and are formed in parallel (one warp each); the
@@ -345,7 +351,7 @@ struct EmItem {
 
 // The whole IP+EM run of one frequency by one CTA (see the file comment).  `smem_raw` is the
 // CTA's dynamic shared memory (EmSmem<M, N>::bytes(blockDim.x)); T <= blockDim.x * kSlots.
-template <int M, int N>
+template <int M, int N, bool MM = false>
 __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned char* smem_raw) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
@@ -510,7 +516,7 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
       for (int k = 0; k < kSlots; ++k) {
         const int t = tid + k * bd;
         if (t < T) {
-          if (it > 0) {
+          if (!MM && it > 0) {
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
@@ -629,62 +635,150 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
     pass_U();
     FFCA_MARK(it, 4);
 
-    // ---- NMF EM sweep over sources (Algorithm 1 n-loop, Gauss-Seidel).  Pass n applies
-    // the H[n-1,:] update of the previous source, then forms r for source n.
+    if constexpr (MM) {
+      // ---- Algorithm 2: L <- L (.) {[U (.) (LH)^-2] H^T / (LH)^-1 H^T}^1/2, sources in chunks
+      // of NC; r[k][m] still holds 1/sigma^2 of pass A (L and H are unchanged since)
+      constexpr int NC = (N < 16 / M) ? N : 16 / M;            // 2 M NC <= 32 values per chunk
+      constexpr int VLP = pow2_ceil(2 * M * NC);
 #pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-      float* pHn = pH + n;                   // this thread's H[n, .] (slot k at k*N)
-      float Lr[M][N];
-      load_L(Lr);
-      float Ln[M];
+      for (int n0 = 0; n0 < N; n0 += NC) {
+        float acc[VLP];
 #pragma unroll
-      for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
-      float acc[MP];
+        for (int i = 0; i < VLP; ++i) acc[i] = 0.f;
 #pragma unroll
-      for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+        for (int k = 0; k < kSlots; ++k) {
+          const int t = tid + k * bd;
+          if (t < T) {
 #pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        const int t = tid + k * bd;
-        if (t < T) {
-          if (n > 0) {
-            float g = 0.f;
+            for (int m = 0; m < M; ++m) {
+              const float rs = r[k][m];
+              const float a = pU[k * M + m] * rs * rs;
 #pragma unroll
-            for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-            pHn[k * N - 1] *= g;
+              for (int nc = 0; nc < NC; ++nc) {
+                const int n = n0 + nc < N ? n0 + nc : N - 1;   // a partial last chunk repeats a source; its sums are not used
+                const float h = pH[k * N + n];
+                acc[m * NC + nc] = fmaf(a, h, acc[m * NC + nc]);
+                acc[M * NC + m * NC + nc] = fmaf(rs, h, acc[M * NC + m * NC + nc]);
+              }
+            }
           }
-          float h[N];
+        }
+        warp_reduce_scatter<VLP>(acc, lane);
+        {
+          float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
+          if ((lane * VLP) % 32 == 0) red[(lane * VLP) / 32] = acc[0];
+        }
+        __syncthreads();
+        if (tid < M * NC) {
+          const int m = tid / NC, nc = tid - (tid / NC) * NC;
+          if (n0 + nc < N) {
+            const float* red = sRed + par * kMaxWarps * SM::kRedW;
+            float num = 0.f, den = 0.f;
+            for (int w = 0; w < nw; ++w) {
+              num += red[w * SM::kRedW + m * NC + nc];
+              den += red[w * SM::kRedW + M * NC + m * NC + nc];
+            }
+            // a source whose H row has underflowed to zero in FP32 gives 0/0 here; L[:, n] then
+            // has no effect on the model and is left as it is
+            sL[m * N + n0 + nc] *= (den > 0.f) ? sqrtf(num / den) : 1.0f;
+          }
+        }
+        par ^= 1;
+      }
+      __syncthreads();
+      // ---- H <- H (.) {L^T [U (.) (LH)^-2] / L^T (LH)^-1}^1/2 with sigma^2 from the new L
+      {
+        float Lr[M][N];
+        load_L(Lr);
 #pragma unroll
-          for (int n2 = 0; n2 < N; ++n2) h[n2] = pH[k * N + n2];
-          const float hn = pHn[k * N];
+        for (int k = 0; k < kSlots; ++k) {
+          const int t = tid + k * bd;
+          if (t < T) {
+            float h[N];
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            float s2 = 0.f;
+            for (int n = 0; n < N; ++n) h[n] = pH[k * N + n];
+            float a[M], b[M];
 #pragma unroll
-            for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
-            const float rs = fast_rcp(s2);
-            const float G = Ln[m] * hn * rs;
-            const float rr = fmaf(G, fmaf(pU[k * M + m], rs, -1.f), 1.f);
-            r[k][m] = rr;
-            acc[m] += rr;
+            for (int m = 0; m < M; ++m) {
+              float s2 = 0.f;
+#pragma unroll
+              for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], h[n], s2);
+              const float rs = fast_rcp(s2);
+              b[m] = rs;
+              a[m] = pU[k * M + m] * rs * rs;
+            }
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+              float num = 0.f, den = 0.f;
+#pragma unroll
+              for (int m = 0; m < M; ++m) {
+                num = fmaf(Lr[m][n], a[m], num);
+                den = fmaf(Lr[m][n], b[m], den);
+              }
+              pH[k * N + n] = (den > 0.f) ? h[n] * sqrtf(num * fast_rcp(den)) : h[n];
+            }
           }
         }
       }
-      warp_reduce_scatter<MP>(acc, lane);
-      {
-        float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
-        if ((lane * MP) % 32 == 0) red[(lane * MP) / 32] = acc[0];
-      }
-      __syncthreads();
-      float tot[M];
-      cta_rows_sum<M, MP>(sRed + par * kMaxWarps * SM::kRedW, nw, lane, tot);
-      par ^= 1;
+      __syncthreads();           // the next pass A reads L and the new H
+    } else {
+      // ---- NMF EM sweep over sources (Algorithm 1 n-loop, Gauss-Seidel).  Pass n applies
+      // the H[n-1,:] update of the previous source, then forms r for source n.
+#pragma unroll 1
+      for (int n = 0; n < N; ++n) {
+        float* pHn = pH + n;                   // this thread's H[n, .] (slot k at k*N)
+        float Lr[M][N];
+        load_L(Lr);
+        float Ln[M];
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const float mean = tot[m] * invTf;
-        sL[m * N + n] = Ln[m] * mean;       // same value from every thread
-        coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+        for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
+        float acc[MP];
+#pragma unroll
+        for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+          const int t = tid + k * bd;
+          if (t < T) {
+            if (n > 0) {
+              float g = 0.f;
+#pragma unroll
+              for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
+              pHn[k * N - 1] *= g;
+            }
+            float h[N];
+#pragma unroll
+            for (int n2 = 0; n2 < N; ++n2) h[n2] = pH[k * N + n2];
+            const float hn = pHn[k * N];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              float s2 = 0.f;
+#pragma unroll
+              for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
+              const float rs = fast_rcp(s2);
+              const float G = Ln[m] * hn * rs;
+              const float rr = fmaf(G, fmaf(pU[k * M + m], rs, -1.f), 1.f);
+              r[k][m] = rr;
+              acc[m] += rr;
+            }
+          }
+        }
+        warp_reduce_scatter<MP>(acc, lane);
+        {
+          float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
+          if ((lane * MP) % 32 == 0) red[(lane * MP) / 32] = acc[0];
+        }
+        __syncthreads();
+        float tot[M];
+        cta_rows_sum<M, MP>(sRed + par * kMaxWarps * SM::kRedW, nw, lane, tot);
+        par ^= 1;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float mean = tot[m] * invTf;
+          sL[m * N + n] = Ln[m] * mean;       // same value from every thread
+          coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+        }
+        FFCA_MARK(it, 5 + (n < 9 ? n : 9));
       }
-      FFCA_MARK(it, 5 + (n < 9 ? n : 9));
     }
     FFCA_MARK(it, 15);
   }
@@ -708,7 +802,7 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
 }
 
 
-template <int M, int N>
+template <int M, int N, bool MM = false>
 __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   const int f = blockIdx.x;
   if (f >= p.F) return;
@@ -732,7 +826,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   q.T = p.T;
   q.n_iter = p.n_iter;
   q.b_valid = p.b_valid;
-  em_frequency<M, N>(q, p.err, smem_raw);
+  em_frequency<M, N, MM>(q, p.err, smem_raw);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {

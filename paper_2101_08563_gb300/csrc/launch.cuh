@@ -8,6 +8,7 @@ namespace ffca {
 
 struct FastOps {
   cudaError_t (*em)(const EmArgs& a, cudaStream_t s);
+  cudaError_t (*em_mm)(const EmArgs& a, cudaStream_t s);   // IP+MM (Algorithm 2); null if none
   cudaError_t (*winv)(const double2* P, float2* WmH, int F, int* err, cudaStream_t s);
   cudaError_t (*mwf)(const float2* x, const double2* P, const float2* WmH, const float* lam,
                      const float* v, float2* c, int F, int T, int N, cudaStream_t s);
@@ -26,15 +27,15 @@ inline int em_threads(int T) {
   return (warps < 1 ? 1 : warps) * 32;
 }
 
-template <int M, int N>
+template <int M, int N, bool MM = false>
 cudaError_t launch_em(const EmArgs& a, cudaStream_t s) {
   const int threads = em_threads(a.T);
   if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
   const size_t smem = EmSmem<M, N>::bytes(threads);
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N>,
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N, MM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fastfca_em_kernel<M, N><<<a.F, threads, smem, s>>>(a);
+  fastfca_em_kernel<M, N, MM><<<a.F, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -86,6 +87,7 @@ template <int M, int N>
 FastOps make_fast_ops() {
   FastOps o;
   o.em = &launch_em<M, N>;
+  o.em_mm = &launch_em<M, N, true>;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf<M, N>;
   o.em_persistent = &launch_em_persistent<M, N>;
@@ -154,6 +156,7 @@ template <int M>
 FastOps make_cluster_ops() {
   FastOps o{};
   o.em = &launch_em_cluster<M>;
+  o.em_mm = nullptr;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf_wide<M>;
   o.em_persistent = nullptr;

@@ -24,6 +24,7 @@ except Exception:  # pragma: no cover
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "EUNSUPPORTED"}
 MODEL_FASTFCA = 0
 MODEL_FCA = 1
+MODEL_FASTFCA_MM = 2
 
 # Every entry point of include/fastfca.h with (restype, argtypes).
 _P = ctypes.c_void_p
@@ -142,7 +143,8 @@ def _default_stream():
 class Separator:
     """One separation problem (one mixture) held by the library.
 
-    x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" or "fca".
+    x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" (IP+EM,
+    Algorithm 1), "fastfca_mm" (the same model by IP+MM, Algorithm 2) or "fca".
     A CUDA x is borrowed (kept referenced here); a host x is copied by the library.  seed
     selects the random factor of the default initial v (see fastfca_create).
     """
@@ -154,7 +156,7 @@ class Separator:
             raise ValueError("x must have shape (F, T, M)")
         self.F, self.T, self.M = (int(s) for s in shape)
         self.N = int(N)
-        self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA}[model]
+        self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA, "fastfca_mm": MODEL_FASTFCA_MM}[model]
         cfg = Config(self.F, self.T, self.M, self.N, self.model, int(seed) & 0x7fffffff)
         px, self._x = _ptr(x, np.complex64, shape, "x")
         self.stream = _default_stream() if stream is None else stream

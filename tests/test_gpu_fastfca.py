@@ -231,3 +231,39 @@ def test_set_mixture_and_async_host_separation(ff):
     assert torch.equal(c_f.cpu(), c_h)
     fresh.close()
     reused.close()
+
+
+# ---------------------------------------------------------------------------- IP+MM (Algorithm 2)
+@pytest.mark.parametrize("M,N,F,T,iters", [
+    (2, 3, 9, 250, 5),
+    (3, 5, 4, 500, 4),
+    (4, 6, 3, 1250, 3),
+    (4, 8, 2, 2048, 2),    # the largest T one CTA holds
+    (3, 7, 3, 77, 6),      # a partial chunk of sources in the L update
+])
+def test_ip_mm_parity(ff, M, N, F, T, iters):
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=40 + M * N)
+    init = synth.random_init(mix.x, N, seed=40 + M * N)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N, model="fastfca_mm")
+    sep.set_params(init.P, init.lam, init.v)
+    ll = sep.iterate(iters)
+    c = sep.separate()
+    sep.close()
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters, algorithm="mm")
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
+    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert rel(c.sum(axis=2), mix.x) < 1e-5
+
+
+def test_ip_mm_monotone_and_limits(ff):
+    mix = synth.generate_mixture(4, 6, 8, 600, 8, seed=44)
+    init = synth.random_init(mix.x, 6, seed=44)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 6, model="fastfca_mm")
+    sep.set_params(init.P, init.lam, init.v)
+    ll = sep.iterate(30)
+    sep.close()
+    assert np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
+    x = torch.zeros((2, 64, 8), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
+        ff.Separator(x, 12, model="fastfca_mm")
