@@ -92,6 +92,17 @@ typedef struct fastfca_ctx fastfca_ctx;
 fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream,
                               fastfca_ctx** out);
 
+/* Piecewise-stationary FastFCA (Sec. VI-B): the T frames of x (complex64 [F][T][M], host or
+ * device, as for fastfca_create) are partitioned into J = T / B blocks of B consecutive
+ * frames, and the model is fitted to X^_j = (1/B) sum_b x x^H (the paper's Eq. 44 cost) by
+ * Algorithm 1 or 2 (cfg->model FASTFCA or FASTFCA_MM).  Every parameter call then has J
+ * columns where fastfca_create's contexts have T: v float32 [F][N][J], the log-likelihood
+ * is Eq. 44's (per block).  fastfca_separate filters every frame with the powers of its
+ * block (c complex64 [F][T][N][M]).  B = 1 is fastfca_create.  EINVAL unless B divides T;
+ * EUNSUPPORTED outside M 2..4, N 2..8, J <= 2048, or for the FCA model. */
+fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
+                                     fastfca_ctx** out);
+
 /* Replaces the FastFCA parameters: P complex128 [F][M][M], lam float32 [F][M][N],
  * v float32 [F][N][T] (each host or device).  All three are required.  Clears a sticky
  * ENUMERIC and the log-likelihood history. */

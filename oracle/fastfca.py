@@ -18,6 +18,7 @@ index i is dropped, as in Sec. III-IV; the frame index j runs over T frames, so 
 * ``iterate_mm``         Algorithm 2, one pass of the repeat loop
 * ``loglik``             Eq. 31 (negated, with its additive constant -M J ln(pi) restored)
 * ``mwf``/``separate``   Eq. 39: F_jn = W^{-H} diag(L[:, n] H[n, j] / sigma^2_{:, j}) W^H
+* ``separate_blocks``    Eq. 39 with the block powers of Sec. VI-B
 
 Readings where the paper is silent:
 * Inside the n-loop the updates are Gauss-Seidel: G_n uses L and H as already updated for
@@ -177,10 +178,17 @@ def separate_fast(x: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray) ->
 
 
 # ----------------------------------------------------------------------------- whole problem
+def separate_blocks(x: np.ndarray, W: np.ndarray, L: np.ndarray, H: np.ndarray, B: int) -> np.ndarray:
+    """Eq. 39 under the piecewise-stationary model of Sec. VI-B: every frame b of block j has
+    the block's covariances, so frame t is filtered with the powers H[:, t // B]."""
+    return separate_fast(x, W, L, np.repeat(np.asarray(H, dtype=np.float64), B, axis=1))
+
+
 def run(x: np.ndarray, P: np.ndarray, lam: np.ndarray, v: np.ndarray, iters: int,
-        freqs=None, with_ll: bool = True, algorithm: str = "em"):
+        freqs=None, with_ll: bool = True, algorithm: str = "em", block: int = 1):
     """Algorithm 1 ("em", IP+EM) or Algorithm 2 ("mm", IP+MM) for every frequency bin (or the
-    listed ones), ``iters`` repeats each.
+    listed ones), ``iters`` repeats each.  With block = B > 1 the input is the block average
+    X^_j of Sec. VI-B and v has T / B columns.
 
     x (F, T, M) complex; P (F, M, M); lam (F, M, N); v (F, N, T).
     Returns dict with W, L, H (float64/complex128 copies for the processed bins) and
@@ -190,7 +198,7 @@ def run(x: np.ndarray, P: np.ndarray, lam: np.ndarray, v: np.ndarray, iters: int
     step = {"em": iterate, "mm": iterate_mm}[algorithm]
     Ws, Ls, Hs, lls = [], [], [], []
     for f in freqs:
-        Xhat = Xhat_from_x(x[f])
+        Xhat = Xhat_from_x(x[f], block)
         W = np.asarray(P[f], dtype=np.complex128).copy()
         L = np.asarray(lam[f], dtype=np.float64).copy()
         H = np.asarray(v[f], dtype=np.float64).copy()

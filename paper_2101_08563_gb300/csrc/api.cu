@@ -28,10 +28,13 @@ void set_thread_error(const char* msg) { snprintf(g_create_error, sizeof g_creat
 }  // namespace ffca
 
 struct fastfca_ctx {
-  fastfca_config cfg{};
+  fastfca_config cfg{};          // cfg.T counts the parameter columns: frames, or blocks
+  int Tf = 0;                    // frames of the mixture
+  int B = 1;                     // frames per block (Sec. VI-B); 1 = frame-wise model
   cudaStream_t stream = nullptr;
-  const float2* x = nullptr;     // device mixture (borrowed or owned)
+  const float2* x = nullptr;     // device mixture (borrowed or owned), F x Tf x M
   float2* x_owned = nullptr;
+  float* xh = nullptr;           // blocks: packed X^_j, F x cfg.T x M^2
   // FastFCA parameters
   double2* P = nullptr;
   float* lam = nullptr;
@@ -139,6 +142,27 @@ __global__ void bst_to_winv_kernel(const double2* __restrict__ B, float2* __rest
   if (i < n) WmH[i] = make_float2((float)B[i].x, (float)B[i].y);
 }
 
+// Default start of the piecewise-stationary model: W = I, L = 1, v[n][j] = tr(X^_j)/(M N) u,
+// u ~ U[0.5, 1.5) from Philox4x32-10 (the frame-wise default with tr(X^_j) for ||x_t||^2).
+__global__ void default_params_blocks_kernel(const float* __restrict__ xh, double2* __restrict__ P,
+                                             float* __restrict__ lam, float* __restrict__ v, int F, int J, int M,
+                                             int N, uint32_t seed) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < (size_t)F * M * M) {
+    const size_t r = i % ((size_t)M * M);
+    P[i] = make_double2((r / M == r % M) ? 1.0 : 0.0, 0.0);
+  }
+  if (i < (size_t)F * M * N) lam[i] = 1.0f;
+  if (i < (size_t)F * N * J) {
+    const size_t f = i / ((size_t)N * J), n = (i / J) % N, j = i % J;
+    const float* e = xh + (f * J + j) * (size_t)M * M;
+    float tr = 0.f;
+    for (int a = 0; a < M; ++a) tr += e[a];
+    const ffca::U4 r = ffca::philox4x32_10(ffca::U4{(uint32_t)f, (uint32_t)n, (uint32_t)j, 0x1d17u}, seed, 0u);
+    v[i] = fmaxf(tr / (float)(M * N) * (0.5f + ffca::u01(r.x)), 1e-30f);
+  }
+}
+
 __global__ void sum_over_f_kernel(const double* __restrict__ hist, int F, int stride, int n, double* __restrict__ out) {
   // one thread per column (iteration), fixed summation order over f
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,6 +182,7 @@ __global__ void init_fca_params_kernel(double2* __restrict__ R, int F, int N, in
 
 void free_all(fastfca_ctx* c) {
   cudaFree(c->x_owned);
+  cudaFree(c->xh);
   cudaFree(c->P);
   cudaFree(c->lam);
   cudaFree(c->v);
@@ -194,18 +219,28 @@ const char* fastfca_version(void) { return "fastfca-gb300 0.1 (sm_103a)"; }
 
 const char* fastfca_last_error(const fastfca_ctx* ctx) { return ctx ? ctx->msg : g_create_error; }
 
-fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream, fastfca_ctx** out) {
+static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* x, void* stream, fastfca_ctx** out) {
   if (!out) return fail(nullptr, FASTFCA_EINVAL, "out is NULL");
   *out = nullptr;
   if (!cfg || !x) return fail(nullptr, FASTFCA_EINVAL, "cfg and x are required");
-  const fastfca_config c = *cfg;
+  fastfca_config c = *cfg;
   if (c.F < 1 || c.T < 1 || c.M < 1 || c.N < 1)
     return fail(nullptr, FASTFCA_EINVAL, "F, T, M, N must be positive (got %d %d %d %d)", c.F, c.T, c.M, c.N);
   if (!fastfca_family(c.model) && c.model != FASTFCA_MODEL_FCA)
     return fail(nullptr, FASTFCA_EINVAL, "unknown model %d", c.model);
+  if (B < 1 || c.T % B != 0)
+    return fail(nullptr, FASTFCA_EINVAL, "the block size B=%d must be >= 1 and divide T=%d", B, c.T);
+  const int Tf = c.T;
+  c.T = Tf / B;                                   // parameter columns: blocks
   ffca::FastOps ops{};
   ffca::FcaOps fops{};
-  if (fastfca_family(c.model)) {
+  if (B > 1) {
+    if (!fastfca_family(c.model))
+      return fail(nullptr, FASTFCA_EINVAL, "the piecewise-stationary input serves the FastFCA models only");
+    if (!ffca::fast_ops(c.M, c.N, &ops) || c.T > ops.max_T || !ops.em_blk)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED,
+                  "blocks of B frames run on M in 2..4, N in 2..8 and at most %d blocks", ffca::kMaxThreads * ffca::kSlots);
+  } else if (fastfca_family(c.model)) {
     if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED,
                   "no FastFCA kernel for M=%d N=%d T=%d (M in 2..%d, N in 1..%d, T within eight CTAs' "
@@ -221,10 +256,12 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
   fastfca_ctx* ctx = new (std::nothrow) fastfca_ctx();
   if (!ctx) return fail(nullptr, FASTFCA_ENOMEM, "host allocation failed");
   ctx->cfg = c;
+  ctx->Tf = Tf;
+  ctx->B = B;
   ctx->stream = (cudaStream_t)stream;
   ctx->ops = ops;
   ctx->fops = fops;
-  const size_t nx = FT(c) * c.M;
+  const size_t nx = (size_t)c.F * Tf * c.M;
   auto bail = [&](fastfca_status st) {
     snprintf(g_create_error, sizeof g_create_error, "%s", ctx->msg);
     free_all(ctx);
@@ -255,8 +292,15 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
     CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
     CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
     const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
-    ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        ctx->x, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
+    if (B > 1) {
+      CKC(cudaMalloc(&ctx->xh, sizeof(float) * FT(c) * c.M * c.M), "block statistics alloc");
+      CKC(ctx->ops.block_stats(ctx->x, ctx->xh, c.F, c.T, B, ctx->stream), "block statistics launch");
+      default_params_blocks_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+          ctx->xh, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
+    } else {
+      ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+          ctx->x, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
+    }
     CKC(cudaGetLastError(), "init launch");
   } else {
     CKC(cudaMalloc(&ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M), "R alloc");
@@ -282,6 +326,15 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
 #undef CKC
   *out = ctx;
   return FASTFCA_OK;
+}
+
+fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream, fastfca_ctx** out) {
+  return create_impl(cfg, 1, x, stream, out);
+}
+
+fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
+                                     fastfca_ctx** out) {
+  return create_impl(cfg, B, x, stream, out);
 }
 
 void fastfca_destroy(fastfca_ctx* ctx) {
@@ -353,6 +406,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
   if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
+    a.xh = ctx->xh;
     a.P = ctx->P;
     a.lam = ctx->lam;
     a.v = ctx->v;
@@ -367,8 +421,9 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     a.N = c.N;
     a.n_iter = n_iter;
     a.ll_stride = n_iter;
-    CK(ctx, (c.model == FASTFCA_MODEL_FASTFCA_MM ? ctx->ops.em_mm : ctx->ops.em)(a, ctx->stream),
-       "FastFCA IP+EM/IP+MM launch");
+    const bool mm = c.model == FASTFCA_MODEL_FASTFCA_MM;
+    auto launch = ctx->B > 1 ? (mm ? ctx->ops.em_mm_blk : ctx->ops.em_blk) : (mm ? ctx->ops.em_mm : ctx->ops.em);
+    CK(ctx, launch(a, ctx->stream), "FastFCA IP+EM/IP+MM launch");
     ctx->b_valid = 1;
   } else {
     ffca::FcaArgs a{};
@@ -400,6 +455,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
   if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
+    a.xh = ctx->xh;
     a.P = ctx->P;
     a.lam = ctx->lam;
     a.v = ctx->v;
@@ -414,7 +470,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
     a.N = c.N;
     a.n_iter = 0;
     a.ll_stride = 0;
-    CK(ctx, ctx->ops.em(a, ctx->stream), "FastFCA log-likelihood launch");
+    CK(ctx, (ctx->B > 1 ? ctx->ops.em_blk : ctx->ops.em)(a, ctx->stream), "FastFCA log-likelihood launch");
     ctx->b_valid = 1;
   } else {
     ffca::FcaArgs a{};
@@ -444,7 +500,7 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   if (st) return st;
   if (!c_out) return fail(ctx, FASTFCA_EINVAL, "c is required");
   const fastfca_config& c = ctx->cfg;
-  const size_t bytes = sizeof(float2) * FT(c) * c.N * c.M;
+  const size_t bytes = sizeof(float2) * (size_t)c.F * ctx->Tf * c.N * c.M;
   const bool dev = is_device_ptr(c_out);
   float2* dst = static_cast<float2*>(c_out);
   float2* tmp = nullptr;
@@ -461,7 +517,8 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
     } else {
       e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
     }
-    if (e == cudaSuccess) e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, c.T, c.N, ctx->stream);
+    if (e == cudaSuccess)
+      e = ctx->ops.mwf(ctx->x, ctx->P, ctx->winv, ctx->lam, ctx->v, dst, c.F, ctx->Tf, c.N, ctx->B, ctx->stream);
   } else {
     e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
   }
@@ -483,10 +540,12 @@ fastfca_status fastfca_set_mixture(fastfca_ctx* ctx, const void* x) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
   if (!x) return fail(ctx, FASTFCA_EINVAL, "x is required");
-  const size_t bytes = sizeof(float2) * FT(ctx->cfg) * ctx->cfg.M;
+  const size_t bytes = sizeof(float2) * (size_t)ctx->cfg.F * ctx->Tf * ctx->cfg.M;
   if (!ctx->x_owned) CK(ctx, cudaMalloc(&ctx->x_owned, bytes), "x alloc");
   CK(ctx, cudaMemcpyAsync(ctx->x_owned, x, bytes, cudaMemcpyDefault, ctx->stream), "x upload");
   ctx->x = ctx->x_owned;
+  if (ctx->B > 1)
+    CK(ctx, ctx->ops.block_stats(ctx->x, ctx->xh, ctx->cfg.F, ctx->cfg.T, ctx->B, ctx->stream), "block statistics launch");
   return FASTFCA_OK;
 }
 

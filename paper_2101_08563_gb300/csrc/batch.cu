@@ -543,7 +543,7 @@ fastfca_status fastfca_batch_separate(fastfca_batch* b, int32_t i, void* c) {
   const fastfca_config& cf = m.cfg;
   if (!is_dev(c)) return bfail(b, FASTFCA_EINVAL, "c must be a device pointer");
   BCK(b, m.ops.winv(m.P, m.winv, cf.F, b->d_err, b->stream), "winv launch");
-  BCK(b, m.ops.mwf(m.x, m.P, m.winv, m.lam, m.v, static_cast<float2*>(c), cf.F, cf.T, cf.N, b->stream), "filter launch");
+  BCK(b, m.ops.mwf(m.x, m.P, m.winv, m.lam, m.v, static_cast<float2*>(c), cf.F, cf.T, cf.N, 1, b->stream), "filter launch");
   return FASTFCA_OK;
 }
 

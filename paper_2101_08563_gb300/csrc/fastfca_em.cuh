@@ -24,6 +24,12 @@
 //   H[n,t] <- (1/M) sum_m Phi/L'[m,n] = H[n,t] * (1/M) sum_m r_{mt} / mean_t r_{mt}
 // (the same numbers as Algorithm 1 with one reciprocal per (m,t) instead of three).
 //
+// Piecewise-stationary input (Sec. VI-B, the BL template flag): the "frames" are blocks j of
+// B frames and the input is X^_j = (1/B) sum_b x x^H, packed as in xxh_packed (M^2 floats
+// per block, built by block_stats_kernel).  The Q pass reads the packed entries instead of
+// forming them from x, and U_mj = w_m^H X^_j w_m is the real quadratic form; Algorithms 1
+// and 2 are otherwise unchanged.
+//
 // IP+MM (Algorithm 2, the MM template flag): the same IP and U, then L and H by the
 // multiplicative MM updates of IS-NMF with exponent 1/2, all sources at once: one pass over
 // the frames accumulates [U (.) (LH)^-2] H^T and (LH)^-1 H^T (in chunks of sources, reduced
@@ -49,6 +55,7 @@ constexpr int kEmMaxRegs = 96;
 
 struct EmArgs {
   const float2* x;      // F x T x M complex64, m fastest
+  const float* xh;      // blocks mode: F x T x M^2 packed X^_j (T counts blocks); else null
   double2* P;           // F x M x M complex128, W[a][m] at P[(f*M + a)*M + m]
   float* lam;           // F x M x N, L[m][n]
   float* v;             // F x N x T, H[n][t]
@@ -336,6 +343,7 @@ __device__ __forceinline__ void cta_rows_sum(const float* red, int nw, int lane,
 // One frequency of one mixture: everything em_frequency needs, as per-frequency pointers.
 struct EmItem {
   const float2* x;      // T x M
+  const float* xh;      // blocks mode: T x M^2 packed X^_j; else null
   double2* P;           // M x M (W[a][m] at a*M + m)
   float* lam;           // M x N
   float* v;             // N rows of T frames
@@ -351,7 +359,7 @@ struct EmItem {
 
 // The whole IP+EM run of one frequency by one CTA (see the file comment).  `smem_raw` is the
 // CTA's dynamic shared memory (EmSmem<M, N>::bytes(blockDim.x)); T <= blockDim.x * kSlots.
-template <int M, int N, bool MM = false>
+template <int M, int N, bool MM = false, bool BL = false>
 __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned char* smem_raw) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
@@ -383,6 +391,7 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
   float* pU = sU + tid * SU;
 
   const float2* xf = q.x;
+  const float* xhf = q.xh;
   const double invT = 1.0 / (double)T;
   const float invTf = 1.0f / (float)T;
 
@@ -463,8 +472,56 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
     }
   };
 
-  // U = |W^H x|^2 for the current W
+  // packed X^_j of block t (blocks mode)
+  auto load_xh = [&](int t, float (&e)[NE]) {
+    const float* src = xhf + (size_t)t * NE;
+    if constexpr (NE % 4 == 0) {
+#pragma unroll
+      for (int i = 0; i < NE; i += 4) {
+        const float4 q4 = __ldg(reinterpret_cast<const float4*>(src + i));
+        e[i] = q4.x; e[i + 1] = q4.y; e[i + 2] = q4.z; e[i + 3] = q4.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NE; ++i) e[i] = __ldg(src + i);
+    }
+  };
+
+  // U = |W^H x|^2 for the current W (blocks: U = w^H X^ w = sum_a |w_a|^2 X_aa
+  // + 2 sum_{a<b} Re(conj(w_a) w_b X_ab), with conj(w_a) = wc[a])
   auto pass_U = [&]() {
+    if constexpr (BL) {
+      float2 wc[M * M];
+#pragma unroll
+      for (int i = 0; i < M * M; ++i) wc[i] = sWc[i];
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float e[NE];
+          load_xh(t, e);
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            float u = 0.f;
+#pragma unroll
+            for (int a = 0; a < M; ++a) u = fmaf(fmaf(wc[m * M + a].x, wc[m * M + a].x, wc[m * M + a].y * wc[m * M + a].y), e[a], u);
+            int idx = M;
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+              for (int b = a + 1; b < M; ++b) {
+                const float2 wa = wc[m * M + a], wb = wc[m * M + b];
+                const float pr = fmaf(wa.x, wb.x, wa.y * wb.y);       // wa conj(wb)
+                const float pi = fmaf(wa.y, wb.x, -wa.x * wb.y);
+                u = fmaf(2.f, fmaf(pr, e[idx], -pi * e[idx + 1]), u);
+                idx += 2;
+              }
+            pU[k * M + m] = u;
+          }
+        }
+      }
+      return;
+    }
     float2 wc[M * M];
 #pragma unroll
     for (int i = 0; i < M * M; ++i) wc[i] = sWc[i];
@@ -565,10 +622,14 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
       for (int k = 0; k < kSlots; ++k) {
         const int t = tid + k * bd;
         if (t < T) {
-          float2 xv[M];
-          load_x(t, xv);
           float e[NE];
-          xxh_packed<M>(xv, e);
+          if constexpr (BL) {
+            load_xh(t, e);
+          } else {
+            float2 xv[M];
+            load_x(t, xv);
+            xxh_packed<M>(xv, e);
+          }
 #pragma unroll
           for (int mm = 0; mm < MC; ++mm) {
             float w = r[k][mm];
@@ -802,7 +863,7 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
 }
 
 
-template <int M, int N, bool MM = false>
+template <int M, int N, bool MM = false, bool BL = false>
 __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   const int f = blockIdx.x;
   if (f >= p.F) return;
@@ -813,6 +874,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EmItem q;
   q.x = p.x + (size_t)f * p.T * M;
+  q.xh = BL ? p.xh + (size_t)f * p.T * M * M : nullptr;
   q.P = p.P + (size_t)f * M * M;
   q.lam = p.lam + (size_t)f * M * N;
   q.v = p.v + (size_t)f * N * p.T;
@@ -826,7 +888,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   q.T = p.T;
   q.n_iter = p.n_iter;
   q.b_valid = p.b_valid;
-  em_frequency<M, N, MM>(q, p.err, smem_raw);
+  em_frequency<M, N, MM, BL>(q, p.err, smem_raw);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -865,6 +927,32 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_persistent_kernel(const EmIte
       q.stamp[1] = global_ns();
     }
   }
+}
+
+// X^_j = (1/B) sum_b x x^H of the blocks j of B consecutive frames (Sec. VI-B), packed as in
+// xxh_packed; one thread per (frequency, block).  x: F x (J B) x M; xh: F x J x M^2.
+template <int M>
+__global__ void block_stats_kernel(const float2* __restrict__ x, float* __restrict__ xh, int F, int J, int B) {
+  constexpr int NE = M * M;
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)F * J) return;
+  const size_t f = i / J, j = i - (i / J) * J;
+  const float2* src = x + (f * J * B + j * B) * M;
+  float acc[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) acc[e] = 0.f;
+  for (int b = 0; b < B; ++b) {
+    float2 xv[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) xv[a] = src[(size_t)b * M + a];
+    float e[NE];
+    xxh_packed<M>(xv, e);
+#pragma unroll
+    for (int q = 0; q < NE; ++q) acc[q] += e[q];
+  }
+  const float invB = 1.0f / (float)B;
+#pragma unroll
+  for (int q = 0; q < NE; ++q) xh[i * NE + q] = acc[q] * invB;
 }
 
 }  // namespace ffca

@@ -33,12 +33,13 @@ __global__ void __launch_bounds__(32) winv_kernel(const double2* __restrict__ P,
 
 constexpr int kMwfThreads = 128;
 
-// One thread per frame; grid (F, ceil(T / kMwfThreads)).  The N x M images of a frame are
+// One thread per frame; grid (F, ceil(T / kMwfThreads)).  With piecewise-stationary parameters
+// (Sec. VI-B) frame t uses the powers of its block t / B.  The N x M images of a frame are
 // staged in shared memory so that each warp writes its frames' output as one contiguous span.
 template <int M, int N>
 __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
     const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
-    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T) {
+    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int B) {
   __shared__ float2 sWc[M * M];       // conj(W[a][m]) at [m*M + a]
   __shared__ float2 sWi[M * M];       // W^{-H}[a][m] at [a*M + m]
   __shared__ float sL[M * N];
@@ -69,8 +70,9 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
       y[m] = acc;
     }
     float h[N];
+    const int J = T / B;                 // v holds one column per block of B frames
 #pragma unroll
-    for (int n = 0; n < N; ++n) h[n] = v[((size_t)f * N + n) * T + t];
+    for (int n = 0; n < N; ++n) h[n] = v[((size_t)f * N + n) * J + t / B];
     float rs[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {

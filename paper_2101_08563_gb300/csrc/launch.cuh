@@ -9,9 +9,15 @@ namespace ffca {
 struct FastOps {
   cudaError_t (*em)(const EmArgs& a, cudaStream_t s);
   cudaError_t (*em_mm)(const EmArgs& a, cudaStream_t s);   // IP+MM (Algorithm 2); null if none
+  // piecewise-stationary input (Sec. VI-B): a.xh holds the packed block statistics, a.T counts
+  // blocks; null if none
+  cudaError_t (*em_blk)(const EmArgs& a, cudaStream_t s);
+  cudaError_t (*em_mm_blk)(const EmArgs& a, cudaStream_t s);
+  cudaError_t (*block_stats)(const float2* x, float* xh, int F, int J, int B, cudaStream_t s);
   cudaError_t (*winv)(const double2* P, float2* WmH, int F, int* err, cudaStream_t s);
+  // B: frames per block of v (1 = per frame; frame t reads v column t / B)
   cudaError_t (*mwf)(const float2* x, const double2* P, const float2* WmH, const float* lam,
-                     const float* v, float2* c, int F, int T, int N, cudaStream_t s);
+                     const float* v, float2* c, int F, int T, int N, int B, cudaStream_t s);
   // persistent batch form: items in device memory, `bd` threads per CTA, `grid` CTAs
   cudaError_t (*em_persistent)(const EmItem* items, int n_items, int n_iter, int* counter, int* err, int bd,
                                int grid, cudaStream_t s);
@@ -27,15 +33,23 @@ inline int em_threads(int T) {
   return (warps < 1 ? 1 : warps) * 32;
 }
 
-template <int M, int N, bool MM = false>
+template <int M, int N, bool MM = false, bool BL = false>
 cudaError_t launch_em(const EmArgs& a, cudaStream_t s) {
   const int threads = em_threads(a.T);
   if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
+  if (BL && !a.xh) return cudaErrorInvalidValue;
   const size_t smem = EmSmem<M, N>::bytes(threads);
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N, MM>,
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N, MM, BL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fastfca_em_kernel<M, N, MM><<<a.F, threads, smem, s>>>(a);
+  fastfca_em_kernel<M, N, MM, BL><<<a.F, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_block_stats(const float2* x, float* xh, int F, int J, int B, cudaStream_t s) {
+  const size_t n = (size_t)F * J;
+  block_stats_kernel<M><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, xh, F, J, B);
   return cudaGetLastError();
 }
 
@@ -77,9 +91,10 @@ cudaError_t launch_winv(const double2* P, float2* WmH, int F, int* err, cudaStre
 
 template <int M, int N>
 cudaError_t launch_mwf(const float2* x, const double2* P, const float2* WmH, const float* lam,
-                       const float* v, float2* c, int F, int T, int /*N*/, cudaStream_t s) {
+                       const float* v, float2* c, int F, int T, int /*N*/, int B, cudaStream_t s) {
+  if (B < 1 || T % B != 0) return cudaErrorInvalidValue;
   dim3 grid(F, (T + kMwfThreads - 1) / kMwfThreads);
-  fastfca_mwf_kernel<M, N><<<grid, kMwfThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T);
+  fastfca_mwf_kernel<M, N><<<grid, kMwfThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T, B);
   return cudaGetLastError();
 }
 
@@ -88,6 +103,9 @@ FastOps make_fast_ops() {
   FastOps o;
   o.em = &launch_em<M, N>;
   o.em_mm = &launch_em<M, N, true>;
+  o.em_blk = &launch_em<M, N, false, true>;
+  o.em_mm_blk = &launch_em<M, N, true, true>;
+  o.block_stats = &launch_block_stats<M>;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf<M, N>;
   o.em_persistent = &launch_em_persistent<M, N>;
@@ -145,8 +163,8 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
 
 template <int M>
 cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
-                            float2* c, int F, int T, int N, cudaStream_t s) {
-  if (N < 1 || N > kMwfWMaxN) return cudaErrorInvalidValue;
+                            float2* c, int F, int T, int N, int B, cudaStream_t s) {
+  if (N < 1 || N > kMwfWMaxN || B != 1) return cudaErrorInvalidValue;
   dim3 grid(F, (T + kMwfWFrames - 1) / kMwfWFrames);
   fastfca_mwf_wide_kernel<M><<<grid, M * 32, 0, s>>>(x, P, WmH, lam, v, c, F, T, N);
   return cudaGetLastError();
@@ -157,6 +175,9 @@ FastOps make_cluster_ops() {
   FastOps o{};
   o.em = &launch_em_cluster<M>;
   o.em_mm = nullptr;
+  o.em_blk = nullptr;
+  o.em_mm_blk = nullptr;
+  o.block_stats = nullptr;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf_wide<M>;
   o.em_persistent = nullptr;

@@ -92,7 +92,7 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
   cudaError_t e = ops.winv(static_cast<const double2*>(P), winv, F, status, s);
   if (e == cudaSuccess)
     e = ops.mwf(static_cast<const float2*>(x), static_cast<const double2*>(P), winv, lam, v,
-                static_cast<float2*>(c), F, T, N, s);
+                static_cast<float2*>(c), F, T, N, 1, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(FASTFCA_ECUDA, cudaGetErrorString(e));

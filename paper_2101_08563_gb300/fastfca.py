@@ -30,6 +30,7 @@ MODEL_FASTFCA_MM = 2
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "fastfca_create": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "fastfca_create_blocks": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(_P)]),
     "fastfca_set_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "fastfca_get_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "fastfca_set_params_fca": (ctypes.c_int, [_P, _P, _P]),
@@ -149,7 +150,7 @@ class Separator:
     selects the random factor of the default initial v (see fastfca_create).
     """
 
-    def __init__(self, x, N: int, model: str = "fastfca", stream=None, seed: int = 0):
+    def __init__(self, x, N: int, model: str = "fastfca", stream=None, seed: int = 0, block: int = 1):
         self.lib = load()
         shape = tuple(x.shape)
         if len(shape) != 3:
@@ -161,7 +162,13 @@ class Separator:
         px, self._x = _ptr(x, np.complex64, shape, "x")
         self.stream = _default_stream() if stream is None else stream
         h = ctypes.c_void_p()
-        st = self.lib.fastfca_create(ctypes.byref(cfg), px, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        self.block = int(block)
+        self.J = self.T // self.block if self.block >= 1 else self.T   # parameter columns
+        if self.block == 1:
+            st = self.lib.fastfca_create(ctypes.byref(cfg), px, ctypes.c_void_p(self.stream), ctypes.byref(h))
+        else:
+            st = self.lib.fastfca_create_blocks(ctypes.byref(cfg), self.block, px, ctypes.c_void_p(self.stream),
+                                                ctypes.byref(h))
         if st != 0:
             raise FastFCAError(st, self.lib.fastfca_last_error(None).decode())
         self._h = h
@@ -190,14 +197,14 @@ class Separator:
 
     # ------------------------------------------------------------------ parameters
     def set_params(self, P, lam, v):
-        F, M, N, T = self.F, self.M, self.N, self.T
+        F, M, N, T = self.F, self.M, self.N, self.J
         pP, kP = _ptr(P, np.complex128, (F, M, M), "P")
         pl, kl = _ptr(lam, np.float32, (F, M, N), "lam")
         pv, kv = _ptr(v, np.float32, (F, N, T), "v")
         self._check(self.lib.fastfca_set_params(self._h, pP, pl, pv))
 
     def get_params(self):
-        F, M, N, T = self.F, self.M, self.N, self.T
+        F, M, N, T = self.F, self.M, self.N, self.J
         P = np.empty((F, M, M), np.complex128)
         lam = np.empty((F, M, N), np.float32)
         v = np.empty((F, N, T), np.float32)
@@ -207,7 +214,7 @@ class Separator:
         return P, lam, v
 
     def get_params_into(self, P=None, lam=None, v=None):
-        F, M, N, T = self.F, self.M, self.N, self.T
+        F, M, N, T = self.F, self.M, self.N, self.J
         self._check(self.lib.fastfca_get_params(self._h, _ptr(P, np.complex128, (F, M, M), "P", True)[0],
                                                 _ptr(lam, np.float32, (F, M, N), "lam", True)[0],
                                                 _ptr(v, np.float32, (F, N, T), "v", True)[0]))

@@ -267,3 +267,52 @@ def test_ip_mm_monotone_and_limits(ff):
     x = torch.zeros((2, 64, 8), dtype=torch.complex64, device="cuda")
     with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
         ff.Separator(x, 12, model="fastfca_mm")
+
+
+# ---------------------------------------------------------------------------- piecewise stationary (Sec. VI-B)
+@pytest.mark.parametrize("M,N,F,T,B,algorithm", [
+    (2, 3, 7, 250, 2, "em"),
+    (3, 5, 4, 500, 4, "em"),
+    (4, 6, 3, 1250, 5, "em"),
+    (4, 6, 3, 1250, 5, "mm"),
+    (3, 4, 3, 96, 8, "mm"),
+])
+def test_block_input_parity(ff, M, N, F, T, B, algorithm):
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=60 + B)
+    J = T // B
+    rng = np.random.Generator(np.random.PCG64(60 + B))
+    P = np.tile(np.eye(M, dtype=np.complex128), (F, 1, 1))
+    lam = np.ones((F, M, N), np.float32)
+    # start: block power of the mixture times a seeded factor (the frame-wise start per block)
+    pw = (np.abs(mix.x) ** 2).sum(axis=2).reshape(F, J, B).mean(axis=2) / (M * N)
+    v = (pw[:, None, :] * rng.uniform(0.5, 1.5, (F, N, J))).astype(np.float32)
+    model = "fastfca" if algorithm == "em" else "fastfca_mm"
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N, model=model, block=B)
+    sep.set_params(P, lam, v)
+    ll = sep.iterate(4)
+    c = sep.separate()
+    sep.close()
+    ref = off.run(mix.x, P, lam, v, iters=4, algorithm=algorithm, block=B)
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
+    cr = np.stack([off.separate_blocks(mix.x[f], ref["W"][f], ref["L"][f], ref["H"][f], B) for f in range(F)])
+    assert rel(c, cr) <= IMG_TOL
+    assert rel(c.sum(axis=2), mix.x) < 1e-5
+
+
+def test_block_input_errors(ff):
+    x = torch.zeros((2, 100, 3), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ff.FastFCAError, match="EINVAL"):
+        ff.Separator(x, 4, block=7)                       # 7 does not divide 100
+    with pytest.raises(ff.FastFCAError, match="EINVAL"):
+        ff.Separator(x, 4, model="fca", block=4)
+    x = torch.zeros((1, 2500 * 2, 2), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
+        ff.Separator(x, 3, block=2)                       # 2500 blocks
+    # the default start of a block context is a valid start
+    mix = synth.generate_mixture(2, 3, 4, 120, 4, seed=5)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 3, block=4, seed=3)
+    ll = sep.iterate(5)
+    P, lam, v = sep.get_params()
+    assert v.shape == (4, 3, 30) and np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
+    sep.close()

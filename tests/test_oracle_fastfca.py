@@ -430,3 +430,22 @@ def test_ip_mm_log_likelihood_is_monotone():
     for f in range(3):
         ll = ref["ll"][f]
         assert np.all(np.diff(ll) >= -1e-9 * np.abs(ll[1:]))
+
+
+def test_block_separation_equals_the_frame_filter_with_repeated_powers(rng):
+    """Sec. VI-B: frames of one block share their covariances, so the block filter of every
+    frame is the frame-wise Eq. 39 filter with that block's powers (checked per frame with the
+    explicit FCA filter of Eq. 7 under Eq. 19)."""
+    M, N, B, J = 3, 4, 5, 4
+    x = rand_complex(rng, B * J, M)
+    W = rand_complex(rng, M, M) + 2 * np.eye(M)
+    L = rng.uniform(0.3, 2.0, (M, N))
+    H = rng.uniform(0.3, 2.0, (N, J))
+    c = ff.separate_blocks(x, W, L, H, B)
+    Wi = np.linalg.inv(W)
+    for t in range(B * J):
+        j = t // B
+        Rs = [Wi.conj().T @ np.diag(L[:, n] * H[n, j]) @ Wi for n in range(N)]
+        X = sum(Rs)
+        for n in range(N):
+            assert np.allclose(c[t, n], Rs[n] @ np.linalg.solve(X, x[t]), atol=1e-10)
