@@ -66,8 +66,10 @@ typedef enum {
 typedef enum {
   FASTFCA_MODEL_FASTFCA = 0,    /* joint-diagonalisation model, Sec. IV, IP+EM (Algorithm 1) */
   FASTFCA_MODEL_FCA = 1,        /* full-rank FCA, Sec. III (comparison model) */
-  FASTFCA_MODEL_FASTFCA_MM = 2  /* the FastFCA model fitted by IP+MM (Algorithm 2); same
+  FASTFCA_MODEL_FASTFCA_MM = 2, /* the FastFCA model fitted by IP+MM (Algorithm 2); same
                                    parameters and calls as FASTFCA; M 2..4, N 2..8, T <= 2048 */
+  FASTFCA_MODEL_FCA_MM = 3      /* full-rank FCA fitted by MM (Eq. 15-17, geometric-mean R
+                                   update); same parameters and calls as FCA */
 } fastfca_model;
 
 typedef struct {
@@ -99,7 +101,7 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
  * columns where fastfca_create's contexts have T: v float32 [F][N][J], the log-likelihood
  * is Eq. 44's (per block).  fastfca_separate filters every frame with the powers of its
  * block (c complex64 [F][T][N][M]).  B = 1 is fastfca_create.  EINVAL unless B divides T;
- * EUNSUPPORTED outside M 2..4, N 2..8, J <= 2048, or for the FCA model. */
+ * EUNSUPPORTED outside M 2..4, N 2..8, J <= 2048, or for the FCA models. */
 fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
                                      fastfca_ctx** out);
 
@@ -112,14 +114,15 @@ fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* 
  * NULL to skip).  Synchronises the stream. */
 fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* v);
 
-/* FCA model: replaces R complex128 [F][N][M][M] and h float32 [F][N][T]. */
+/* FCA models (FCA, FCA_MM): replaces R complex128 [F][N][M][M] and h float32 [F][N][T]. */
 fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const float* h);
 
-/* FCA model: copies R and h out (host or device; NULL skips).  Synchronises. */
+/* FCA models: copies R and h out (host or device; NULL skips).  Synchronises. */
 fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h);
 
 /* Runs n_iter iterations of the model's algorithm on every frequency: FastFCA IP+EM
- * (Algorithm 1, Sec. IV-E) or FCA EM (Eq. 12-13).  n_iter >= 1.  If ll_per_iter is not
+ * (Algorithm 1, Sec. IV-E), FastFCA IP+MM (Algorithm 2), FCA EM (Eq. 12-13) or FCA MM
+ * (Eq. 15-17).  n_iter >= 1.  If ll_per_iter is not
  * NULL (host or device, n_iter doubles) it receives the total log-likelihood sum_f l_f
  * after each iteration,
  * l_f = T ln|det W_f|^2 - sum_{m,t} (|y_mt|^2 / sigma^2_mt + ln sigma^2_mt) - M T ln(pi)
@@ -134,7 +137,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
 fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per_f);
 
 /* Source images by the multichannel Wiener filter of the current parameters: FastFCA
- * Eq. 39 (c = W^{-H} diag(g_n) W^H x), FCA Eq. 7 (c = h_n R_n X^{-1} x).  c is complex64
+ * Eq. 39 (c = W^{-H} diag(g_n) W^H x), FCA (both fits) Eq. 7 (c = h_n R_n X^{-1} x).  c is complex64
  * [F][T][N][M], host or device, caller-allocated.  Stream-ordered and asynchronous for both:
  * a host c (pinned for a truly asynchronous copy) holds the images once the context's
  * stream has passed the call, e.g. after fastfca_sync, which also reports any kernel

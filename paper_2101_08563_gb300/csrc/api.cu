@@ -113,6 +113,8 @@ size_t FT(const fastfca_config& c) { return (size_t)c.F * c.T; }
 
 // The FastFCA model, fitted by IP+EM (Algorithm 1) or IP+MM (Algorithm 2): the same parameters.
 bool fastfca_family(int model) { return model == FASTFCA_MODEL_FASTFCA || model == FASTFCA_MODEL_FASTFCA_MM; }
+// The full-rank FCA model, fitted by EM (Eq. 12-13) or MM (Eq. 15-17).
+bool fca_family(int model) { return model == FASTFCA_MODEL_FCA || model == FASTFCA_MODEL_FCA_MM; }
 
 fastfca_status check_ready(fastfca_ctx* c) {
   if (!c) return FASTFCA_EINVAL;
@@ -226,7 +228,7 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* 
   fastfca_config c = *cfg;
   if (c.F < 1 || c.T < 1 || c.M < 1 || c.N < 1)
     return fail(nullptr, FASTFCA_EINVAL, "F, T, M, N must be positive (got %d %d %d %d)", c.F, c.T, c.M, c.N);
-  if (!fastfca_family(c.model) && c.model != FASTFCA_MODEL_FCA)
+  if (!fastfca_family(c.model) && !fca_family(c.model))
     return fail(nullptr, FASTFCA_EINVAL, "unknown model %d", c.model);
   if (B < 1 || c.T % B != 0)
     return fail(nullptr, FASTFCA_EINVAL, "the block size B=%d must be >= 1 and divide T=%d", B, c.T);
@@ -373,7 +375,7 @@ fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* 
 fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const float* h) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (ctx->cfg.model != FASTFCA_MODEL_FCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
   if (!R || !h) return fail(ctx, FASTFCA_EINVAL, "R and h are required");
   const fastfca_config& c = ctx->cfg;
   CK(ctx, to_device(ctx->R, R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R upload");
@@ -385,7 +387,7 @@ fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const flo
 fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (ctx->cfg.model != FASTFCA_MODEL_FCA) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
   const fastfca_config& c = ctx->cfg;
   if (R) CK(ctx, from_device(R, ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R download");
   if (h) CK(ctx, from_device(h, ctx->h, sizeof(float) * FT(c) * c.N, ctx->stream), "h download");
@@ -437,7 +439,8 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     a.T = c.T;
     a.n_iter = n_iter;
     a.ll_stride = n_iter;
-    CK(ctx, ctx->fops.em(a, &ctx->fca, ctx->stream), "FCA EM launch");
+    auto launch = c.model == FASTFCA_MODEL_FCA_MM ? ctx->fops.em_mm : ctx->fops.em;
+    CK(ctx, launch(a, &ctx->fca, ctx->stream), "FCA EM/MM launch");
   }
   if (!ll_per_iter) return FASTFCA_OK;
   sum_over_f_kernel<<<(n_iter + 127) / 128, 128, 0, ctx->stream>>>(ctx->ll_hist, c.F, n_iter, n_iter, ctx->ll_sum);

@@ -25,6 +25,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "EUNS
 MODEL_FASTFCA = 0
 MODEL_FCA = 1
 MODEL_FASTFCA_MM = 2
+MODEL_FCA_MM = 3
 
 # Every entry point of include/fastfca.h with (restype, argtypes).
 _P = ctypes.c_void_p
@@ -145,7 +146,8 @@ class Separator:
     """One separation problem (one mixture) held by the library.
 
     x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" (IP+EM,
-    Algorithm 1), "fastfca_mm" (the same model by IP+MM, Algorithm 2) or "fca".
+    Algorithm 1), "fastfca_mm" (the same model by IP+MM, Algorithm 2), "fca" (full-rank FCA by EM,
+    Eq. 12-13) or "fca_mm" (the same model by MM, Eq. 15-17).
     A CUDA x is borrowed (kept referenced here); a host x is copied by the library.  seed
     selects the random factor of the default initial v (see fastfca_create).
     """
@@ -157,7 +159,8 @@ class Separator:
             raise ValueError("x must have shape (F, T, M)")
         self.F, self.T, self.M = (int(s) for s in shape)
         self.N = int(N)
-        self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA, "fastfca_mm": MODEL_FASTFCA_MM}[model]
+        self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA, "fastfca_mm": MODEL_FASTFCA_MM,
+                      "fca_mm": MODEL_FCA_MM}[model]
         cfg = Config(self.F, self.T, self.M, self.N, self.model, int(seed) & 0x7fffffff)
         px, self._x = _ptr(x, np.complex64, shape, "x")
         self.stream = _default_stream() if stream is None else stream
