@@ -9,7 +9,9 @@ no Wiener filter).  It produces
   v_n(t,f) = sum_k B_n(f,k) A_n(k,t) (nonnegative factors with Gamma(1,1) entries) and
   R_n(f) = a_n(f) a_n(f)^H + 0.01 I, a_n(f) the far-field steering vector of the array;
 * the random starting point that both the CUDA path and the oracle are given:
-  P_f = I, lambda_n(f) = 1 and v_n(t,f) = (||x(t,f)||^2 / (M N)) * u, u ~ U[0.5, 1.5).
+  P_f = I, lambda_n(f) = 1 and v_n(t,f) = (||x(t,f)||^2 / (M N)) * u, u ~ U[0.5, 1.5);
+* the FastMNMF starting point (App. C): W_i = I, lambda = 1, bases and activations from the
+  frequency and frame marginals of ||x||^2 / (M N), each times its own u ~ U[0.5, 1.5).
 
 The paper evaluates on recorded room impulse responses and speech (Sec. VII); those are not
 available, so these model-generated mixtures with the paper's STFT shape family stand in.
@@ -144,3 +146,27 @@ def fca_random_init(x: np.ndarray, N: int, *, seed: int):
     p = random_init(x, N, seed=seed)
     R = np.broadcast_to(np.eye(M, dtype=np.complex128), (F, N, M, M)).copy()
     return R, p.v
+
+
+@dataclass
+class FastMNMFInit:
+    W: np.ndarray     # (F, M, M) complex128, demixing matrices
+    lam: np.ndarray   # (F, M, N) float32, spatial weights lambda_imn
+    t: np.ndarray     # (F, K, N) float32, bases t_ikn
+    v: np.ndarray     # (T, K, N) float32, activations v_jkn
+
+
+def fastmnmf_random_init(x: np.ndarray, N: int, K: int, *, seed: int) -> FastMNMFInit:
+    """W = I, lambda = 1; with p_ij = ||x_ij||^2 / (M N):
+    t_ikn = (mean_j p_ij / K) u and v_jkn = (mean_i p_ij / mean_ij p_ij) u', u, u' ~ U[0.5, 1.5),
+    so that sum_k t v starts near the separable part of p (float32 values)."""
+    F, T, M = x.shape
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x3A3F))
+    p = (np.abs(x.astype(np.complex128)) ** 2).sum(axis=2) / (M * N)     # (F, T)
+    pf = p.mean(axis=1)
+    pt = p.mean(axis=0) / p.mean()
+    t = (pf[:, None, None] / K * rng.uniform(0.5, 1.5, size=(F, K, N))).astype(np.float32)
+    v = (pt[:, None, None] * rng.uniform(0.5, 1.5, size=(T, K, N))).astype(np.float32)
+    W = np.broadcast_to(np.eye(M, dtype=np.complex128), (F, M, M)).copy()
+    lam = np.ones((F, M, N), dtype=np.float32)
+    return FastMNMFInit(W=W, lam=lam, t=np.maximum(t, np.float32(1e-30)), v=np.maximum(v, np.float32(1e-30)))
