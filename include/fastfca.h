@@ -68,8 +68,11 @@ typedef enum {
   FASTFCA_MODEL_FCA = 1,        /* full-rank FCA, Sec. III (comparison model) */
   FASTFCA_MODEL_FASTFCA_MM = 2, /* the FastFCA model fitted by IP+MM (Algorithm 2); same
                                    parameters and calls as FASTFCA; M 2..4, N 2..8, T <= 2048 */
-  FASTFCA_MODEL_FCA_MM = 3      /* full-rank FCA fitted by MM (Eq. 15-17, geometric-mean R
+  FASTFCA_MODEL_FCA_MM = 3,     /* full-rank FCA fitted by MM (Eq. 15-17, geometric-mean R
                                    update); same parameters and calls as FCA */
+  FASTFCA_MODEL_FASTMNMF = 4    /* FastMNMF (Sec. IV-H, App. C): FastFCA with the source powers
+                                   factored across frequencies, h_ijn = sum_k t_ikn v_jkn
+                                   (Eq. 52); created by fastfca_create_mnmf */
 } fastfca_model;
 
 typedef struct {
@@ -114,6 +117,29 @@ fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* 
  * NULL to skip).  Synchronises the stream. */
 fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* v);
 
+/* FastMNMF (App. C): the FastFCA model in every frequency i (demixing W_i, weights
+ * lambda_imn) with the source powers h_ijn = sum_k t_ikn v_jkn (Eq. 52) shared across
+ * frequencies through the activations v, fitted by minimising Eq. 53.  One fastfca_iterate
+ * iteration runs IP (Eq. 33-35) in every frequency, then the exponent-1/2 multiplicative MM
+ * updates of lambda, t and v in that order (the rules Algorithm 2 gives for L and H, applied to
+ * each factor; sigma^2 recomputed before each); the v update sums over all frequencies.
+ * cfg->model must be FASTFCA_MODEL_FASTMNMF; K is the number of bases per source, 1..16;
+ * M 2..4, N 2..8, T <= 2048, F*K <= 40960.  x as for fastfca_create.  The default start is W = I,
+ * lambda = 1, t_ikn = (mean_j p_ij / K) u, v_jkn = (mean_i p_ij / mean p) u', p_ij =
+ * ||x_ij||^2 / (M N), u and u' ~ U[0.5, 1.5) from Philox4x32-10 keyed by cfg->seed.
+ * fastfca_iterate, fastfca_loglik (Eq. 53 negated, with -M T ln(pi) per frequency),
+ * fastfca_separate (Eq. 39 with h from Eq. 52), fastfca_set_mixture, fastfca_sync and
+ * fastfca_destroy take the context.  Errors as for fastfca_create, EINVAL for K out of range. */
+fastfca_status fastfca_create_mnmf(const fastfca_config* cfg, int32_t K, const void* x, void* stream,
+                                   fastfca_ctx** out);
+
+/* FastMNMF parameters (host or device): W complex128 [F][M][M] (W[a][m] at (f*M + a)*M + m),
+ * lam float32 [F][M][N], t float32 [F][N][K] (t_ikn at (i*N + n)*K + k), v float32 [N][K][T]
+ * (v_jkn at (n*K + k)*T + j).  set: all four required; get: NULL skips, synchronises. */
+fastfca_status fastfca_set_params_mnmf(fastfca_ctx* ctx, const void* W, const float* lam, const float* t,
+                                       const float* v);
+fastfca_status fastfca_get_params_mnmf(fastfca_ctx* ctx, void* W, float* lam, float* t, float* v);
+
 /* FCA models (FCA, FCA_MM): replaces R complex128 [F][N][M][M] and h float32 [F][N][T]. */
 fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const float* h);
 
@@ -121,8 +147,8 @@ fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const flo
 fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h);
 
 /* Runs n_iter iterations of the model's algorithm on every frequency: FastFCA IP+EM
- * (Algorithm 1, Sec. IV-E), FastFCA IP+MM (Algorithm 2), FCA EM (Eq. 12-13) or FCA MM
- * (Eq. 15-17).  n_iter >= 1.  If ll_per_iter is not
+ * (Algorithm 1, Sec. IV-E), FastFCA IP+MM (Algorithm 2), FCA EM (Eq. 12-13), FCA MM
+ * (Eq. 15-17) or FastMNMF (App. C; see fastfca_create_mnmf).  n_iter >= 1.  If ll_per_iter is not
  * NULL (host or device, n_iter doubles) it receives the total log-likelihood sum_f l_f
  * after each iteration,
  * l_f = T ln|det W_f|^2 - sum_{m,t} (|y_mt|^2 / sigma^2_mt + ln sigma^2_mt) - M T ln(pi)

@@ -22,6 +22,7 @@ LIB_NAME = "libfastfca.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 SOURCES = ["api.cu", "fastfca_m2.cu", "fastfca_m3.cu", "fastfca_m4.cu", "fca_ops.cu", "noalloc.cu", "batch.cu",
+           "fastmnmf_m2.cu", "fastmnmf_m3.cu", "fastmnmf_m4.cu", "fastmnmf_common.cu",
            "learn.cu", "fastfca_cluster_lo.cu", "fastfca_cluster_hi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -11,6 +11,7 @@
 
 #include "../../include/fastfca.h"
 #include "fca.cuh"
+#include "fastmnmf.cuh"
 #include "init.cuh"
 #include "launch.cuh"
 
@@ -43,6 +44,13 @@ struct fastfca_ctx {
   double2* Bst = nullptr;        // W^{-H} (FP64) carried between FastFCA launches
   double* detst = nullptr;       // |det W|^2 as (mantissa, exponent) per frequency
   int b_valid = 0;               // Bst/detst match the current P
+  // FastMNMF parameters (P, lam, Bst, detst, winv as above; v holds h = t v for the filter)
+  int K = 0;
+  float* tb = nullptr;           // F x N x K bases
+  float* va = nullptr;           // N x K x T activations
+  float* ab = nullptr;           // 2 x F x N x T per-bin terms of the activation update
+  float* mscratch = nullptr;     // F + T + 1 floats (default start)
+  ffca::MnmfOps mops{};
   // FCA parameters
   double2* R = nullptr;
   float* h = nullptr;
@@ -191,6 +199,10 @@ void free_all(fastfca_ctx* c) {
   cudaFree(c->winv);
   cudaFree(c->Bst);
   cudaFree(c->detst);
+  cudaFree(c->tb);
+  cudaFree(c->va);
+  cudaFree(c->ab);
+  cudaFree(c->mscratch);
   cudaFree(c->R);
   cudaFree(c->h);
   ffca::fca_work_free(&c->fca);
@@ -221,22 +233,37 @@ const char* fastfca_version(void) { return "fastfca-gb300 0.1 (sm_103a)"; }
 
 const char* fastfca_last_error(const fastfca_ctx* ctx) { return ctx ? ctx->msg : g_create_error; }
 
-static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* x, void* stream, fastfca_ctx** out) {
+static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const void* x, void* stream,
+                                  fastfca_ctx** out) {
   if (!out) return fail(nullptr, FASTFCA_EINVAL, "out is NULL");
   *out = nullptr;
   if (!cfg || !x) return fail(nullptr, FASTFCA_EINVAL, "cfg and x are required");
   fastfca_config c = *cfg;
   if (c.F < 1 || c.T < 1 || c.M < 1 || c.N < 1)
     return fail(nullptr, FASTFCA_EINVAL, "F, T, M, N must be positive (got %d %d %d %d)", c.F, c.T, c.M, c.N);
-  if (!fastfca_family(c.model) && !fca_family(c.model))
+  const bool mnmf = c.model == FASTFCA_MODEL_FASTMNMF;
+  if (!fastfca_family(c.model) && !fca_family(c.model) && !mnmf)
     return fail(nullptr, FASTFCA_EINVAL, "unknown model %d", c.model);
+  if (mnmf != (K > 0))
+    return fail(nullptr, FASTFCA_EINVAL, mnmf ? "FastMNMF contexts are created by fastfca_create_mnmf"
+                                              : "fastfca_create_mnmf needs cfg->model = FASTFCA_MODEL_FASTMNMF");
+  if (mnmf && K > ffca::kMnmfMaxK)
+    return fail(nullptr, FASTFCA_EINVAL, "K=%d bases per source is outside 1..%d", K, ffca::kMnmfMaxK);
   if (B < 1 || c.T % B != 0)
     return fail(nullptr, FASTFCA_EINVAL, "the block size B=%d must be >= 1 and divide T=%d", B, c.T);
   const int Tf = c.T;
   c.T = Tf / B;                                   // parameter columns: blocks
   ffca::FastOps ops{};
   ffca::FcaOps fops{};
-  if (B > 1) {
+  ffca::MnmfOps mops{};
+  if (mnmf) {
+    if (!ffca::fast_ops(c.M, c.N, &ops) || !ffca::mnmf_ops(c.M, c.N, &mops) || c.T > mops.max_T)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "FastMNMF runs on M in 2..4, N in 2..8 and T <= %d",
+                  ffca::kMaxThreads * ffca::kSlots);
+    if ((long long)c.F * K > ffca::kMnmfMaxFK)
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "FastMNMF holds F*K <= %d bases of one source on chip (F=%d, K=%d)",
+                  ffca::kMnmfMaxFK, c.F, K);
+  } else if (B > 1) {
     if (!fastfca_family(c.model))
       return fail(nullptr, FASTFCA_EINVAL, "the piecewise-stationary input serves the FastFCA models only");
     if (!ffca::fast_ops(c.M, c.N, &ops) || c.T > ops.max_T || !ops.em_blk)
@@ -263,6 +290,8 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* 
   ctx->stream = (cudaStream_t)stream;
   ctx->ops = ops;
   ctx->fops = fops;
+  ctx->mops = mops;
+  ctx->K = K;
   const size_t nx = (size_t)c.F * Tf * c.M;
   auto bail = [&](fastfca_status st) {
     snprintf(g_create_error, sizeof g_create_error, "%s", ctx->msg);
@@ -286,7 +315,21 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* 
   CKC(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "status clear");
   CKC(cudaMalloc(&ctx->ll_last, sizeof(double) * c.F), "ll alloc");
   const int threads = 256;
-  if (fastfca_family(c.model)) {
+  if (mnmf) {
+    CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "W alloc");
+    CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "h alloc");
+    CKC(cudaMalloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    CKC(cudaMalloc(&ctx->tb, sizeof(float) * (size_t)c.F * c.N * K), "t alloc");
+    CKC(cudaMalloc(&ctx->va, sizeof(float) * (size_t)c.N * K * c.T), "v alloc");
+    CKC(cudaMalloc(&ctx->ab, sizeof(float) * 2 * FT(c) * c.N), "activation-update terms alloc");
+    CKC(cudaMalloc(&ctx->mscratch, sizeof(float) * ((size_t)c.F + c.T + 1)), "scratch alloc");
+    CKC(ffca::launch_mnmf_default(ctx->x, ctx->P, ctx->lam, ctx->tb, ctx->va, ctx->mscratch, c.F, c.T, c.M, c.N, K,
+                                  (uint32_t)c.seed, ctx->stream),
+        "init launch");
+  } else if (fastfca_family(c.model)) {
     CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
     CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
     CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "v alloc");
@@ -331,13 +374,83 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, const void* 
 }
 
 fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream, fastfca_ctx** out) {
-  return create_impl(cfg, 1, x, stream, out);
+  return create_impl(cfg, 1, 0, x, stream, out);
 }
 
 fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
                                      fastfca_ctx** out) {
-  return create_impl(cfg, B, x, stream, out);
+  return create_impl(cfg, B, 0, x, stream, out);
 }
+
+fastfca_status fastfca_create_mnmf(const fastfca_config* cfg, int32_t K, const void* x, void* stream,
+                                   fastfca_ctx** out) {
+  if (K < 1) {
+    if (out) *out = nullptr;
+    return fail(nullptr, FASTFCA_EINVAL, "K=%d bases per source is outside 1..%d", K, ffca::kMnmfMaxK);
+  }
+  return create_impl(cfg, 1, K, x, stream, out);
+}
+
+fastfca_status fastfca_set_params_mnmf(fastfca_ctx* ctx, const void* W, const float* lam, const float* t,
+                                       const float* v) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FASTMNMF) return fail(ctx, FASTFCA_EINVAL, "context does not hold FastMNMF");
+  if (!W || !lam || !t || !v) return fail(ctx, FASTFCA_EINVAL, "W, lam, t and v are required");
+  const fastfca_config& c = ctx->cfg;
+  CK(ctx, to_device(ctx->P, W, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "W upload");
+  CK(ctx, to_device(ctx->lam, lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam upload");
+  CK(ctx, to_device(ctx->tb, t, sizeof(float) * (size_t)c.F * c.N * ctx->K, ctx->stream), "t upload");
+  CK(ctx, to_device(ctx->va, v, sizeof(float) * (size_t)c.N * ctx->K * c.T, ctx->stream), "v upload");
+  ctx->b_valid = 0;
+  if (ctx->sticky == FASTFCA_ENUMERIC) ctx->sticky = FASTFCA_OK;
+  return FASTFCA_OK;
+}
+
+fastfca_status fastfca_get_params_mnmf(fastfca_ctx* ctx, void* W, float* lam, float* t, float* v) {
+  fastfca_status st = check_ready(ctx);
+  if (st) return st;
+  if (ctx->cfg.model != FASTFCA_MODEL_FASTMNMF) return fail(ctx, FASTFCA_EINVAL, "context does not hold FastMNMF");
+  const fastfca_config& c = ctx->cfg;
+  if (W) CK(ctx, from_device(W, ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "W download");
+  if (lam) CK(ctx, from_device(lam, ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam download");
+  if (t) CK(ctx, from_device(t, ctx->tb, sizeof(float) * (size_t)c.F * c.N * ctx->K, ctx->stream), "t download");
+  if (v) CK(ctx, from_device(v, ctx->va, sizeof(float) * (size_t)c.N * ctx->K * c.T, ctx->stream), "v download");
+  return collect_device_status(ctx);
+}
+
+}  // extern "C"
+
+namespace {
+// One FastMNMF launch of the per-frequency kernel (iterate = 1: one iteration; 0: the
+// log-likelihood of the current parameters only).
+fastfca_status mnmf_freq(fastfca_ctx* ctx, int iterate, double* ll_out, int ll_stride, double* ll_last) {
+  const fastfca_config& c = ctx->cfg;
+  ffca::MnmfArgs a{};
+  a.x = ctx->x;
+  a.P = ctx->P;
+  a.Bst = ctx->Bst;
+  a.detst = ctx->detst;
+  a.b_valid = ctx->b_valid;
+  a.lam = ctx->lam;
+  a.tb = ctx->tb;
+  a.va = ctx->va;
+  a.ab = ctx->ab;
+  a.ll_out = ll_out;
+  a.ll_last = ll_last;
+  a.err = ctx->err;
+  a.F = c.F;
+  a.T = c.T;
+  a.K = ctx->K;
+  a.ll_stride = ll_stride;
+  a.iterate = iterate;
+  CK(ctx, ctx->mops.freq(a, ctx->stream), "FastMNMF frequency launch");
+  ctx->b_valid = 1;
+  return FASTFCA_OK;
+}
+}  // namespace
+
+extern "C" {
 
 void fastfca_destroy(fastfca_ctx* ctx) {
   if (!ctx) return;
@@ -350,7 +463,7 @@ void fastfca_destroy(fastfca_ctx* ctx) {
 fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* lam, const float* v) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context does not hold the FastFCA model");
   if (!P || !lam || !v) return fail(ctx, FASTFCA_EINVAL, "P, lam and v are required");
   const fastfca_config& c = ctx->cfg;
   CK(ctx, to_device(ctx->P, P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P upload");
@@ -364,7 +477,7 @@ fastfca_status fastfca_set_params(fastfca_ctx* ctx, const void* P, const float* 
 fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* v) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FCA model");
+  if (!fastfca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context does not hold the FastFCA model");
   const fastfca_config& c = ctx->cfg;
   if (P) CK(ctx, from_device(P, ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M, ctx->stream), "P download");
   if (lam) CK(ctx, from_device(lam, ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N, ctx->stream), "lam download");
@@ -375,7 +488,7 @@ fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* 
 fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const float* h) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context does not hold the FCA model");
   if (!R || !h) return fail(ctx, FASTFCA_EINVAL, "R and h are required");
   const fastfca_config& c = ctx->cfg;
   CK(ctx, to_device(ctx->R, R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R upload");
@@ -387,7 +500,7 @@ fastfca_status fastfca_set_params_fca(fastfca_ctx* ctx, const void* R, const flo
 fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h) {
   fastfca_status st = check_ready(ctx);
   if (st) return st;
-  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context holds the FastFCA model");
+  if (!fca_family(ctx->cfg.model)) return fail(ctx, FASTFCA_EINVAL, "context does not hold the FCA model");
   const fastfca_config& c = ctx->cfg;
   if (R) CK(ctx, from_device(R, ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M, ctx->stream), "R download");
   if (h) CK(ctx, from_device(h, ctx->h, sizeof(float) * FT(c) * c.N, ctx->stream), "h download");
@@ -405,7 +518,19 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     if (st) return st;
     hist = ctx->ll_hist;
   }
-  if (fastfca_family(c.model)) {
+  if (c.model == FASTFCA_MODEL_FASTMNMF) {
+    // launch it of the per-frequency kernel also gives the log-likelihood after iteration it-1
+    for (int it = 0; it < n_iter; ++it) {
+      st = mnmf_freq(ctx, 1, (hist && it > 0) ? hist + (it - 1) : nullptr, n_iter, nullptr);
+      if (st) return st;
+      CK(ctx, ffca::launch_mnmf_v(ctx->tb, ctx->ab, ctx->va, c.F, c.N, ctx->K, c.T, ctx->stream),
+         "FastMNMF activation update launch");
+    }
+    if (hist) {
+      st = mnmf_freq(ctx, 0, hist + (n_iter - 1), n_iter, ctx->ll_last);
+      if (st) return st;
+    }
+  } else if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
     a.xh = ctx->xh;
@@ -455,7 +580,10 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
   fastfca_status st = check_ready(ctx);
   if (st) return st;
   const fastfca_config& c = ctx->cfg;
-  if (fastfca_family(c.model)) {
+  if (c.model == FASTFCA_MODEL_FASTMNMF) {
+    st = mnmf_freq(ctx, 0, nullptr, 0, ctx->ll_last);
+    if (st) return st;
+  } else if (fastfca_family(c.model)) {
     ffca::EmArgs a{};
     a.x = ctx->x;
     a.xh = ctx->xh;
@@ -511,13 +639,16 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
     CK(ctx, cudaMallocAsync(&tmp, bytes, ctx->stream), "c staging alloc");
     dst = tmp;
   }
-  cudaError_t e;
-  if (fastfca_family(c.model)) {
-    if (ctx->b_valid) {
+  cudaError_t e = cudaSuccess;
+  if (fastfca_family(c.model) || c.model == FASTFCA_MODEL_FASTMNMF) {
+    // FastMNMF: h = t v (Eq. 52) into the FastFCA filter's H, then the same filter (Eq. 39)
+    if (c.model == FASTFCA_MODEL_FASTMNMF)
+      e = ffca::launch_mnmf_h(ctx->tb, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream);
+    if (e == cudaSuccess && ctx->b_valid) {
       const size_t n = (size_t)c.F * c.M * c.M;
       bst_to_winv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->Bst, ctx->winv, n);
       e = cudaGetLastError();
-    } else {
+    } else if (e == cudaSuccess) {
       e = ctx->ops.winv(ctx->P, ctx->winv, c.F, ctx->err, ctx->stream);
     }
     if (e == cudaSuccess)

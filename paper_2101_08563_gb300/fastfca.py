@@ -26,12 +26,16 @@ MODEL_FASTFCA = 0
 MODEL_FCA = 1
 MODEL_FASTFCA_MM = 2
 MODEL_FCA_MM = 3
+MODEL_FASTMNMF = 4
 
 # Every entry point of include/fastfca.h with (restype, argtypes).
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "fastfca_create": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_P)]),
     "fastfca_create_blocks": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(_P)]),
+    "fastfca_create_mnmf": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(_P)]),
+    "fastfca_set_params_mnmf": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "fastfca_get_params_mnmf": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "fastfca_set_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "fastfca_get_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "fastfca_set_params_fca": (ctypes.c_int, [_P, _P, _P]),
@@ -147,12 +151,14 @@ class Separator:
 
     x: complex64 (F, T, M), host or CUDA.  N: number of sources.  model: "fastfca" (IP+EM,
     Algorithm 1), "fastfca_mm" (the same model by IP+MM, Algorithm 2), "fca" (full-rank FCA by EM,
-    Eq. 12-13) or "fca_mm" (the same model by MM, Eq. 15-17).
+    Eq. 12-13), "fca_mm" (the same model by MM, Eq. 15-17) or "fastmnmf" (App. C, with
+    `bases` = K NMF bases per source; parameters through set/get_params_mnmf).
     A CUDA x is borrowed (kept referenced here); a host x is copied by the library.  seed
     selects the random factor of the default initial v (see fastfca_create).
     """
 
-    def __init__(self, x, N: int, model: str = "fastfca", stream=None, seed: int = 0, block: int = 1):
+    def __init__(self, x, N: int, model: str = "fastfca", stream=None, seed: int = 0, block: int = 1,
+                 bases: int = 0):
         self.lib = load()
         shape = tuple(x.shape)
         if len(shape) != 3:
@@ -160,14 +166,18 @@ class Separator:
         self.F, self.T, self.M = (int(s) for s in shape)
         self.N = int(N)
         self.model = {"fastfca": MODEL_FASTFCA, "fca": MODEL_FCA, "fastfca_mm": MODEL_FASTFCA_MM,
-                      "fca_mm": MODEL_FCA_MM}[model]
+                      "fca_mm": MODEL_FCA_MM, "fastmnmf": MODEL_FASTMNMF}[model]
+        self.K = int(bases)
         cfg = Config(self.F, self.T, self.M, self.N, self.model, int(seed) & 0x7fffffff)
         px, self._x = _ptr(x, np.complex64, shape, "x")
         self.stream = _default_stream() if stream is None else stream
         h = ctypes.c_void_p()
         self.block = int(block)
         self.J = self.T // self.block if self.block >= 1 else self.T   # parameter columns
-        if self.block == 1:
+        if self.model == MODEL_FASTMNMF:
+            st = self.lib.fastfca_create_mnmf(ctypes.byref(cfg), self.K, px, ctypes.c_void_p(self.stream),
+                                              ctypes.byref(h))
+        elif self.block == 1:
             st = self.lib.fastfca_create(ctypes.byref(cfg), px, ctypes.c_void_p(self.stream), ctypes.byref(h))
         else:
             st = self.lib.fastfca_create_blocks(ctypes.byref(cfg), self.block, px, ctypes.c_void_p(self.stream),
@@ -235,6 +245,28 @@ class Separator:
         self._check(self.lib.fastfca_get_params_fca(self._h, _ptr(R, np.complex128, R.shape, "R", True)[0],
                                                     _ptr(h, np.float32, h.shape, "h", True)[0]))
         return R, h
+
+    def set_params_mnmf(self, W, lam, t, v):
+        """FastMNMF parameters: W complex128 (F, M, M), lam float32 (F, M, N), t float32
+        (F, N, K) bases, v float32 (N, K, T) activations; host or CUDA."""
+        F, M, N, K, T = self.F, self.M, self.N, self.K, self.T
+        pW, kW = _ptr(W, np.complex128, (F, M, M), "W")
+        pl, kl = _ptr(lam, np.float32, (F, M, N), "lam")
+        pt, kt = _ptr(t, np.float32, (F, N, K), "t")
+        pv, kv = _ptr(v, np.float32, (N, K, T), "v")
+        self._check(self.lib.fastfca_set_params_mnmf(self._h, pW, pl, pt, pv))
+
+    def get_params_mnmf(self):
+        F, M, N, K, T = self.F, self.M, self.N, self.K, self.T
+        W = np.empty((F, M, M), np.complex128)
+        lam = np.empty((F, M, N), np.float32)
+        t = np.empty((F, N, K), np.float32)
+        v = np.empty((N, K, T), np.float32)
+        self._check(self.lib.fastfca_get_params_mnmf(self._h, _ptr(W, np.complex128, W.shape, "W", True)[0],
+                                                     _ptr(lam, np.float32, lam.shape, "lam", True)[0],
+                                                     _ptr(t, np.float32, t.shape, "t", True)[0],
+                                                     _ptr(v, np.float32, v.shape, "v", True)[0]))
+        return W, lam, t, v
 
     # ------------------------------------------------------------------ algorithm
     def iterate(self, n_iter: int, return_ll: bool = True):
