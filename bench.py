@@ -31,6 +31,14 @@ if ROOT not in sys.path:
 from paper_2101_08563_gb300 import synth  # noqa: E402
 
 WORKLOAD = synth.WORKLOADS["fca_cmp"]
+MNMF_K = 8            # FastMNMF bases per source on the bench mixture (its generator's K)
+MNMF_ITERS = 20
+
+
+def mnmf_abi_params(st):
+    """A FastMNMF start in the C ABI's layouts: t (F, N, K), v (N, K, T)."""
+    return (st.W, st.lam, np.ascontiguousarray(st.t.transpose(0, 2, 1)),
+            np.ascontiguousarray(st.v.transpose(2, 1, 0)))
 METRIC = "FastFCA EM TF-bin-iters/s"
 UNIT = "bin-iters/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -516,6 +524,25 @@ def run_gpu(args, rank, world, local_rank):
         fca_ll[model] = float(fsep.loglik()) / (w.F * w.T)
         fsep.close()
 
+    # FastMNMF (App. C) on the same mixture, K bases per source, from the same kind of start
+    st = synth.fastmnmf_random_init(mix.x, w.N, MNMF_K, seed=w.seed + rank)
+    mparams = [torch.from_numpy(a).to(dev) for a in mnmf_abi_params(st)]
+    mnsep = fastfca.Separator(x, w.N, model="fastmnmf", bases=MNMF_K, stream=stream.cuda_stream)
+    mnsep.set_params_mnmf(*mparams)
+    mnsep.iterate(2, return_ll=False)
+    mn_ms = []
+    for _ in range(3):
+        flush.zero_()
+        mnsep.set_params_mnmf(*mparams)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        mnsep.iterate(MNMF_ITERS, return_ll=False)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        mn_ms.append(a0.elapsed_time(a1))
+    mn_ll = float(mnsep.loglik()) / (w.F * w.T)
+    mnsep.close()
+
     # end-to-end through the public API with host buffers (pinned), copies inside the span:
     # every step uploads its mixture and start, runs the iterations (reading back the
     # log-likelihood per iteration) and downloads the images.  Two long-lived contexts on two
@@ -558,7 +585,8 @@ def run_gpu(args, rank, world, local_rank):
     sep.close()
     return {
         "value": value, "ms_per_step": tot_ms / args.steps, "em_ms": em_ms, "step_ms": step_ms, "sep_ms": sep_ms,
-        "clocks": clock_info, "fca_ms": fca_ms, "fca_ll": fca_ll, "fca_iters": fca_iters, "mm_ms": mm_ms, "mm_ll": mm_ll,
+        "clocks": clock_info, "fca_ms": fca_ms, "fca_ll": fca_ll, "fca_iters": fca_iters, "mn_ms": mn_ms,
+        "mn_ll": mn_ll, "mm_ms": mm_ms, "mm_ll": mm_ll,
         "mm_iters": mm_iters, "em_ll_same": em_ll_same, "em_ms_same": em_ms_same, "blk": blk, "blk_ms": blk_ms,
         "e2e_value": world * units * e2e_steps / e2e_s, "h2d": h2d, "d2h": d2h,
         "final_ll": float(ll[-1].item() if hasattr(ll[-1], "item") else ll[-1]),
@@ -567,9 +595,25 @@ def run_gpu(args, rank, world, local_rank):
 
 def run_profile_case(F, iters, workload="fca_cmp"):
     """A workload's first 8 frequencies tiled to F (so the launch has F frequencies of the
-    workload's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`."""
+    workload's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`.
+    workload "fastmnmf": the full M=4 N=6 K=8 F=513 T=1250 mixture, FastMNMF, 2 iterations
+    then `iters` (each iteration one fastmnmf_freq_kernel and one fastmnmf_v_kernel launch)."""
     import torch
     from paper_2101_08563_gb300 import build, fastfca
+    if workload == "fastmnmf":
+        w = WORKLOAD
+        mix = synth.workload_mixture(w)
+        st = synth.fastmnmf_random_init(mix.x, w.N, MNMF_K, seed=w.seed)
+        build.build()
+        sep = fastfca.Separator(torch.from_numpy(mix.x).cuda(), w.N, model="fastmnmf", bases=MNMF_K)
+        params = mnmf_abi_params(st)
+        for n in (2, iters):
+            sep.set_params_mnmf(*params)
+            sep.iterate(n, return_ll=False)
+        torch.cuda.synchronize()
+        sep.close()
+        print("profile case done")
+        return
     w = synth.WORKLOADS[workload]
     mix = synth.generate_mixture(w.M, w.N, 8, w.T, w.K, seed=w.seed, array=w.array, spacing=w.spacing,
                                  keep_images=False)
@@ -635,7 +679,7 @@ def main():
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
     ap.add_argument("--profile-F", type=int, default=608)
     ap.add_argument("--profile-iters", type=int, default=5)
-    ap.add_argument("--profile-workload", default="fca_cmp", choices=["fca_cmp", "large"])
+    ap.add_argument("--profile-workload", default="fca_cmp", choices=["fca_cmp", "large", "fastmnmf"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -747,6 +791,10 @@ def main():
                     "loglik_per_bin": r["fca_ll"][model],
                     "update": {"fca": "EM, Eq. 12-13", "fca_mm": "MM with the geometric mean, Eq. 15-17"}[model]}
             for model in ("fca", "fca_mm")},
+        "fastmnmf": {"model": "FastMNMF (App. C), K = %d bases per source, same mixture" % MNMF_K,
+                     "iters": MNMF_ITERS, "ms": statistics.mean(r["mn_ms"]),
+                     "value": w.F * w.T * MNMF_ITERS / (statistics.mean(r["mn_ms"]) * 1e-3), "unit": UNIT,
+                     "launches_per_iter": 2, "loglik_per_bin": r["mn_ll"]},
         "em_launch_ms": statistics.mean(r["em_ms"]),
         "final_loglik": r["final_ll"],
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),

@@ -50,6 +50,7 @@ struct fastfca_ctx {
   float* va = nullptr;           // N x K x T activations
   float* ab = nullptr;           // 2 x F x N x T per-bin terms of the activation update
   float* mscratch = nullptr;     // F + T + 1 floats (default start)
+  int h_valid = 0;               // v (the h buffer) holds t va of the current t and va
   ffca::MnmfOps mops{};
   // FCA parameters
   double2* R = nullptr;
@@ -403,6 +404,7 @@ fastfca_status fastfca_set_params_mnmf(fastfca_ctx* ctx, const void* W, const fl
   CK(ctx, to_device(ctx->tb, t, sizeof(float) * (size_t)c.F * c.N * ctx->K, ctx->stream), "t upload");
   CK(ctx, to_device(ctx->va, v, sizeof(float) * (size_t)c.N * ctx->K * c.T, ctx->stream), "v upload");
   ctx->b_valid = 0;
+  ctx->h_valid = 0;
   if (ctx->sticky == FASTFCA_ENUMERIC) ctx->sticky = FASTFCA_OK;
   return FASTFCA_OK;
 }
@@ -422,10 +424,21 @@ fastfca_status fastfca_get_params_mnmf(fastfca_ctx* ctx, void* W, float* lam, fl
 }  // extern "C"
 
 namespace {
+// h = t v (Eq. 52) into the h buffer unless it already holds it.
+fastfca_status mnmf_ensure_h(fastfca_ctx* ctx) {
+  if (ctx->h_valid) return FASTFCA_OK;
+  const fastfca_config& c = ctx->cfg;
+  CK(ctx, ffca::launch_mnmf_h(ctx->tb, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream), "FastMNMF h launch");
+  ctx->h_valid = 1;
+  return FASTFCA_OK;
+}
+
 // One FastMNMF launch of the per-frequency kernel (iterate = 1: one iteration; 0: the
 // log-likelihood of the current parameters only).
 fastfca_status mnmf_freq(fastfca_ctx* ctx, int iterate, double* ll_out, int ll_stride, double* ll_last) {
   const fastfca_config& c = ctx->cfg;
+  fastfca_status st = mnmf_ensure_h(ctx);
+  if (st) return st;
   ffca::MnmfArgs a{};
   a.x = ctx->x;
   a.P = ctx->P;
@@ -435,6 +448,7 @@ fastfca_status mnmf_freq(fastfca_ctx* ctx, int iterate, double* ll_out, int ll_s
   a.lam = ctx->lam;
   a.tb = ctx->tb;
   a.va = ctx->va;
+  a.hin = ctx->v;
   a.ab = ctx->ab;
   a.ll_out = ll_out;
   a.ll_last = ll_last;
@@ -523,7 +537,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     for (int it = 0; it < n_iter; ++it) {
       st = mnmf_freq(ctx, 1, (hist && it > 0) ? hist + (it - 1) : nullptr, n_iter, nullptr);
       if (st) return st;
-      CK(ctx, ffca::launch_mnmf_v(ctx->tb, ctx->ab, ctx->va, c.F, c.N, ctx->K, c.T, ctx->stream),
+      CK(ctx, ffca::launch_mnmf_v(ctx->tb, ctx->ab, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream),
          "FastMNMF activation update launch");
     }
     if (hist) {
@@ -641,9 +655,11 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   }
   cudaError_t e = cudaSuccess;
   if (fastfca_family(c.model) || c.model == FASTFCA_MODEL_FASTMNMF) {
-    // FastMNMF: h = t v (Eq. 52) into the FastFCA filter's H, then the same filter (Eq. 39)
-    if (c.model == FASTFCA_MODEL_FASTMNMF)
+    // FastMNMF: h = t v (Eq. 52) in the FastFCA filter's H layout, then the same filter (Eq. 39)
+    if (c.model == FASTFCA_MODEL_FASTMNMF && !ctx->h_valid) {
       e = ffca::launch_mnmf_h(ctx->tb, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream);
+      if (e == cudaSuccess) ctx->h_valid = 1;
+    }
     if (e == cudaSuccess && ctx->b_valid) {
       const size_t n = (size_t)c.F * c.M * c.M;
       bst_to_winv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->Bst, ctx->winv, n);

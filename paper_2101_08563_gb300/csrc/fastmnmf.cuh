@@ -4,7 +4,7 @@
 // One iteration (IP for W, then the exponent-1/2 MM rules of IS-NMF for lambda, t, v in that
 // order, sigma^2 recomputed before each):
 //   fastmnmf_freq_kernel, one CTA per frequency i (frames owned as in fastfca_em_kernel):
-//     h_ijn = sum_k t_ikn v_jkn                                           Eq. 52
+//     h_ijn = sum_k t_ikn v_jkn  (read: the previous activation update wrote it)  Eq. 52
 //     sigma^2 = Lambda_i h, log-likelihood of the incoming parameters    Eq. 28, Eq. 53
 //     Q_m, IP (FP64), U = |W^H x|^2                                        Eq. 33-35, 37
 //     lambda_imn *= (sum_j h U/sigma^4 / sum_j h/sigma^2)^1/2
@@ -12,7 +12,8 @@
 //        a_ijn = sum_m lambda_imn U_mij/sigma^4_mij, b_ijn = sum_m lambda_imn/sigma^2_mij
 //     a_ijn, b_ijn again with sigma^2 from the new t, written to memory for the v update
 //   fastmnmf_v_kernel: v_jkn *= (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2, the sum over
-//     every frequency (the step that couples the bins).
+//     every frequency (the step that couples the bins), then h = t v of the new t and v for
+//     the next iteration and for the Wiener filter.
 //
 // Layouts: t (bases) F x N x K, t_ikn at tb[(i N + n) K + k]; v (activations) N x K x T,
 // v_jkn at va[(n K + k) T + j] (frames contiguous, so a warp's reads of one v row coalesce);
@@ -24,8 +25,8 @@
 namespace ffca {
 
 constexpr int kMnmfMaxK = 16;      // bases per source
-constexpr int kMnmfPairs = 16;     // (n, k) pairs per reduction chunk of the t update
-constexpr int kMnmfMaxFK = 40960;  // the activation update stages t[:, n, :] (F*K floats) on chip
+static_assert(2 * kMnmfMaxK == 32, "the t update reduces num and den of one source as one 32-wide row");
+constexpr int kMnmfMaxFK = 36864;  // the activation update stages t[:, n, :] (F*K floats) on chip
 
 struct MnmfArgs {
   const float2* x;     // F x T x M
@@ -36,6 +37,7 @@ struct MnmfArgs {
   float* lam;          // F x M x N
   float* tb;           // F x N x K
   const float* va;     // N x K x T
+  const float* hin;    // F x N x T: h = t v of the incoming t and v (Eq. 52)
   float* ab;           // 2 x F x N x T (a plane, then b plane); written when iterating
   double* ll_out;      // log-likelihood of the incoming parameters at ll_out[f * ll_stride], or null
   double* ll_last;     // F or null: the same value, when only the log-likelihood is asked for
@@ -138,21 +140,25 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
       for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
     }
   };
-  // h_n = sum_k t_nk v_nk(t) for this thread's frames (Eq. 52), into pH
+  // h_n = sum_k t_nk v_nk(t) for this thread's frames (Eq. 52), into pH.  The frame slots
+  // are the inner loop, so each basis issues kSlots independent coalesced loads of v.
   auto pass_h = [&]() {
+#pragma unroll 1
+    for (int n = 0; n < N; ++n) {
+      float hs[kSlots];
 #pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      const int t = tid + k * bd;
-      if (t < T) {
+      for (int k = 0; k < kSlots; ++k) hs[k] = 0.f;
+      const float* vr = p.va + (size_t)n * K * T + tid;
+#pragma unroll 2
+      for (int kk = 0; kk < K; ++kk) {
+        const float tv = sT[n * K + kk];
 #pragma unroll
-        for (int n = 0; n < N; ++n) {
-          const float* vr = p.va + (size_t)n * K * T + t;
-          const float* tr = sT + n * K;
-          float h = 0.f;
-          for (int kk = 0; kk < K; ++kk) h = fmaf(tr[kk], __ldg(vr + (size_t)kk * T), h);
-          pH[k * N + n] = h;
-        }
+        for (int k = 0; k < kSlots; ++k)
+          if (tid + k * bd < T) hs[k] = fmaf(tv, __ldg(vr + (size_t)kk * T + k * bd), hs[k]);
       }
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (tid + k * bd < T) pH[k * N + n] = hs[k];
     }
   };
   auto pass_U = [&]() {
@@ -204,7 +210,14 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
   };
 
   __syncthreads();
-  pass_h();
+#pragma unroll
+  for (int k = 0; k < kSlots; ++k) {
+    const int t = tid + k * bd;
+    if (t < T) {
+#pragma unroll
+      for (int n = 0; n < N; ++n) pH[k * N + n] = __ldg(p.hin + ((size_t)f * N + n) * T + t);
+    }
+  }
   if (need_ll) pass_U();
   int par = 0;
   {
@@ -351,64 +364,58 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
   }
   __syncthreads();
 
-  // ---- t_nk <- t_nk (sum_j v a / sum_j v b)^1/2 with sigma^2 from the new lambda (and the
-  // incoming t), formed per frame from shared memory so that the frame loop stays rolled
+  // ---- t_nk <- t_nk (sum_j v_nk a_n / sum_j v_nk b_n)^1/2, a and b with sigma^2 from the new
+  // lambda and the incoming t (pH); one source per pass: a_n, b_n of the thread's frames in
+  // registers, then every basis's v row with the frame slots as the inner loop
   {
-    const int NK = N * K;
+    float dummy = 0.f;
+    if (pass_sigma(false, dummy)) atomicOr(p.err, kErrSigma);     // r = 1/sigma^2, new lambda
 #pragma unroll 1
-    for (int p0 = 0; p0 < NK; p0 += kMnmfPairs) {
-      float acc[2 * kMnmfPairs];
+    for (int n = 0; n < N; ++n) {
+      float av[kSlots], bv[kSlots];
 #pragma unroll
-      for (int i = 0; i < 2 * kMnmfPairs; ++i) acc[i] = 0.f;
-      int nq[kMnmfPairs];                     // source of pair p0 + q (one division per chunk)
-#pragma unroll
-      for (int q = 0; q < kMnmfPairs; ++q) nq[q] = (p0 + q) / K;
-      bool bad = false;
-#pragma unroll 1
       for (int k = 0; k < kSlots; ++k) {
-        const int t = tid + k * bd;
-        if (t < T) {
-          float e[M], s[M];
+        av[k] = 0.f;
+        bv[k] = 0.f;
+        if (tid + k * bd < T) {
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            float s2 = 0.f;
-#pragma unroll
-            for (int n = 0; n < N; ++n) s2 = fmaf(sL[m * N + n], pH[k * N + n], s2);
-            bad |= !(s2 > 0.f && s2 < INFINITY);
-            s[m] = fast_rcp(s2);
-            e[m] = pU[k * M + m] * s[m] * s[m];
-          }
-#pragma unroll
-          for (int q = 0; q < kMnmfPairs; ++q) {
-            const int pr = p0 + q;
-            if (pr < NK) {
-              const int n = nq[q];
-              float a = 0.f, b = 0.f;
-#pragma unroll
-              for (int m = 0; m < M; ++m) {
-                const float l = sL[m * N + n];
-                a = fmaf(l, e[m], a);
-                b = fmaf(l, s[m], b);
-              }
-              const float vv = __ldg(p.va + (size_t)pr * T + t);
-              acc[q] = fmaf(vv, a, acc[q]);
-              acc[kMnmfPairs + q] = fmaf(vv, b, acc[kMnmfPairs + q]);
-            }
+            const float rs = r[k][m];
+            const float l = sL[m * N + n];
+            av[k] = fmaf(l, pU[k * M + m] * rs * rs, av[k]);
+            bv[k] = fmaf(l, rs, bv[k]);
           }
         }
       }
-      if (bad) atomicOr(p.err, kErrSigma);
-      warp_reduce_scatter<2 * kMnmfPairs>(acc, lane);
+      float acc[2 * kMnmfMaxK];
+      const float* vr = p.va + (size_t)n * K * T + tid;
+#pragma unroll
+      for (int kk = 0; kk < kMnmfMaxK; ++kk) {
+        float sn = 0.f, sd = 0.f;
+        if (kk < K) {
+#pragma unroll
+          for (int k = 0; k < kSlots; ++k) {
+            if (tid + k * bd < T) {
+              const float vv = __ldg(vr + (size_t)kk * T + k * bd);
+              sn = fmaf(vv, av[k], sn);
+              sd = fmaf(vv, bv[k], sd);
+            }
+          }
+        }
+        acc[kk] = sn;
+        acc[kMnmfMaxK + kk] = sd;
+      }
+      warp_reduce_scatter<2 * kMnmfMaxK>(acc, lane);
       sRed[par * kMaxWarps * 32 + warp * 32 + lane] = acc[0];
       __syncthreads();
-      if (tid < kMnmfPairs && p0 + tid < NK) {
+      if (tid < K) {
         const float* red = sRed + par * kMaxWarps * 32;
         float num = 0.f, den = 0.f;
         for (int w = 0; w < nw; ++w) {
           num += red[w * 32 + tid];
-          den += red[w * 32 + kMnmfPairs + tid];
+          den += red[w * 32 + kMnmfMaxK + tid];
         }
-        sT[p0 + tid] *= (den > 0.f) ? sqrtf(num / den) : 1.0f;   // sT[n K + k], pair index p
+        sT[n * K + tid] *= (den > 0.f) ? sqrtf(num / den) : 1.0f;
       }
       par ^= 1;
     }
@@ -471,8 +478,10 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
 }
 
 // The cross-frequency v update, h for the filter, and the default start (fastmnmf_common.cu).
-// v_jkn <- v_jkn (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2 over every frequency i.
-cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, int F, int N, int K, int T, cudaStream_t s);
+// v_jkn <- v_jkn (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2 over every frequency i, then
+// h = t v (Eq. 52) of the new v into h (F x N x T).
+cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, float* h, int F, int N, int K, int T,
+                          cudaStream_t s);
 // h_ijn = sum_k t_ikn v_jkn (Eq. 52) as F x N x T (the FastFCA filter's H layout).
 cudaError_t launch_mnmf_h(const float* tb, const float* va, float* h, int F, int N, int K, int T, cudaStream_t s);
 // Default start: W = I, lambda = 1; with p_ij = ||x_ij||^2 / (M N),

@@ -5,15 +5,19 @@
 
 namespace ffca {
 
-// v_jkn <- v_jkn (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2.  Grid (ceil(T/32), N), 256
-// threads: lane = frame within the CTA's 32, warp w sums frequencies i = w, w + 8, ...; the 8
-// partial sums meet in shared memory.  Dynamic shared memory: F*K floats (t[:, n, :]) plus
-// 8 x 32 x 2K floats of partial sums.
-constexpr int kMnmfVWarps = 8;
+// v_jkn <- v_jkn (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2.  Grid (ceil(T/32), N), 512
+// threads: lane = frame within the CTA's 32, warp w sums frequencies i = w, w + 16, ... (eight
+// at a time, so each warp keeps 16 loads in flight); the 16 partial sums meet in shared
+// memory (two CTAs per SM, so the N x ceil(T/32) CTAs of the bench shape fit in one wave).
+// Then h_ijn = sum_k t_ikn v_jkn of the new v for every frequency (the next
+// iteration's h, and the Wiener filter's), written to h (F x N x T).  Dynamic shared memory:
+// F*K floats (t[:, n, :]) plus 16 x 32 x 2K floats (partial sums, then the new v of the tile).
+constexpr int kMnmfVWarps = 16;
 
-__global__ void __launch_bounds__(kMnmfVWarps * 32) fastmnmf_v_kernel(const float* __restrict__ tb,
+__global__ void __launch_bounds__(kMnmfVWarps * 32, 2) fastmnmf_v_kernel(const float* __restrict__ tb,
                                                                      const float* __restrict__ ab,
-                                                                     float* __restrict__ va, int F, int N, int K,
+                                                                     float* __restrict__ va,
+                                                                     float* __restrict__ h, int F, int N, int K,
                                                                      int T) {
   extern __shared__ __align__(16) float smv[];
   const int n = blockIdx.y;
@@ -33,7 +37,7 @@ __global__ void __launch_bounds__(kMnmfVWarps * 32) fastmnmf_v_kernel(const floa
     const float* ap = ab + (size_t)n * T + j;
     const float* bp = ab + (size_t)F * N * T + (size_t)n * T + j;
     const size_t fs = (size_t)N * T;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = w; i < F; i += kMnmfVWarps) {
       const float a = __ldg(ap + (size_t)i * fs);
       const float b = __ldg(bp + (size_t)i * fs);
@@ -56,16 +60,42 @@ __global__ void __launch_bounds__(kMnmfVWarps * 32) fastmnmf_v_kernel(const floa
     }
   }
   __syncthreads();
-  if (j < T) {
-    for (int k = w; k < K; k += kMnmfVWarps) {
-      float nm = 0.f, dn = 0.f;
-      for (int q = 0; q < kMnmfVWarps; ++q) {
-        const float* o = sP + ((size_t)q * 32 + lane) * 2 * K;
-        nm += o[k];
-        dn += o[K + k];
-      }
+  float vnew[kMnmfMaxK / kMnmfVWarps > 0 ? kMnmfMaxK / kMnmfVWarps : 1];
+  int c = 0;
+  for (int k = w; k < K; k += kMnmfVWarps, ++c) {
+    float nm = 0.f, dn = 0.f;
+    for (int q = 0; q < kMnmfVWarps; ++q) {
+      const float* o = sP + ((size_t)q * 32 + lane) * 2 * K;
+      nm += o[k];
+      dn += o[K + k];
+    }
+    float val = 0.f;
+    if (j < T) {
       float* vp = va + ((size_t)n * K + k) * T + j;
-      *vp *= (dn > 0.f) ? sqrtf(nm / dn) : 1.0f;
+      val = *vp * ((dn > 0.f) ? sqrtf(nm / dn) : 1.0f);
+      *vp = val;
+    }
+    vnew[c] = val;
+  }
+  __syncthreads();                           // the partial sums are consumed: reuse sP
+  float* sV = sP;                            // [k][lane], the new v of the tile
+  c = 0;
+  for (int k = w; k < K; k += kMnmfVWarps, ++c) sV[k * 32 + lane] = vnew[c];
+  __syncthreads();
+  if (j < T) {
+    const size_t fs = (size_t)N * T;
+    float* hp = h + (size_t)n * T + j;
+    float vk[kMnmfMaxK];
+#pragma unroll
+    for (int k = 0; k < kMnmfMaxK; ++k) vk[k] = (k < K) ? sV[k * 32 + lane] : 0.f;
+#pragma unroll 4
+    for (int i = w; i < F; i += kMnmfVWarps) {
+      const float* tr = sTn + (size_t)i * K;
+      float hv = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMnmfMaxK; ++k)
+        if (k < K) hv = fmaf(tr[k], vk[k], hv);
+      hp[(size_t)i * fs] = hv;
     }
   }
 }
@@ -86,12 +116,13 @@ static size_t mnmf_v_smem(int F, int K) {
   return sizeof(float) * ((size_t)F * K + (size_t)kMnmfVWarps * 32 * 2 * K);
 }
 
-cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, int F, int N, int K, int T, cudaStream_t s) {
+cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, float* h, int F, int N, int K, int T,
+                          cudaStream_t s) {
   const size_t smem = mnmf_v_smem(F, K);
   cudaError_t e = cudaFuncSetAttribute(fastmnmf_v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((T + 31) / 32, N);
-  fastmnmf_v_kernel<<<grid, kMnmfVWarps * 32, smem, s>>>(tb, ab, va, F, N, K, T);
+  fastmnmf_v_kernel<<<grid, kMnmfVWarps * 32, smem, s>>>(tb, ab, va, h, F, N, K, T);
   return cudaGetLastError();
 }
 
@@ -120,16 +151,26 @@ __global__ void mnmf_pf_kernel(const float2* __restrict__ x, float* __restrict__
   if (threadIdx.x == 0) pf[i] = red[0] / ((float)T * (float)(M * N));
 }
 
-// pt[j] = mean_i ||x_ij||^2 / (M N): one thread per frame.
+// pt[j] = mean_i ||x_ij||^2 / (M N): a CTA of 32 x 32 threads per 32 frames; thread (lane, y)
+// sums frequencies i = y, y + 32, ..., then the 32 partial sums are added in a fixed order.
 __global__ void mnmf_pt_kernel(const float2* __restrict__ x, float* __restrict__ pt, int F, int T, int M, int N) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= T) return;
+  __shared__ float part[32][33];
+  const int lane = threadIdx.x, y = threadIdx.y;
+  const int j = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int i = 0; i < F; ++i) {
-    const float2* xv = x + ((size_t)i * T + j) * M;
-    for (int a = 0; a < M; ++a) s = fmaf(xv[a].x, xv[a].x, fmaf(xv[a].y, xv[a].y, s));
+  if (j < T) {
+    for (int i = y; i < F; i += 32) {
+      const float2* xv = x + ((size_t)i * T + j) * M;
+      for (int a = 0; a < M; ++a) s = fmaf(xv[a].x, xv[a].x, fmaf(xv[a].y, xv[a].y, s));
+    }
   }
-  pt[j] = s / ((float)F * (float)(M * N));
+  part[y][lane] = s;
+  __syncthreads();
+  if (y == 0 && j < T) {
+    float tot = 0.f;
+    for (int q = 0; q < 32; ++q) tot += part[q][lane];
+    pt[j] = tot / ((float)F * (float)(M * N));
+  }
 }
 
 // mean of pf (= mean_ij p_ij), one CTA.
@@ -174,7 +215,7 @@ __global__ void mnmf_fill_kernel(const float* __restrict__ scratch, double2* __r
 cudaError_t launch_mnmf_default(const float2* x, double2* P, float* lam, float* tb, float* va, float* scratch, int F,
                                 int T, int M, int N, int K, uint32_t seed, cudaStream_t s) {
   mnmf_pf_kernel<<<F, 256, 0, s>>>(x, scratch, T, M, N);
-  mnmf_pt_kernel<<<(T + 127) / 128, 128, 0, s>>>(x, scratch + F, F, T, M, N);
+  mnmf_pt_kernel<<<(T + 31) / 32, dim3(32, 32), 0, s>>>(x, scratch + F, F, T, M, N);
   mnmf_mean_kernel<<<1, 256, 0, s>>>(scratch, scratch + F + T, F);
   size_t n = (size_t)F * M * M;
   if ((size_t)F * M * N > n) n = (size_t)F * M * N;
