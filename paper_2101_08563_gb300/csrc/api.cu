@@ -48,7 +48,8 @@ struct fastfca_ctx {
   int K = 0;
   float* tb = nullptr;           // F x N x K bases
   float* va = nullptr;           // N x K x T activations
-  float* ab = nullptr;           // 2 x F x N x T per-bin terms of the activation update
+  float* ab = nullptr;           // 2 x F x N x T per-bin terms of the t and v updates
+  float* ubuf = nullptr;         // F x M x T: U of the current W
   float* mscratch = nullptr;     // F + T + 1 floats (default start)
   int h_valid = 0;               // v (the h buffer) holds t va of the current t and va
   ffca::MnmfOps mops{};
@@ -203,6 +204,7 @@ void free_all(fastfca_ctx* c) {
   cudaFree(c->tb);
   cudaFree(c->va);
   cudaFree(c->ab);
+  cudaFree(c->ubuf);
   cudaFree(c->mscratch);
   cudaFree(c->R);
   cudaFree(c->h);
@@ -325,7 +327,8 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
     CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
     CKC(cudaMalloc(&ctx->tb, sizeof(float) * (size_t)c.F * c.N * K), "t alloc");
     CKC(cudaMalloc(&ctx->va, sizeof(float) * (size_t)c.N * K * c.T), "v alloc");
-    CKC(cudaMalloc(&ctx->ab, sizeof(float) * 2 * FT(c) * c.N), "activation-update terms alloc");
+    CKC(cudaMalloc(&ctx->ab, sizeof(float) * 2 * FT(c) * c.N), "update terms alloc");
+    CKC(cudaMalloc(&ctx->ubuf, sizeof(float) * FT(c) * c.M), "U alloc");
     CKC(cudaMalloc(&ctx->mscratch, sizeof(float) * ((size_t)c.F + c.T + 1)), "scratch alloc");
     CKC(ffca::launch_mnmf_default(ctx->x, ctx->P, ctx->lam, ctx->tb, ctx->va, ctx->mscratch, c.F, c.T, c.M, c.N, K,
                                   (uint32_t)c.seed, ctx->stream),
@@ -446,16 +449,14 @@ fastfca_status mnmf_freq(fastfca_ctx* ctx, int iterate, double* ll_out, int ll_s
   a.detst = ctx->detst;
   a.b_valid = ctx->b_valid;
   a.lam = ctx->lam;
-  a.tb = ctx->tb;
-  a.va = ctx->va;
   a.hin = ctx->v;
   a.ab = ctx->ab;
+  a.u = ctx->ubuf;
   a.ll_out = ll_out;
   a.ll_last = ll_last;
   a.err = ctx->err;
   a.F = c.F;
   a.T = c.T;
-  a.K = ctx->K;
   a.ll_stride = ll_stride;
   a.iterate = iterate;
   CK(ctx, ctx->mops.freq(a, ctx->stream), "FastMNMF frequency launch");
@@ -535,8 +536,13 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
   if (c.model == FASTFCA_MODEL_FASTMNMF) {
     // launch it of the per-frequency kernel also gives the log-likelihood after iteration it-1
     for (int it = 0; it < n_iter; ++it) {
+      // IP and lambda (per frequency), then t, then the v update's terms with the new t, then v
       st = mnmf_freq(ctx, 1, (hist && it > 0) ? hist + (it - 1) : nullptr, n_iter, nullptr);
       if (st) return st;
+      CK(ctx, ffca::launch_mnmf_t(ctx->tb, ctx->va, ctx->ab, c.F, c.N, ctx->K, c.T, ctx->stream),
+         "FastMNMF basis update launch");
+      CK(ctx, ctx->mops.ab(ctx->lam, ctx->tb, ctx->va, ctx->ubuf, ctx->ab, c.F, ctx->K, c.T, ctx->err, ctx->stream),
+         "FastMNMF activation-update terms launch");
       CK(ctx, ffca::launch_mnmf_v(ctx->tb, ctx->ab, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream),
          "FastMNMF activation update launch");
     }

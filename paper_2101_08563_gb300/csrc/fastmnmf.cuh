@@ -2,23 +2,28 @@
 // frequencies by NMF, h_ijn = sum_k t_ikn v_jkn (Eq. 52), fitted by minimising Eq. 53.
 //
 // One iteration (IP for W, then the exponent-1/2 MM rules of IS-NMF for lambda, t, v in that
-// order, sigma^2 recomputed before each):
+// order, sigma^2 recomputed before each) is four launches, each shaped for its work:
 //   fastmnmf_freq_kernel, one CTA per frequency i (frames owned as in fastfca_em_kernel):
-//     h_ijn = sum_k t_ikn v_jkn  (read: the previous activation update wrote it)  Eq. 52
-//     sigma^2 = Lambda_i h, log-likelihood of the incoming parameters    Eq. 28, Eq. 53
-//     Q_m, IP (FP64), U = |W^H x|^2                                        Eq. 33-35, 37
+//     h_ijn = sum_k t_ikn v_jkn (read: the previous activation update wrote it)   Eq. 52
+//     sigma^2 = Lambda_i h, log-likelihood of the incoming parameters       Eq. 28, Eq. 53
+//     Q_m, IP (FP64), U = |W^H x|^2                                           Eq. 33-35, 37
 //     lambda_imn *= (sum_j h U/sigma^4 / sum_j h/sigma^2)^1/2
-//     t_ikn *= (sum_j v_jkn a_ijn / sum_j v_jkn b_ijn)^1/2, with sigma^2 from the new lambda,
-//        a_ijn = sum_m lambda_imn U_mij/sigma^4_mij, b_ijn = sum_m lambda_imn/sigma^2_mij
-//     a_ijn, b_ijn again with sigma^2 from the new t, written to memory for the v update
+//     then, with sigma^2 from the new lambda: a_ijn = sum_m lambda_imn U_mij/sigma^4_mij and
+//     b_ijn = sum_m lambda_imn/sigma^2_mij, written with U
+//   fastmnmf_t_kernel: t_ikn *= (sum_j v_jkn a_ijn / sum_j v_jkn b_ijn)^1/2 -- a contraction
+//     over frames with v staged once per CTA in shared memory for 16 frequencies
+//   fastmnmf_ab_kernel: a, b again with sigma^2 from the new t (h = t v recomputed per bin,
+//     each thread's v column in registers across a tile of frequencies)
 //   fastmnmf_v_kernel: v_jkn *= (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2, the sum over
 //     every frequency (the step that couples the bins), then h = t v of the new t and v for
 //     the next iteration and for the Wiener filter.
+// The per-frequency kernel holds the latency-bound part (reductions, FP64 IP); the three
+// contractions over v run in kernels that read v once per tile instead of once per frequency.
 //
 // Layouts: t (bases) F x N x K, t_ikn at tb[(i N + n) K + k]; v (activations) N x K x T,
 // v_jkn at va[(n K + k) T + j] (frames contiguous, so a warp's reads of one v row coalesce);
-// a and b: two planes F x N x T.  W, W^{-H} and |det W|^2 are carried between launches as in
-// the FastFCA kernels.
+// a and b: two planes F x N x T; U: F x M x T.  W, W^{-H} and |det W|^2 are carried between
+// launches as in the FastFCA kernels.
 #pragma once
 #include "fastfca_em.cuh"
 
@@ -35,14 +40,13 @@ struct MnmfArgs {
   double* detst;       // F x 2, |det W|^2 as (mantissa, exponent)
   int b_valid;         // Bst/detst are current
   float* lam;          // F x M x N
-  float* tb;           // F x N x K
-  const float* va;     // N x K x T
   const float* hin;    // F x N x T: h = t v of the incoming t and v (Eq. 52)
   float* ab;           // 2 x F x N x T (a plane, then b plane); written when iterating
+  float* u;            // F x M x T: U = |W^H x|^2 of the new W; written when iterating
   double* ll_out;      // log-likelihood of the incoming parameters at ll_out[f * ll_stride], or null
   double* ll_last;     // F or null: the same value, when only the log-likelihood is asked for
   int* err;
-  int F, T, K, ll_stride;
+  int F, T, ll_stride;
   int iterate;         // 1: one iteration; 0: log-likelihood only
 };
 
@@ -56,7 +60,6 @@ struct MnSmem {
     b += sizeof(double) * 4;                 // sDet
     b += sizeof(float2) * E::kWcPad;         // sWc
     b += sizeof(float) * ((M * N + 3) & ~3); // sL
-    b += sizeof(float) * N * kMnmfMaxK;      // sT
     b += sizeof(float) * 2 * kMaxWarps * 32; // reduction rows
     b += sizeof(float) * kMaxWarps;          // sLL
     b += sizeof(float) * (size_t)threads * (kSlots * N + 1);   // sH, thread-major
@@ -73,9 +76,9 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
   const int f = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bd = blockDim.x, nw = bd >> 5;
-  const int T = p.T, K = p.K;
+  const int T = p.T;
   if (f >= p.F) return;
-  if (bd * kSlots < T || bd > kMaxThreads || K < 1 || K > kMnmfMaxK) {    // uniform
+  if (bd * kSlots < T || bd > kMaxThreads) {    // uniform
     if (tid == 0) atomicOr(p.err, kErrConfig);
     return;
   }
@@ -86,8 +89,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
   double* sDet = reinterpret_cast<double*>(sQ + SM::kQsz);
   float2* sWc = reinterpret_cast<float2*>(sDet + 4);
   float* sL = reinterpret_cast<float*>(sWc + SM::kWcPad);
-  float* sT = sL + ((M * N + 3) & ~3);
-  float* sRed = sT + N * kMnmfMaxK;
+  float* sRed = sL + ((M * N + 3) & ~3);
   float* sLL = sRed + 2 * kMaxWarps * 32;
   float* sH = sLL + kMaxWarps;
   constexpr int SH = kSlots * N + 1, SU = kSlots * M + 1;
@@ -101,7 +103,6 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
 
   // ---- parameters of frequency f; B = W^{-H} and |det W|^2 carried over or formed once
   for (int i = tid; i < M * N; i += bd) sL[i] = p.lam[(size_t)f * M * N + i];
-  for (int i = tid; i < N * K; i += bd) sT[i] = p.tb[(size_t)f * N * K + i];
   for (int i = tid; i < M * M; i += bd) sW[i] = p.P[(size_t)f * M * M + i];
   __syncthreads();
   if (warp == 0) {
@@ -138,27 +139,6 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
     } else {
 #pragma unroll
       for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
-    }
-  };
-  // h_n = sum_k t_nk v_nk(t) for this thread's frames (Eq. 52), into pH.  The frame slots
-  // are the inner loop, so each basis issues kSlots independent coalesced loads of v.
-  auto pass_h = [&]() {
-#pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-      float hs[kSlots];
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) hs[k] = 0.f;
-      const float* vr = p.va + (size_t)n * K * T + tid;
-#pragma unroll 2
-      for (int kk = 0; kk < K; ++kk) {
-        const float tv = sT[n * K + kk];
-#pragma unroll
-        for (int k = 0; k < kSlots; ++k)
-          if (tid + k * bd < T) hs[k] = fmaf(tv, __ldg(vr + (size_t)kk * T + k * bd), hs[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k)
-        if (tid + k * bd < T) pH[k * N + n] = hs[k];
     }
   };
   auto pass_U = [&]() {
@@ -364,67 +344,12 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
   }
   __syncthreads();
 
-  // ---- t_nk <- t_nk (sum_j v_nk a_n / sum_j v_nk b_n)^1/2, a and b with sigma^2 from the new
-  // lambda and the incoming t (pH); one source per pass: a_n, b_n of the thread's frames in
-  // registers, then every basis's v row with the frame slots as the inner loop
+  // ---- the t update's per-bin terms with sigma^2 from the new lambda and the incoming h:
+  // a_jn = sum_m lambda_mn U_mj / sigma^4_mj, b_jn = sum_m lambda_mn / sigma^2_mj, written with
+  // U for the kernels that finish the iteration
   {
     float dummy = 0.f;
-    if (pass_sigma(false, dummy)) atomicOr(p.err, kErrSigma);     // r = 1/sigma^2, new lambda
-#pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-      float av[kSlots], bv[kSlots];
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        av[k] = 0.f;
-        bv[k] = 0.f;
-        if (tid + k * bd < T) {
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float rs = r[k][m];
-            const float l = sL[m * N + n];
-            av[k] = fmaf(l, pU[k * M + m] * rs * rs, av[k]);
-            bv[k] = fmaf(l, rs, bv[k]);
-          }
-        }
-      }
-      float acc[2 * kMnmfMaxK];
-      const float* vr = p.va + (size_t)n * K * T + tid;
-#pragma unroll
-      for (int kk = 0; kk < kMnmfMaxK; ++kk) {
-        float sn = 0.f, sd = 0.f;
-        if (kk < K) {
-#pragma unroll
-          for (int k = 0; k < kSlots; ++k) {
-            if (tid + k * bd < T) {
-              const float vv = __ldg(vr + (size_t)kk * T + k * bd);
-              sn = fmaf(vv, av[k], sn);
-              sd = fmaf(vv, bv[k], sd);
-            }
-          }
-        }
-        acc[kk] = sn;
-        acc[kMnmfMaxK + kk] = sd;
-      }
-      warp_reduce_scatter<2 * kMnmfMaxK>(acc, lane);
-      sRed[par * kMaxWarps * 32 + warp * 32 + lane] = acc[0];
-      __syncthreads();
-      if (tid < K) {
-        const float* red = sRed + par * kMaxWarps * 32;
-        float num = 0.f, den = 0.f;
-        for (int w = 0; w < nw; ++w) {
-          num += red[w * 32 + tid];
-          den += red[w * 32 + kMnmfMaxK + tid];
-        }
-        sT[n * K + tid] *= (den > 0.f) ? sqrtf(num / den) : 1.0f;
-      }
-      par ^= 1;
-    }
-  }
-  __syncthreads();
-
-  // ---- a, b with sigma^2 from the new t, for the v update over all frequencies
-  pass_h();
-  {
+    if (pass_sigma(false, dummy)) atomicOr(p.err, kErrSigma);
     float Lr[M][N];
 #pragma unroll
     for (int m = 0; m < M; ++m)
@@ -432,41 +357,36 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
       for (int n = 0; n < N; ++n) Lr[m][n] = sL[m * N + n];
     float* ap = p.ab + (size_t)f * N * T;
     float* bp = p.ab + (size_t)p.F * N * T + (size_t)f * N * T;
-    bool bad = false;
+    float* up = p.u + (size_t)f * M * T;
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
       const int t = tid + k * bd;
       if (t < T) {
-        float e[M], s[M];
+        float e[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          float s2 = 0.f;
-#pragma unroll
-          for (int n = 0; n < N; ++n) s2 = fmaf(Lr[m][n], pH[k * N + n], s2);
-          bad |= !(s2 > 0.f && s2 < INFINITY);
-          s[m] = fast_rcp(s2);
-          e[m] = pU[k * M + m] * s[m] * s[m];
+          const float u = pU[k * M + m];
+          e[m] = u * r[k][m] * r[k][m];
+          up[(size_t)m * T + t] = u;
         }
 #pragma unroll
         for (int n = 0; n < N; ++n) {
-          float a = 0.f, b = 0.f;
+          float av = 0.f, bv = 0.f;
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            a = fmaf(Lr[m][n], e[m], a);
-            b = fmaf(Lr[m][n], s[m], b);
+            av = fmaf(Lr[m][n], e[m], av);
+            bv = fmaf(Lr[m][n], r[k][m], bv);
           }
-          ap[(size_t)n * T + t] = a;
-          bp[(size_t)n * T + t] = b;
+          ap[(size_t)n * T + t] = av;
+          bp[(size_t)n * T + t] = bv;
         }
       }
     }
-    if (bad) atomicOr(p.err, kErrSigma);
   }
 
   // ---- write back
   __syncthreads();
   for (int i = tid; i < M * N; i += bd) p.lam[(size_t)f * M * N + i] = sL[i];
-  for (int i = tid; i < N * K; i += bd) p.tb[(size_t)f * N * K + i] = sT[i];
   for (int i = tid; i < M * M; i += bd) {
     p.P[(size_t)f * M * M + i] = sW[i];
     p.Bst[(size_t)f * M * M + i] = sB[i];
@@ -482,6 +402,8 @@ __global__ void __maxnreg__(kEmMaxRegs) fastmnmf_freq_kernel(MnmfArgs p) {
 // h = t v (Eq. 52) of the new v into h (F x N x T).
 cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, float* h, int F, int N, int K, int T,
                           cudaStream_t s);
+// t_ikn *= (sum_j v_jkn a_ijn / sum_j v_jkn b_ijn)^1/2 for every frequency.
+cudaError_t launch_mnmf_t(float* tb, const float* va, const float* ab, int F, int N, int K, int T, cudaStream_t s);
 // h_ijn = sum_k t_ikn v_jkn (Eq. 52) as F x N x T (the FastFCA filter's H layout).
 cudaError_t launch_mnmf_h(const float* tb, const float* va, float* h, int F, int N, int K, int T, cudaStream_t s);
 // Default start: W = I, lambda = 1; with p_ij = ||x_ij||^2 / (M N),
@@ -491,8 +413,102 @@ cudaError_t launch_mnmf_h(const float* tb, const float* va, float* h, int F, int
 cudaError_t launch_mnmf_default(const float2* x, double2* P, float* lam, float* tb, float* va, float* scratch, int F,
                                 int T, int M, int N, int K, uint32_t seed, cudaStream_t s);
 
+// a_ijn = sum_m lambda_imn U_mij / sigma^4_mij and b_ijn = sum_m lambda_imn / sigma^2_mij with
+// sigma^2_mij = sum_n lambda_imn h_ijn, h_ijn = sum_k t_ikn v_jkn (the current t and v).
+// Grid (ceil(T / 128), ceil(F / kMnmfAbFreqs)), 128 threads, one frame each; the CTA's
+// v[:, :, frames] (N K x 128 floats) is staged once in shared memory and serves every
+// frequency of the tile; t and lambda of the tile are staged too.
+constexpr int kMnmfAbFreqs = 8;
+constexpr int kMnmfAbFrames = 128;
+
+template <int M, int N>
+__global__ void __launch_bounds__(kMnmfAbFrames) fastmnmf_ab_kernel(const float* __restrict__ lam,
+                                                                    const float* __restrict__ tb,
+                                                                    const float* __restrict__ va,
+                                                                    const float* __restrict__ u,
+                                                                    float* __restrict__ ab, int F, int K, int T,
+                                                                    int* err) {
+  extern __shared__ __align__(16) float sab[];
+  float* sV = sab;                                       // [n K + k][jj]
+  float* sTt = sV + (size_t)N * K * kMnmfAbFrames;       // [ii][n K + k]
+  float* sLm = sTt + (size_t)kMnmfAbFreqs * N * K;       // [ii][m N + n]
+  const int jj = threadIdx.x;
+  const int j = blockIdx.x * kMnmfAbFrames + jj;
+  const int i0 = blockIdx.y * kMnmfAbFreqs;
+  const int NK = N * K;
+  for (int e = jj; e < NK * kMnmfAbFrames; e += kMnmfAbFrames) {
+    const int row = e / kMnmfAbFrames, c = e - row * kMnmfAbFrames;
+    const int jc = blockIdx.x * kMnmfAbFrames + c;
+    sV[e] = (jc < T) ? __ldg(va + (size_t)row * T + jc) : 0.f;
+  }
+  for (int e = jj; e < kMnmfAbFreqs * NK; e += kMnmfAbFrames) {
+    const int ii = e / NK;
+    sTt[e] = (i0 + ii < F) ? __ldg(tb + (size_t)(i0 + ii) * NK + (e - ii * NK)) : 0.f;
+  }
+  for (int e = jj; e < kMnmfAbFreqs * M * N; e += kMnmfAbFrames) {
+    const int ii = e / (M * N);
+    sLm[e] = (i0 + ii < F) ? __ldg(lam + (size_t)(i0 + ii) * M * N + (e - ii * M * N)) : 0.f;
+  }
+  __syncthreads();
+  if (j >= T) return;
+  bool bad = false;
+  const size_t plane = (size_t)F * N * T;
+  for (int ii = 0; ii < kMnmfAbFreqs && i0 + ii < F; ++ii) {
+    const int i = i0 + ii;
+    const float* tr = sTt + ii * NK;
+    const float* lr = sLm + ii * M * N;
+    float h[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float s = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < K; ++k) s = fmaf(tr[n * K + k], sV[(n * K + k) * kMnmfAbFrames + jj], s);
+      h[n] = s;
+    }
+    float e[M], r[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float s2 = 0.f;
+#pragma unroll
+      for (int n = 0; n < N; ++n) s2 = fmaf(lr[m * N + n], h[n], s2);
+      bad |= !(s2 > 0.f && s2 < INFINITY);
+      r[m] = fast_rcp(s2);
+      e[m] = __ldg(u + ((size_t)i * M + m) * T + j) * r[m] * r[m];
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        a = fmaf(lr[m * N + n], e[m], a);
+        b = fmaf(lr[m * N + n], r[m], b);
+      }
+      ab[((size_t)i * N + n) * T + j] = a;
+      ab[plane + ((size_t)i * N + n) * T + j] = b;
+    }
+  }
+  if (bad) atomicOr(err, kErrSigma);
+}
+
+inline size_t mnmf_ab_smem(int M, int N, int K) {
+  return sizeof(float) * ((size_t)N * K * kMnmfAbFrames + (size_t)kMnmfAbFreqs * N * K + (size_t)kMnmfAbFreqs * M * N);
+}
+
+template <int M, int N>
+cudaError_t launch_mnmf_ab_mn(const float* lam, const float* tb, const float* va, const float* u, float* ab, int F,
+                              int K, int T, int* err, cudaStream_t s) {
+  const size_t smem = mnmf_ab_smem(M, N, K);
+  cudaError_t e = cudaFuncSetAttribute(fastmnmf_ab_kernel<M, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((T + kMnmfAbFrames - 1) / kMnmfAbFrames, (F + kMnmfAbFreqs - 1) / kMnmfAbFreqs);
+  fastmnmf_ab_kernel<M, N><<<grid, kMnmfAbFrames, smem, s>>>(lam, tb, va, u, ab, F, K, T, err);
+  return cudaGetLastError();
+}
+
 struct MnmfOps {
   cudaError_t (*freq)(const MnmfArgs& a, cudaStream_t s);
+  cudaError_t (*ab)(const float* lam, const float* tb, const float* va, const float* u, float* ab, int F, int K,
+                    int T, int* err, cudaStream_t s);
   int max_T;
 };
 
@@ -526,6 +542,7 @@ template <int M, int N>
 MnmfOps make_mnmf_ops() {
   MnmfOps o;
   o.freq = &launch_mnmf_freq<M, N>;
+  o.ab = &launch_mnmf_ab_mn<M, N>;
   o.max_T = kMaxThreads * kSlots;
   return o;
 }

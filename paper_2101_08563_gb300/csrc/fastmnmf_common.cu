@@ -8,31 +8,47 @@ namespace ffca {
 // v_jkn <- v_jkn (sum_i t_ikn a_ijn / sum_i t_ikn b_ijn)^1/2.  Grid (ceil(T/32), N), 512
 // threads: lane = frame within the CTA's 32, warp w sums frequencies i = w, w + 16, ... (eight
 // at a time, so each warp keeps 16 loads in flight); the 16 partial sums meet in shared
-// memory (two CTAs per SM, so the N x ceil(T/32) CTAs of the bench shape fit in one wave).
-// Then h_ijn = sum_k t_ikn v_jkn of the new v for every frequency (the next
-// iteration's h, and the Wiener filter's), written to h (F x N x T).  Dynamic shared memory:
-// F*K floats (t[:, n, :]) plus 16 x 32 x 2K floats (partial sums, then the new v of the tile).
+// memory, laid out [warp][2K][lane] so that a warp's accesses fall on distinct banks (two
+// CTAs per SM, so the N x ceil(T/32) CTAs of the bench shape fit in one wave).  Then
+// h_ijn = sum_k t_ikn v_jkn of the new v for every frequency (the next iteration's h, and the
+// Wiener filter's), written to h (F x N x T).  K is a template parameter so that no lane
+// issues work for absent bases.  Dynamic shared memory: F*K floats (t[:, n, :]) plus
+// 16 x 2K x 32 floats (partial sums, then the new v of the tile).
 constexpr int kMnmfVWarps = 16;
 
+template <int K>
+__device__ __forceinline__ void load_row(const float* p, float (&r)[K]) {
+  if constexpr (K % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < K; k += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(p + k);
+      r[k] = q.x; r[k + 1] = q.y; r[k + 2] = q.z; r[k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k] = p[k];
+  }
+}
+
+template <int K>
 __global__ void __launch_bounds__(kMnmfVWarps * 32, 2) fastmnmf_v_kernel(const float* __restrict__ tb,
                                                                      const float* __restrict__ ab,
                                                                      float* __restrict__ va,
-                                                                     float* __restrict__ h, int F, int N, int K,
-                                                                     int T) {
+                                                                     float* __restrict__ h, int F, int N, int T) {
   extern __shared__ __align__(16) float smv[];
   const int n = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
   float* sTn = smv;                          // F x K
-  float* sP = smv + (size_t)F * K;           // [w][lane][2K]
+  float* sP = smv + (size_t)F * K;           // [w][2K][lane]
   for (int e = threadIdx.x; e < F * K; e += blockDim.x) {
     const int i = e / K, k = e - (e / K) * K;
     sTn[e] = tb[((size_t)i * N + n) * K + k];
   }
   __syncthreads();
-  float num[kMnmfMaxK], den[kMnmfMaxK];
+  float num[K], den[K];
 #pragma unroll
-  for (int k = 0; k < kMnmfMaxK; ++k) { num[k] = 0.f; den[k] = 0.f; }
+  for (int k = 0; k < K; ++k) { num[k] = 0.f; den[k] = 0.f; }
   if (j < T) {
     const float* ap = ab + (size_t)n * T + j;
     const float* bp = ab + (size_t)F * N * T + (size_t)n * T + j;
@@ -41,64 +57,58 @@ __global__ void __launch_bounds__(kMnmfVWarps * 32, 2) fastmnmf_v_kernel(const f
     for (int i = w; i < F; i += kMnmfVWarps) {
       const float a = __ldg(ap + (size_t)i * fs);
       const float b = __ldg(bp + (size_t)i * fs);
-      const float* tr = sTn + (size_t)i * K;
+      float tr[K];
+      load_row<K>(sTn + (size_t)i * K, tr);
 #pragma unroll
-      for (int k = 0; k < kMnmfMaxK; ++k) {
-        if (k < K) {
-          num[k] = fmaf(tr[k], a, num[k]);
-          den[k] = fmaf(tr[k], b, den[k]);
-        }
+      for (int k = 0; k < K; ++k) {
+        num[k] = fmaf(tr[k], a, num[k]);
+        den[k] = fmaf(tr[k], b, den[k]);
       }
     }
   }
-  float* mine = sP + ((size_t)w * 32 + lane) * 2 * K;
+  float* mine = sP + (size_t)w * 2 * K * 32 + lane;
 #pragma unroll
-  for (int k = 0; k < kMnmfMaxK; ++k) {
-    if (k < K) {
-      mine[k] = num[k];
-      mine[K + k] = den[k];
-    }
+  for (int k = 0; k < K; ++k) {
+    mine[k * 32] = num[k];
+    mine[(K + k) * 32] = den[k];
   }
   __syncthreads();
-  float vnew[kMnmfMaxK / kMnmfVWarps > 0 ? kMnmfMaxK / kMnmfVWarps : 1];
-  int c = 0;
-  for (int k = w; k < K; k += kMnmfVWarps, ++c) {
+  float vnew = 0.f;                          // K <= 16 = warps: warp w owns basis w
+  if (w < K) {
     float nm = 0.f, dn = 0.f;
     for (int q = 0; q < kMnmfVWarps; ++q) {
-      const float* o = sP + ((size_t)q * 32 + lane) * 2 * K;
-      nm += o[k];
-      dn += o[K + k];
+      const float* o = sP + (size_t)q * 2 * K * 32 + lane;
+      nm += o[w * 32];
+      dn += o[(K + w) * 32];
     }
-    float val = 0.f;
     if (j < T) {
-      float* vp = va + ((size_t)n * K + k) * T + j;
-      val = *vp * ((dn > 0.f) ? sqrtf(nm / dn) : 1.0f);
-      *vp = val;
+      float* vp = va + ((size_t)n * K + w) * T + j;
+      vnew = *vp * ((dn > 0.f) ? sqrtf(nm / dn) : 1.0f);
+      *vp = vnew;
     }
-    vnew[c] = val;
   }
   __syncthreads();                           // the partial sums are consumed: reuse sP
   float* sV = sP;                            // [k][lane], the new v of the tile
-  c = 0;
-  for (int k = w; k < K; k += kMnmfVWarps, ++c) sV[k * 32 + lane] = vnew[c];
+  if (w < K) sV[w * 32 + lane] = vnew;
   __syncthreads();
   if (j < T) {
     const size_t fs = (size_t)N * T;
     float* hp = h + (size_t)n * T + j;
-    float vk[kMnmfMaxK];
+    float vk[K];
 #pragma unroll
-    for (int k = 0; k < kMnmfMaxK; ++k) vk[k] = (k < K) ? sV[k * 32 + lane] : 0.f;
+    for (int k = 0; k < K; ++k) vk[k] = sV[k * 32 + lane];
 #pragma unroll 4
     for (int i = w; i < F; i += kMnmfVWarps) {
-      const float* tr = sTn + (size_t)i * K;
+      float tr[K];
+      load_row<K>(sTn + (size_t)i * K, tr);
       float hv = 0.f;
 #pragma unroll
-      for (int k = 0; k < kMnmfMaxK; ++k)
-        if (k < K) hv = fmaf(tr[k], vk[k], hv);
+      for (int k = 0; k < K; ++k) hv = fmaf(tr[k], vk[k], hv);
       hp[(size_t)i * fs] = hv;
     }
   }
 }
+static_assert(kMnmfMaxK <= kMnmfVWarps, "one warp per basis in the v update");
 
 // h_ijn = sum_k t_ikn v_jkn (Eq. 52) as F x N x T, the layout of the FastFCA filter's H.
 __global__ void fastmnmf_h_kernel(const float* __restrict__ tb, const float* __restrict__ va, float* __restrict__ h,
@@ -112,18 +122,116 @@ __global__ void fastmnmf_h_kernel(const float* __restrict__ tb, const float* __r
   h[e] = s;
 }
 
-static size_t mnmf_v_smem(int F, int K) {
-  return sizeof(float) * ((size_t)F * K + (size_t)kMnmfVWarps * 32 * 2 * K);
+// t_ikn <- t_ikn (sum_j v_jkn a_ijn / sum_j v_jkn b_ijn)^1/2.  Grid (ceil(F / 16), N), 512
+// threads: warp w takes frequency i = 16 blockIdx.x + w, lanes stride over frames.  The
+// CTA's source row block v[n][:][chunk] is staged in shared memory chunk by chunk and serves
+// all 16 frequencies; each lane keeps 2K partial sums, one warp reduction at the end.
+constexpr int kMnmfTFreqs = 16;
+constexpr int kMnmfTChunk = 256;
+
+template <int K>
+__global__ void __launch_bounds__(kMnmfTFreqs * 32, 2) fastmnmf_t_kernel(float* __restrict__ tb,
+                                                                        const float* __restrict__ va,
+                                                                        const float* __restrict__ ab, int F, int N,
+                                                                        int T) {
+  constexpr int VP = pow2_ceil(2 * K);
+  __shared__ float sV[K * kMnmfTChunk];
+  const int n = blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * kMnmfTFreqs + w;
+  const bool live = i < F;
+  const float* ap = ab + ((size_t)(live ? i : 0) * N + n) * T;
+  const float* bp = ap + (size_t)F * N * T;
+  float acc[VP];
+#pragma unroll
+  for (int k = 0; k < VP; ++k) acc[k] = 0.f;
+  for (int c0 = 0; c0 < T; c0 += kMnmfTChunk) {
+    __syncthreads();                          // the previous chunk is consumed
+    for (int e = threadIdx.x; e < K * kMnmfTChunk; e += blockDim.x) {
+      const int k = e / kMnmfTChunk, jj = e - k * kMnmfTChunk;
+      sV[e] = (c0 + jj < T) ? __ldg(va + ((size_t)n * K + k) * T + c0 + jj) : 0.f;
+    }
+    __syncthreads();
+    if (live) {
+      const int cn = (T - c0 < kMnmfTChunk) ? T - c0 : kMnmfTChunk;
+#pragma unroll 8
+      for (int jj = lane; jj < cn; jj += 32) {
+        const float a = __ldg(ap + c0 + jj);
+        const float b = __ldg(bp + c0 + jj);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float vk = sV[k * kMnmfTChunk + jj];
+          acc[k] = fmaf(vk, a, acc[k]);
+          acc[K + k] = fmaf(vk, b, acc[K + k]);
+        }
+      }
+    }
+  }
+  warp_reduce_scatter<VP>(acc, lane);       // lane l holds the total of element (l VP) / 32
+  const int kk = lane < K ? lane : 0;
+  const float num = __shfl_sync(0xffffffffu, acc[0], (kk * 32) / VP);
+  const float den = __shfl_sync(0xffffffffu, acc[0], ((K + kk) * 32) / VP);
+  if (live && lane < K) {
+    // a basis whose activations have all underflowed to zero gives 0/0: it has no effect on
+    // the model and is left as it is (the lambda update treats a source the same way)
+    float* tp = tb + ((size_t)i * N + n) * K + lane;
+    *tp *= (den > 0.f) ? sqrtf(num / den) : 1.0f;
+  }
+}
+
+namespace {
+template <template <int> class Fn, typename... Args>
+cudaError_t dispatch_k(int K, Args... args) {
+  switch (K) {
+    case 1: return Fn<1>::run(args...);
+    case 2: return Fn<2>::run(args...);
+    case 3: return Fn<3>::run(args...);
+    case 4: return Fn<4>::run(args...);
+    case 5: return Fn<5>::run(args...);
+    case 6: return Fn<6>::run(args...);
+    case 7: return Fn<7>::run(args...);
+    case 8: return Fn<8>::run(args...);
+    case 9: return Fn<9>::run(args...);
+    case 10: return Fn<10>::run(args...);
+    case 11: return Fn<11>::run(args...);
+    case 12: return Fn<12>::run(args...);
+    case 13: return Fn<13>::run(args...);
+    case 14: return Fn<14>::run(args...);
+    case 15: return Fn<15>::run(args...);
+    case 16: return Fn<16>::run(args...);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+struct RunT {
+  static cudaError_t run(float* tb, const float* va, const float* ab, int F, int N, int T, cudaStream_t s) {
+    dim3 grid((F + kMnmfTFreqs - 1) / kMnmfTFreqs, N);
+    fastmnmf_t_kernel<K><<<grid, kMnmfTFreqs * 32, 0, s>>>(tb, va, ab, F, N, T);
+    return cudaGetLastError();
+  }
+};
+
+template <int K>
+struct RunV {
+  static cudaError_t run(const float* tb, const float* ab, float* va, float* h, int F, int N, int T, cudaStream_t s) {
+    const size_t smem = sizeof(float) * ((size_t)F * K + (size_t)kMnmfVWarps * 32 * 2 * K);
+    cudaError_t e = cudaFuncSetAttribute(fastmnmf_v_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((T + 31) / 32, N);
+    fastmnmf_v_kernel<K><<<grid, kMnmfVWarps * 32, smem, s>>>(tb, ab, va, h, F, N, T);
+    return cudaGetLastError();
+  }
+};
+}  // namespace
+
+cudaError_t launch_mnmf_t(float* tb, const float* va, const float* ab, int F, int N, int K, int T, cudaStream_t s) {
+  return dispatch_k<RunT>(K, tb, va, ab, F, N, T, s);
 }
 
 cudaError_t launch_mnmf_v(const float* tb, const float* ab, float* va, float* h, int F, int N, int K, int T,
                           cudaStream_t s) {
-  const size_t smem = mnmf_v_smem(F, K);
-  cudaError_t e = cudaFuncSetAttribute(fastmnmf_v_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((T + 31) / 32, N);
-  fastmnmf_v_kernel<<<grid, kMnmfVWarps * 32, smem, s>>>(tb, ab, va, h, F, N, K, T);
-  return cudaGetLastError();
+  return dispatch_k<RunV>(K, tb, ab, va, h, F, N, T, s);
 }
 
 cudaError_t launch_mnmf_h(const float* tb, const float* va, float* h, int F, int N, int K, int T, cudaStream_t s) {
