@@ -67,7 +67,7 @@ typedef enum {
   FASTFCA_MODEL_FASTFCA = 0,    /* joint-diagonalisation model, Sec. IV, IP+EM (Algorithm 1) */
   FASTFCA_MODEL_FCA = 1,        /* full-rank FCA, Sec. III (comparison model) */
   FASTFCA_MODEL_FASTFCA_MM = 2, /* the FastFCA model fitted by IP+MM (Algorithm 2); same
-                                   parameters and calls as FASTFCA; M 2..4, N 2..8, T <= 2048 */
+                                   parameters, calls and shapes as FASTFCA */
   FASTFCA_MODEL_FCA_MM = 3,     /* full-rank FCA fitted by MM (Eq. 15-17, geometric-mean R
                                    update); same parameters and calls as FCA */
   FASTFCA_MODEL_FASTMNMF = 4    /* FastMNMF (Sec. IV-H, App. C): FastFCA with the source powers

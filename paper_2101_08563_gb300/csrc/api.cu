@@ -278,7 +278,7 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
                   "no FastFCA kernel for M=%d N=%d T=%d (M in 2..%d, N in 1..%d, T within eight CTAs' "
                   "shared memory)", c.M, c.N, c.T, kMaxM, kMaxN);
     if (c.model == FASTFCA_MODEL_FASTFCA_MM && !ops.em_mm)
-      return fail(nullptr, FASTFCA_EUNSUPPORTED, "IP+MM (Algorithm 2) runs on M in 2..4, N in 2..8, T <= 2048");
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no IP+MM (Algorithm 2) kernel for M=%d N=%d T=%d", c.M, c.N, c.T);
   } else {
     if (!ffca::fca_ops(c.M, c.N, &fops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FCA kernel for M=%d N=%d", c.M, c.N);

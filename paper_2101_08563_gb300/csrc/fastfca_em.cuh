@@ -520,23 +520,23 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
           }
         }
       }
-      return;
-    }
-    float2 wc[M * M];
+    } else {
+      float2 wc[M * M];
 #pragma unroll
-    for (int i = 0; i < M * M; ++i) wc[i] = sWc[i];
+      for (int i = 0; i < M * M; ++i) wc[i] = sWc[i];
 #pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
-      const int t = tid + k * bd;
-      if (t < T) {
-        float2 xv[M];
-        load_x(t, xv);
+      for (int k = 0; k < kSlots; ++k) {
+        const int t = tid + k * bd;
+        if (t < T) {
+          float2 xv[M];
+          load_x(t, xv);
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          float2 y = make_float2(0.f, 0.f);
+          for (int m = 0; m < M; ++m) {
+            float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int a = 0; a < M; ++a) y = cfmaf(wc[m * M + a], xv[a], y);
-          pU[k * M + m] = fmaf(y.x, y.x, y.y * y.y);
+            for (int a = 0; a < M; ++a) y = cfmaf(wc[m * M + a], xv[a], y);
+            pU[k * M + m] = fmaf(y.x, y.x, y.y * y.y);
+          }
         }
       }
     }

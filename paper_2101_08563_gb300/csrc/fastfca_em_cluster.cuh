@@ -17,6 +17,10 @@
 //   n-loop   for each source: r = 1 + G (U / sigma^2 - 1), L[:,n] *= mean_t r, then
 //            H[n,:] *= (1/M) sum_m r / mean_t r in the next pass (Gauss-Seidel), with sigma^2
 //            updated by the change of that source's term: sigma^2_m += L'H' - LH
+//   (MM)     IP+MM (Algorithm 2, the MM template flag) replaces the n-loop: one pass forms
+//            sum_t U sigma^-4 H_n and sum_t sigma^-2 H_n for every (m, n), one cluster
+//            exchange sums them and every CTA updates all of L; then each frame's H column
+//            is updated with sigma^2 from the new L.  One cluster barrier for all sources.
 //
 // Every reduction over t (Q, log-likelihood, the n-loop means) is summed per warp, then per
 // CTA in warp order, then over the cluster in rank order through distributed shared memory,
@@ -127,7 +131,8 @@ template <int M>
 struct ClusterSmem {
   static constexpr int NE = M * M;                        // packed Hermitian entries of Q_m
   static constexpr int V = M * NE;                        // reals of all Q_m
-  static constexpr int kXV = (V > kCWarps * 8 ? V : kCWarps * 8) + 4;   // float exchange row
+  static constexpr int kXV0 = (V > kCWarps * 8 ? V : kCWarps * 8);
+  static constexpr int kXV = (kXV0 > 2 * M * kCMaxN ? kXV0 : 2 * M * kCMaxN) + 4;   // float exchange row
   static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
   static constexpr int kWcPad = (M * M + 1) & ~1;
   // byte offsets (all multiples of 16)
@@ -302,7 +307,7 @@ __device__ __forceinline__ void decode_entry(int e, int& a, int& b, int& kind) {
 // ------------------------------------------------------------------ the kernel
 // Grid: F * C CTAs of kCThreads threads in clusters of C (rank c of cluster f owns frames
 // [c Tc, ...) of frequency f); dynamic shared memory ClusterSmem<M>::bytes(N, Tc).
-template <int M>
+template <int M, bool MM = false>
 __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs p) {
   using SM = ClusterSmem<M>;
   constexpr int NE = SM::NE, V = SM::V, XV = SM::kXV;
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   // transaction barriers of the n-loop exchange: each phase expects one value per (CTA, warp,
   // m); armed here for the first two uses, re-armed after each use
   const unsigned push_bytes = (unsigned)(C * kCWarps * M * sizeof(float));
-  if (tid == 0) {
+  if (!MM && tid == 0) {
     mbar_init(&sMbar[0], 1);
     mbar_init(&sMbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       float llp = 0.f;
       bool bad = false;
       for (int j = tid; j < Tl; j += kCThreads) {
-        if (it > 0) {
+        if (!MM && it > 0) {
           float g = 0.f;
 #pragma unroll
           for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
@@ -648,84 +653,165 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     pass_U();
     FFCA_CMARK(it, 5);
 
-    // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's
-    // H update and its change of sigma^2
-#pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-      float Ln[M];
+    if constexpr (MM) {
+      // ---- Algorithm 2, the L line: num_mn = sum_t U sigma^-4 H_nt, den_mn = sum_t sigma^-2
+      // H_nt with sigma^2 of pass A (L and H unchanged since).  Warp w takes m = w % M and
+      // frame phase w / M (kCWarps / M phases; warps past them idle); each lane keeps the 2N
+      // sums of its frames, one warp reduction, then the phases and the cluster are summed in
+      // a fixed order, so every CTA computes the same L.
+      constexpr int NPH = kCWarps / M;
+      __syncthreads();        // U of frames other threads wrote (the EM loop reads only its own)
+      float acc[2 * kCMaxN];
 #pragma unroll
-      for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
-      float acc[MP];
+      for (int i = 0; i < 2 * kCMaxN; ++i) acc[i] = 0.f;
+      const int m = warp % M, ph = warp / M;
+      if (ph < NPH) {
+        for (int j = ph * 32 + lane; j < Tl; j += NPH * 32) {
+          const float rs = sR[m * Tcp + j];
+          const float a = sU[m * Tcp + j] * rs * rs;
 #pragma unroll
-      for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+          for (int n = 0; n < kCMaxN; ++n) {
+            if (n < N) {
+              const float hv = sH[n * Tcp + j];
+              acc[n] = fmaf(a, hv, acc[n]);
+              acc[kCMaxN + n] = fmaf(rs, hv, acc[kCMaxN + n]);
+            }
+          }
+        }
+      }
+      warp_reduce_scatter<2 * kCMaxN>(acc, lane);          // lane l: total of element l
+      float* scr = sPush;                                   // the EM exchange rows, unused here
+      scr[warp * 32 + lane] = acc[0];
+      __syncthreads();
+      float* xm = sX + par * XV;                            // [num (M N)][den (M N)]
+      for (int i = tid; i < 2 * M * N; i += kCThreads) {
+        const int half = i / (M * N), mn = i - half * (M * N);
+        const int mm = mn / N, n = mn - mm * N;
+        float s2 = 0.f;
+        for (int q = 0; q < NPH; ++q) s2 += scr[(q * M + mm) * 32 + half * kCMaxN + n];
+        xm[i] = s2;
+      }
+      cluster_sync();
+      for (int i = tid; i < M * N; i += kCThreads) {
+        const float num = cluster_sum_f(xm + i);
+        const float den = cluster_sum_f(xm + M * N + i);
+        // a source whose H row has underflowed to zero gives 0/0: it has no effect on the
+        // model, and L[:, n] is left as it is
+        sL[i] *= (den > 0.f) ? sqrtf(num / den) : 1.0f;
+      }
+      par ^= 1;
+      __syncthreads();
+      // ---- the H line: H <- H (.) {L^T [U (.) sigma^-4] / L^T sigma^-2}^1/2, sigma^2 from
+      // the new L, frame by frame (this CTA's frames only)
       for (int j = tid; j < Tl; j += kCThreads) {
-        if (n > 0) {
-          float g = 0.f;
+        float h[kCMaxN];
 #pragma unroll
-          for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
-          const float hold = sH[(n - 1) * Tcp + j];
-          const float hnew = hold * g;
-          sH[(n - 1) * Tcp + j] = hnew;
+        for (int n = 0; n < kCMaxN; ++n) h[n] = (n < N) ? sH[n * Tcp + j] : 0.f;
+        float a[M], b[M];
+#pragma unroll
+        for (int m2 = 0; m2 < M; ++m2) {
+          float s2 = 0.f;
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n)
+            if (n < N) s2 = fmaf(sL[m2 * N + n], h[n], s2);
+          const float rs = fast_rcp(s2);
+          b[m2] = rs;
+          a[m2] = sU[m2 * Tcp + j] * rs * rs;
+        }
+#pragma unroll
+        for (int n = 0; n < kCMaxN; ++n) {
+          if (n < N) {
+            float num = 0.f, den = 0.f;
+#pragma unroll
+            for (int m2 = 0; m2 < M; ++m2) {
+              num = fmaf(sL[m2 * N + n], a[m2], num);
+              den = fmaf(sL[m2 * N + n], b[m2], den);
+            }
+            sH[n * Tcp + j] = (den > 0.f) ? h[n] * sqrtf(num * fast_rcp(den)) : h[n];
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's
+      // H update and its change of sigma^2
+#pragma unroll 1
+      for (int n = 0; n < N; ++n) {
+        float Ln[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
+        float acc[MP];
+#pragma unroll
+        for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+        for (int j = tid; j < Tl; j += kCThreads) {
+          if (n > 0) {
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
+            const float hold = sH[(n - 1) * Tcp + j];
+            const float hnew = hold * g;
+            sH[(n - 1) * Tcp + j] = hnew;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              // sigma^2 <- sigma^2 - L H + L' H' (one rounding: fma), never below the new term
+              const float s2 = fmaf(Lnew[m], hnew, fmaf(-Lold[m], hold, sS[m * Tcp + j]));
+              sS[m * Tcp + j] = fmaxf(s2, Lnew[m] * hnew);
+            }
+          }
+          const float hn = sH[n * Tcp + j];
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            // sigma^2 <- sigma^2 - L H + L' H' (one rounding: fma), never below the new term
-            const float s2 = fmaf(Lnew[m], hnew, fmaf(-Lold[m], hold, sS[m * Tcp + j]));
-            sS[m * Tcp + j] = fmaxf(s2, Lnew[m] * hnew);
+            const float s2 = sS[m * Tcp + j];
+            const float rs = fast_rcp(s2);
+            const float G = Ln[m] * hn * rs;
+            const float rr = fmaf(G, fmaf(sU[m * Tcp + j], rs, -1.f), 1.f);
+            sR[m * Tcp + j] = rr;
+            acc[m] += rr;
           }
         }
-        const float hn = sH[n * Tcp + j];
+        // per-warp sums are pushed (st.async) into every CTA's receive row [rank][warp][m] of
+        // this parity, counted by that CTA's transaction barrier; each CTA waits on its own
+        // barrier, then lane (m, q) adds warps 2q, 2q+1 of every rank in rank order and two
+        // shuffles finish: the same order in every warp of every CTA.  A parity's row is
+        // rewritten only after every warp here has pushed the next exchange, i.e. read this one.
+        warp_reduce_scatter<MP>(acc, lane);
+        float* rb = sPush + npar * (kCMaxCluster * kCWarps * 8);
+        if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) {
+          float* slot = rb + (crank * kCWarps + warp) * 8 + (lane * MP) / 32;
+          for (int c = 0; c < C; ++c)
+            st_async_f32(dsmem_addr(slot, (unsigned)c), acc[0], dsmem_addr(&sMbar[npar], (unsigned)c));
+        }
+        {
+          int spins = 0;
+          while (!mbar_try_wait(&sMbar[npar], nphase[npar]) && ++spins < kMbarSpinLimit) {
+          }
+          if (spins >= kMbarSpinLimit && lane == 0) atomicOr(p.err, kErrClusterWait);
+        }
+        nphase[npar] ^= 1u;
+        float tot_l = 0.f;
+        {
+          const int m = lane >> 2, q = lane & 3;
+          if (m < M) {
+            for (int c = 0; c < C; ++c) {
+              tot_l += rb[(c * kCWarps + 2 * q) * 8 + m];
+              tot_l += rb[(c * kCWarps + 2 * q + 1) * 8 + m];
+            }
+          }
+          tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 1);
+          tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 2);
+        }
+        if (tid == 0) mbar_expect_tx(&sMbar[npar], push_bytes);   // arm this parity's next use
+        npar ^= 1;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const float s2 = sS[m * Tcp + j];
-          const float rs = fast_rcp(s2);
-          const float G = Ln[m] * hn * rs;
-          const float rr = fmaf(G, fmaf(sU[m * Tcp + j], rs, -1.f), 1.f);
-          sR[m * Tcp + j] = rr;
-          acc[m] += rr;
+          const float mean = __shfl_sync(0xffffffffu, tot_l, 4 * m) * invTf;
+          Lold[m] = Ln[m];
+          Lnew[m] = Ln[m] * mean;
+          sL[m * N + n] = Lnew[m];           // the same value from every thread
+          coef[m] = fast_rcp(mean) * (1.0f / (float)M);
         }
+        FFCA_CMARK(it, 6 + (n < 25 ? n : 25));
       }
-      // per-warp sums are pushed (st.async) into every CTA's receive row [rank][warp][m] of
-      // this parity, counted by that CTA's transaction barrier; each CTA waits on its own
-      // barrier, then lane (m, q) adds warps 2q, 2q+1 of every rank in rank order and two
-      // shuffles finish: the same order in every warp of every CTA.  A parity's row is
-      // rewritten only after every warp here has pushed the next exchange, i.e. read this one.
-      warp_reduce_scatter<MP>(acc, lane);
-      float* rb = sPush + npar * (kCMaxCluster * kCWarps * 8);
-      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) {
-        float* slot = rb + (crank * kCWarps + warp) * 8 + (lane * MP) / 32;
-        for (int c = 0; c < C; ++c)
-          st_async_f32(dsmem_addr(slot, (unsigned)c), acc[0], dsmem_addr(&sMbar[npar], (unsigned)c));
-      }
-      {
-        int spins = 0;
-        while (!mbar_try_wait(&sMbar[npar], nphase[npar]) && ++spins < kMbarSpinLimit) {
-        }
-        if (spins >= kMbarSpinLimit && lane == 0) atomicOr(p.err, kErrClusterWait);
-      }
-      nphase[npar] ^= 1u;
-      float tot_l = 0.f;
-      {
-        const int m = lane >> 2, q = lane & 3;
-        if (m < M) {
-          for (int c = 0; c < C; ++c) {
-            tot_l += rb[(c * kCWarps + 2 * q) * 8 + m];
-            tot_l += rb[(c * kCWarps + 2 * q + 1) * 8 + m];
-          }
-        }
-        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 1);
-        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 2);
-      }
-      if (tid == 0) mbar_expect_tx(&sMbar[npar], push_bytes);   // arm this parity's next use
-      npar ^= 1;
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const float mean = __shfl_sync(0xffffffffu, tot_l, 4 * m) * invTf;
-        Lold[m] = Ln[m];
-        Lnew[m] = Ln[m] * mean;
-        sL[m * N + n] = Lnew[m];           // the same value from every thread
-        coef[m] = fast_rcp(mean) * (1.0f / (float)M);
-      }
-      FFCA_CMARK(it, 6 + (n < 25 ? n : 25));
     }
   }
 

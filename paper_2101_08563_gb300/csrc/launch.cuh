@@ -137,12 +137,12 @@ bool cluster_shape(int T, int N, int* C, size_t* smem) {
   return false;
 }
 
-template <int M>
+template <int M, bool MM = false>
 cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   int C = 0;
   size_t smem = 0;
   if (!cluster_shape<M>(a.T, a.N, &C, &smem)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_cluster_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_cluster_kernel<M, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -157,7 +157,7 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M>, a);
+  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -173,8 +173,8 @@ cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH
 template <int M>
 FastOps make_cluster_ops() {
   FastOps o{};
-  o.em = &launch_em_cluster<M>;
-  o.em_mm = nullptr;
+  o.em = &launch_em_cluster<M, false>;
+  o.em_mm = &launch_em_cluster<M, true>;
   o.em_blk = nullptr;
   o.em_mm_blk = nullptr;
   o.block_stats = nullptr;

@@ -88,7 +88,10 @@ class Mixture:
 def generate_mixture(M: int, N: int, F: int, T: int, K: int, *, seed: int,
                      array: str = "linear", spacing: float = 0.04,
                      keep_images: bool = False) -> Mixture:
-    """Draw one mixture from the model (see the module docstring)."""
+    """Draw one mixture from the model (see the module docstring).  F >= 2: the frequency
+    grid nu_f = f fs / (2 (F - 1)) runs from 0 to fs / 2."""
+    if F < 2:
+        raise ValueError("the frequency grid needs F >= 2 (take one bin of a larger mixture)")
     rng = np.random.Generator(np.random.PCG64(seed))
     theta = rng.uniform(0.0, np.pi, size=N)
     B = rng.gamma(1.0, 1.0, size=(N, F, K))

@@ -57,9 +57,14 @@ def run_gpu(ff, x, init, N, iters, device_x=True):
     (4, 6, 3, 1250, 2),
     (2, 2, 3, 130, 4),
     (4, 8, 2, 2048, 1),    # the largest T one CTA holds
+    (4, 6, 1, 1250, 3),    # one frequency
+    (2, 1, 2, 100, 4),     # one source: sigma^2 = L H is the whole model (cluster kernel)
+    (4, 1, 1, 300, 3),
 ])
 def test_parity_small(ff, M, N, F, T, iters):
-    mix = synth.generate_mixture(M, N, F, T, 4, seed=100 + M * 10 + N)
+    # the generator's frequency grid needs F >= 2: one frequency is the upper bin of two
+    mix = synth.generate_mixture(M, N, max(F, 2), T, 4, seed=100 + M * 10 + N)
+    mix.x = np.ascontiguousarray(mix.x[-F:])
     init = synth.random_init(mix.x, N, seed=5)
     ll, c, P, lam, v, ll_f = run_gpu(ff, mix.x, init, N, iters)
     ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters)
@@ -256,7 +261,7 @@ def test_ip_mm_parity(ff, M, N, F, T, iters):
     assert rel(c.sum(axis=2), mix.x) < 1e-5
 
 
-def test_ip_mm_monotone_and_limits(ff):
+def test_ip_mm_monotone(ff):
     mix = synth.generate_mixture(4, 6, 8, 600, 8, seed=44)
     init = synth.random_init(mix.x, 6, seed=44)
     sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 6, model="fastfca_mm")
@@ -264,9 +269,32 @@ def test_ip_mm_monotone_and_limits(ff):
     ll = sep.iterate(30)
     sep.close()
     assert np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
-    x = torch.zeros((2, 64, 8), dtype=torch.complex64, device="cuda")
-    with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
-        ff.Separator(x, 12, model="fastfca_mm")
+
+
+@pytest.mark.parametrize("M,N,F,T,iters", [
+    (8, 12, 2, 300, 4),     # cluster of 1
+    (8, 12, 2, 2003, 3),    # cluster of 4, ragged
+    (5, 7, 3, 257, 4),      # odd M: some warps of the L line idle
+    (3, 10, 2, 400, 5),     # N beyond the frequency-resident kernel; two frame phases, two warps idle
+    (2, 16, 2, 150, 4),     # the most sources
+    (2, 1, 2, 100, 4),      # one source
+    (4, 6, 2, 3001, 3),     # T beyond one CTA of the frequency-resident kernel
+])
+def test_ip_mm_cluster_parity(ff, M, N, F, T, iters):
+    """IP+MM on the cluster kernel (large bins) against the oracle's Algorithm 2."""
+    mix = synth.generate_mixture(M, N, F, T, 8, seed=700 + M * 10 + N,
+                                 array="circular" if M >= 5 else "linear", spacing=0.05 if M >= 5 else 0.03)
+    init = synth.random_init(mix.x, N, seed=7)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N, model="fastfca_mm")
+    sep.set_params(init.P, init.lam, init.v)
+    ll = sep.iterate(iters)
+    c = sep.separate()
+    sep.close()
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters, algorithm="mm")
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
+    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
 
 
 # ---------------------------------------------------------------------------- piecewise stationary (Sec. VI-B)

@@ -57,11 +57,14 @@ def run_gpu(ff, x, N, K, st, iters):
     (2, 2, 1, 3, 64, 3),        # one basis
     (3, 2, 16, 2, 96, 2),       # the most bases, several (n, k) chunks
     (4, 8, 3, 2, 2048, 1),      # the most frames one CTA holds
+    (3, 2, 5, 1, 333, 3),       # one frequency: the v update sums over a single bin
 ])
 def test_fastmnmf_parity(ff, M, N, K, F, T, iters):
     """Log-likelihood after every iteration, per-frequency log-likelihood, images, W and the
     scale-free h = t v against the oracle from the same start."""
-    mix = synth.generate_mixture(M, N, F, T, K, seed=300 + M + N + K)
+    # the generator's frequency grid needs F >= 2: one frequency is the upper bin of two
+    mix = synth.generate_mixture(M, N, max(F, 2), T, K, seed=300 + M + N + K)
+    mix.x = np.ascontiguousarray(mix.x[-F:])
     st = synth.fastmnmf_random_init(mix.x, N, K, seed=17)
     ll, c, W, lam, t, v, ll_f = run_gpu(ff, mix.x, N, K, st, iters)
     ref = omn.run(mix.x, st.W, st.lam, st.t, st.v, iters=iters)
