@@ -103,8 +103,9 @@ fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* st
  * Algorithm 1 or 2 (cfg->model FASTFCA or FASTFCA_MM).  Every parameter call then has J
  * columns where fastfca_create's contexts have T: v float32 [F][N][J], the log-likelihood
  * is Eq. 44's (per block).  fastfca_separate filters every frame with the powers of its
- * block (c complex64 [F][T][N][M]).  B = 1 is fastfca_create.  EINVAL unless B divides T;
- * EUNSUPPORTED outside M 2..4, N 2..8, J <= 2048, or for the FCA models. */
+ * block (c complex64 [F][T][N][M]).  B = 1 is fastfca_create.  EINVAL unless B divides T,
+ * or for a model other than FASTFCA and FASTFCA_MM; EUNSUPPORTED for the (M, N, J) that
+ * fastfca_create would reject with J frames. */
 fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
                                      fastfca_ctx** out);
 

@@ -269,9 +269,10 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
   } else if (B > 1) {
     if (!fastfca_family(c.model))
       return fail(nullptr, FASTFCA_EINVAL, "the piecewise-stationary input serves the FastFCA models only");
-    if (!ffca::fast_ops(c.M, c.N, &ops) || c.T > ops.max_T || !ops.em_blk)
+    if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops) || !ops.em_blk)
       return fail(nullptr, FASTFCA_EUNSUPPORTED,
-                  "blocks of B frames run on M in 2..4, N in 2..8 and at most %d blocks", ffca::kMaxThreads * ffca::kSlots);
+                  "no FastFCA kernel for M=%d N=%d and %d blocks (M in 2..%d, N in 1..%d)", c.M, c.N, c.T, kMaxM,
+                  kMaxN);
   } else if (fastfca_family(c.model)) {
     if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops))
       return fail(nullptr, FASTFCA_EUNSUPPORTED,

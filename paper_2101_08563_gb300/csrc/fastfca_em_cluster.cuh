@@ -17,6 +17,9 @@
 //   n-loop   for each source: r = 1 + G (U / sigma^2 - 1), L[:,n] *= mean_t r, then
 //            H[n,:] *= (1/M) sum_m r / mean_t r in the next pass (Gauss-Seidel), with sigma^2
 //            updated by the change of that source's term: sigma^2_m += L'H' - LH
+//   (BL)     piecewise-stationary input (Sec. VI-B, the BL template flag): the "frames" are
+//            blocks j with packed X^_j (M^2 floats each, as block_stats_kernel writes them);
+//            the Q pass reads them instead of forming x x^H, and U = w_m^H X^_j w_m
 //   (MM)     IP+MM (Algorithm 2, the MM template flag) replaces the n-loop: one pass forms
 //            sum_t U sigma^-4 H_n and sum_t sigma^-2 H_n for every (m, n), one cluster
 //            exchange sums them and every CTA updates all of L; then each frame's H column
@@ -307,7 +310,7 @@ __device__ __forceinline__ void decode_entry(int e, int& a, int& b, int& kind) {
 // ------------------------------------------------------------------ the kernel
 // Grid: F * C CTAs of kCThreads threads in clusters of C (rank c of cluster f owns frames
 // [c Tc, ...) of frequency f); dynamic shared memory ClusterSmem<M>::bytes(N, Tc).
-template <int M, bool MM = false>
+template <int M, bool MM = false, bool BL = false>
 __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs p) {
   using SM = ClusterSmem<M>;
   constexpr int NE = SM::NE, V = SM::V, XV = SM::kXV;
@@ -348,7 +351,8 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
 
   const int t0 = crank * Tc;
   const int Tl = min(Tc, T - t0);
-  const float2* xf = p.x + ((size_t)f * T + t0) * M;
+  const float2* xf = BL ? nullptr : p.x + ((size_t)f * T + t0) * M;
+  const float* xhf = BL ? p.xh + ((size_t)f * T + t0) * NE : nullptr;     // blocks: packed X^_j
   double2* Pf = p.P + (size_t)f * M * M;
   float* lamf = p.lam + (size_t)f * M * N;
   float* vf = p.v + (size_t)f * N * T;
@@ -410,24 +414,53 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     }
   };
 
-  // U = |W^H x|^2 for this CTA's frames, two frames per thread at a time (loads overlap)
+  // U = |W^H x|^2 for this CTA's frames, two frames per thread at a time (loads overlap);
+  // blocks: U = w^H X^ w = sum_a |w_a|^2 X_aa + 2 sum_{a<b} Re(conj(w_a) w_b X_ab), with
+  // conj(w_a) = sWc[m M + a] (same frames per thread as for x)
   auto pass_U = [&]() {
-    for (int j = tid; j < Tl; j += 2 * kCThreads) {
-      const int j2 = j + kCThreads;
-      float2 xv[M], xw[M];
-      load_x(j, xv);
-      if (j2 < Tl) load_x(j2, xw);
+    if constexpr (BL) {
+      for (int j = tid; j < Tl; j += kCThreads) {
+        const float* e = xhf + (size_t)j * NE;
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        float2 y = make_float2(0.f, 0.f), z = make_float2(0.f, 0.f);
+        for (int m = 0; m < M; ++m) {
+          float u = 0.f;
 #pragma unroll
-        for (int a = 0; a < M; ++a) {
-          const float2 wc = sWc[m * M + a];
-          y = cfmaf(wc, xv[a], y);
-          z = cfmaf(wc, xw[a], z);
+          for (int a = 0; a < M; ++a) {
+            const float2 wa = sWc[m * M + a];
+            u = fmaf(fmaf(wa.x, wa.x, wa.y * wa.y), __ldg(e + a), u);
+          }
+          int idx = M;
+#pragma unroll
+          for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = a + 1; b < M; ++b) {
+              const float2 wa = sWc[m * M + a], wb = sWc[m * M + b];
+              const float pr = fmaf(wa.x, wb.x, wa.y * wb.y);       // wa conj(wb)
+              const float pi = fmaf(wa.y, wb.x, -wa.x * wb.y);
+              u = fmaf(2.f, fmaf(pr, __ldg(e + idx), -pi * __ldg(e + idx + 1)), u);
+              idx += 2;
+            }
+          sU[m * Tcp + j] = u;
         }
-        sU[m * Tcp + j] = fmaf(y.x, y.x, y.y * y.y);
-        if (j2 < Tl) sU[m * Tcp + j2] = fmaf(z.x, z.x, z.y * z.y);
+      }
+    } else {
+      for (int j = tid; j < Tl; j += 2 * kCThreads) {
+        const int j2 = j + kCThreads;
+        float2 xv[M], xw[M];
+        load_x(j, xv);
+        if (j2 < Tl) load_x(j2, xw);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float2 y = make_float2(0.f, 0.f), z = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            const float2 wc = sWc[m * M + a];
+            y = cfmaf(wc, xv[a], y);
+            z = cfmaf(wc, xw[a], z);
+          }
+          sU[m * Tcp + j] = fmaf(y.x, y.x, y.y * y.y);
+          if (j2 < Tl) sU[m * Tcp + j2] = fmaf(z.x, z.x, z.y * z.y);
+        }
       }
     }
   };
@@ -543,35 +576,55 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       const int per = (Tl + kCWarps - 1) / kCWarps;
       const int fb = warp * per, fe = min(fb + per, Tl);
       const int lf = lane >> 3, la = lane & 7;
-      for (int base = fb; base < fe; base += 32) {
-        float2 xr[8];
+      if constexpr (BL) {
+        // lane l reads entries l + 32 q of each block's packed X^ (coalesced per block)
+#pragma unroll 4
+        for (int fr = fb; fr < fe; ++fr) {
+          float ev[EPL];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int fr = base + 4 * k + lf;
-          xr[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+          for (int q = 0; q < EPL; ++q) {
+            const int e = lane + 32 * q;
+            ev[q] = (e < NE) ? __ldg(xhf + (size_t)fr * NE + e) : 0.f;
+          }
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const float w = sR[m * Tcp + fr];
+#pragma unroll
+            for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+          }
         }
+      }
+      if constexpr (!BL) {
+        for (int base = fb; base < fe; base += 32) {
+          float2 xr[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < 8; ++k) {
+            const int fr = base + 4 * k + lf;
+            xr[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+          }
 #pragma unroll
-          for (int fi = 0; fi < 4; ++fi) {
-            const int fr = base + 4 * k + fi;          // warp-uniform
-            if (fr >= fe) break;
-            float ev[EPL];
+          for (int k = 0; k < 8; ++k) {
 #pragma unroll
-            for (int q = 0; q < EPL; ++q) {
-              const float ax = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + ea[q]);
-              const float ay = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + ea[q]);
-              const float bx = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + eb[q]);
-              const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + eb[q]);
-              ev[q] = (ek[q] == 3) ? 0.f
-                      : (ek[q] == 0) ? fmaf(ax, ax, ay * ay)
-                      : (ek[q] == 1) ? fmaf(ax, bx, ay * by) : fmaf(ay, bx, -ax * by);
-            }
+            for (int fi = 0; fi < 4; ++fi) {
+              const int fr = base + 4 * k + fi;          // warp-uniform
+              if (fr >= fe) break;
+              float ev[EPL];
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-              const float w = sR[m * Tcp + fr];
+              for (int q = 0; q < EPL; ++q) {
+                const float ax = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + ea[q]);
+                const float ay = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + ea[q]);
+                const float bx = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + eb[q]);
+                const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + eb[q]);
+                ev[q] = (ek[q] == 3) ? 0.f
+                        : (ek[q] == 0) ? fmaf(ax, ax, ay * ay)
+                        : (ek[q] == 1) ? fmaf(ax, bx, ay * by) : fmaf(ay, bx, -ax * by);
+              }
 #pragma unroll
-              for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+              for (int m = 0; m < M; ++m) {
+                const float w = sR[m * Tcp + fr];
+#pragma unroll
+                for (int q = 0; q < EPL; ++q) acc[m][q] = fmaf(w, ev[q], acc[m][q]);
+              }
             }
           }
         }

@@ -119,14 +119,17 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
 // reads only the M values of z of its task (shared by the M threads of the task), and
 // consecutive threads write consecutive complex values of the output span (coalesced).
 // Rows of sZ are padded to M + 1 values so that the tasks of a warp fall in distinct banks.
+// With blocks of B frames (Sec. VI-B) v has J = T / B columns and frame t takes column t / B.
 constexpr int kMwfWFrames = 32;
 constexpr int kMwfWMaxN = 16;
 
 template <int M>
 __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
     const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
-    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int N) {
+    const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int N,
+    int B) {
   constexpr int kThreads = M * 32;
+  const int J = T / B;
   __shared__ float2 sWc[M * M];                                   // conj(W[a][m]) at [m*M + a]
   __shared__ float sL[M * kMwfWMaxN];
   __shared__ float2 sZ[kMwfWFrames * kMwfWMaxN * (M + 1)];        // [(tl*N + n)][m], padded
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
     const int tl = tid / M, m = tid - (tid / M) * M;
     if (tl < nt) {
       const int t = t0 + tl;
+      const int tb = t / B;
       const float2* xt = x + ((size_t)f * T + t) * M;
       float2 y = make_float2(0.f, 0.f);
 #pragma unroll
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
 #pragma unroll
       for (int n = 0; n < kMwfWMaxN; ++n) {
         const int nn = (n < N) ? n : 0;                  // index kept inside the arrays
-        const float hv = v[((size_t)f * N + nn) * T + t], lv = sL[m * N + nn];
+        const float hv = v[((size_t)f * N + nn) * J + tb], lv = sL[m * N + nn];
         h[n] = (n < N) ? hv : 0.f;
         s2 = fmaf((n < N) ? lv : 0.f, h[n], s2);
       }

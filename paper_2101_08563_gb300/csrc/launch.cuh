@@ -137,13 +137,14 @@ bool cluster_shape(int T, int N, int* C, size_t* smem) {
   return false;
 }
 
-template <int M, bool MM = false>
+template <int M, bool MM = false, bool BL = false>
 cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   int C = 0;
   size_t smem = 0;
   if (!cluster_shape<M>(a.T, a.N, &C, &smem)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_cluster_kernel<M, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  if (BL && !a.xh) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_cluster_kernel<M, MM, BL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.F * C), 1, 1);
@@ -157,27 +158,27 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM>, a);
+  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM, BL>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int M>
 cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
                             float2* c, int F, int T, int N, int B, cudaStream_t s) {
-  if (N < 1 || N > kMwfWMaxN || B != 1) return cudaErrorInvalidValue;
+  if (N < 1 || N > kMwfWMaxN || B < 1 || T % B != 0) return cudaErrorInvalidValue;
   dim3 grid(F, (T + kMwfWFrames - 1) / kMwfWFrames);
-  fastfca_mwf_wide_kernel<M><<<grid, M * 32, 0, s>>>(x, P, WmH, lam, v, c, F, T, N);
+  fastfca_mwf_wide_kernel<M><<<grid, M * 32, 0, s>>>(x, P, WmH, lam, v, c, F, T, N, B);
   return cudaGetLastError();
 }
 
 template <int M>
 FastOps make_cluster_ops() {
   FastOps o{};
-  o.em = &launch_em_cluster<M, false>;
-  o.em_mm = &launch_em_cluster<M, true>;
-  o.em_blk = nullptr;
-  o.em_mm_blk = nullptr;
-  o.block_stats = nullptr;
+  o.em = &launch_em_cluster<M, false, false>;
+  o.em_mm = &launch_em_cluster<M, true, false>;
+  o.em_blk = &launch_em_cluster<M, false, true>;
+  o.em_mm_blk = &launch_em_cluster<M, true, true>;
+  o.block_stats = &launch_block_stats<M>;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf_wide<M>;
   o.em_persistent = nullptr;

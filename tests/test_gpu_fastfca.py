@@ -304,9 +304,15 @@ def test_ip_mm_cluster_parity(ff, M, N, F, T, iters):
     (4, 6, 3, 1250, 5, "em"),
     (4, 6, 3, 1250, 5, "mm"),
     (3, 4, 3, 96, 8, "mm"),
+    (8, 12, 2, 1200, 4, "em"),    # the cluster kernel from here on
+    (8, 12, 2, 1200, 4, "mm"),
+    (5, 7, 2, 600, 3, "mm"),
+    (3, 10, 2, 800, 2, "em"),
+    (2, 3, 2, 6000, 2, "em"),     # 3000 blocks: more than one frequency-resident CTA holds
 ])
 def test_block_input_parity(ff, M, N, F, T, B, algorithm):
-    mix = synth.generate_mixture(M, N, F, T, 4, seed=60 + B)
+    mix = synth.generate_mixture(M, N, F, T, 4, seed=60 + B, array="circular" if M >= 5 else "linear",
+                                 spacing=0.05 if M >= 5 else 0.04)
     J = T // B
     rng = np.random.Generator(np.random.PCG64(60 + B))
     P = np.tile(np.eye(M, dtype=np.complex128), (F, 1, 1))
@@ -334,9 +340,9 @@ def test_block_input_errors(ff):
         ff.Separator(x, 4, block=7)                       # 7 does not divide 100
     with pytest.raises(ff.FastFCAError, match="EINVAL"):
         ff.Separator(x, 4, model="fca", block=4)
-    x = torch.zeros((1, 2500 * 2, 2), dtype=torch.complex64, device="cuda")
+    x = torch.zeros((1, 200, 9), dtype=torch.complex64, device="cuda")
     with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
-        ff.Separator(x, 3, block=2)                       # 2500 blocks
+        ff.Separator(x, 3, block=2)                       # M = 9
     # the default start of a block context is a valid start
     mix = synth.generate_mixture(2, 3, 4, 120, 4, seed=5)
     sep = ff.Separator(torch.from_numpy(mix.x).cuda(), 3, block=4, seed=3)
