@@ -203,7 +203,8 @@ const char* fastfca_version(void);
  */
 typedef struct fastfca_batch fastfca_batch;
 
-/* Creates a batch of B FastFCA mixtures: cfgs[b] (model must be FASTFCA) and xs[b] (complex64
+/* Creates a batch of B FastFCA mixtures: cfgs[b] (model FASTFCA for IP+EM, Algorithm 1, or
+ * FASTFCA_MM for IP+MM, Algorithm 2; mixtures may differ) and xs[b] (complex64
  * [F][T][M], host or device; device arrays are borrowed).  Parameters start as in
  * fastfca_create.  The initial schedule is the finest bucketing with one grid share per
  * class; fastfca_batch_tune picks a measured one. */

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libfastfca.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
-SOURCES = ["api.cu", "fastfca_m2.cu", "fastfca_m3.cu", "fastfca_m4.cu", "fca_ops.cu", "noalloc.cu", "batch.cu",
+SOURCES = ["fastfca_m4_hi.cu", "fastfca_m4.cu", "fastfca_m3.cu", "fastfca_m2.cu", "api.cu", "fca_ops.cu", "noalloc.cu", "batch.cu",
            "fastmnmf_m2.cu", "fastmnmf_m3.cu", "fastmnmf_m4.cu", "fastmnmf_common.cu",
            "learn.cu", "fastfca_cluster_lo.cu", "fastfca_cluster_hi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

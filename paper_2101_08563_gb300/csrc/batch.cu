@@ -43,7 +43,7 @@ struct Mix {
 };
 
 struct Class {
-  int M = 0, N = 0, bd = 0, grid = 0;
+  int M = 0, N = 0, mm = 0, bd = 0, grid = 0;   // mm: 0 IP+EM (Algorithm 1), 1 IP+MM (Algorithm 2)
   std::vector<size_t> items;          // global item indices, longest first
   ffca::EmItem* d_items = nullptr;
   int* d_counter = nullptr;
@@ -178,16 +178,18 @@ fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
     auto key = std::make_pair(m.cfg.M, m.cfg.N);
     group_max_T[key] = std::max(group_max_T[key], m.cfg.T);
   }
-  std::map<std::tuple<int, int, int>, size_t> index;
+  std::map<std::tuple<int, int, int, int>, size_t> index;
   for (size_t mi = 0; mi < b->mix.size(); ++mi) {
     const Mix& m = b->mix[mi];
     const int bd = bucket_threads(scheme, m.cfg.T, group_max_T[std::make_pair(m.cfg.M, m.cfg.N)]);
-    auto key = std::make_tuple(m.cfg.M, m.cfg.N, bd);
+    const int mm = m.cfg.model == FASTFCA_MODEL_FASTFCA_MM ? 1 : 0;
+    auto key = std::make_tuple(m.cfg.M, m.cfg.N, mm, bd);
     auto it = index.find(key);
     if (it == index.end()) {
       Class c;
       c.M = m.cfg.M;
       c.N = m.cfg.N;
+      c.mm = mm;
       c.bd = bd;
       c.ops = m.ops;
       index[key] = b->classes.size();
@@ -208,7 +210,7 @@ fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
   }
   for (size_t ci = 0; ci < b->classes.size(); ++ci) {
     Class& c = b->classes[ci];
-    const int per_sm = std::max(1, c.ops.em_blocks_per_sm(c.bd));
+    const int per_sm = std::max(1, c.ops.em_blocks_per_sm[c.mm](c.bd));
     const double share = total > 0 ? work[ci] / total : 1.0;
     int grid = (int)std::lround(grid_factor * share * per_sm * b->sms);
     grid = std::max(1, std::min<int>(grid, (int)c.items.size()));
@@ -245,7 +247,7 @@ fastfca_status enqueue_all(fastfca_batch* b, int n_iter, cudaStream_t origin) {
     cudaStream_t s = b->side[ci];
     BCK(b, cudaStreamWaitEvent(s, fork, 0), "fork wait");
     BCK(b, cudaMemsetAsync(c.d_counter, 0, sizeof(int), s), "counter reset");
-    BCK(b, c.ops.em_persistent(c.d_items, (int)c.items.size(), n_iter, c.d_counter, b->d_err, c.bd, c.grid, s),
+    BCK(b, c.ops.em_persistent[c.mm](c.d_items, (int)c.items.size(), n_iter, c.d_counter, b->d_err, c.bd, c.grid, s),
         "persistent launch");
     BCK(b, cudaEventRecord(b->ev[ci], s), "join record");
     BCK(b, cudaStreamWaitEvent(origin, b->ev[ci], 0), "join wait");
@@ -315,7 +317,7 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
     const fastfca_config c = cfgs[i];
     Mix& m = b->mix[i];
     m.cfg = c;
-    if (c.F < 1 || c.T < 1 || c.model != FASTFCA_MODEL_FASTFCA || !xs[i]) {
+    if (c.F < 1 || c.T < 1 || (c.model != FASTFCA_MODEL_FASTFCA && c.model != FASTFCA_MODEL_FASTFCA_MM) || !xs[i]) {
       bfail(b, FASTFCA_EINVAL, "mixture %d: bad config or NULL x", i);
       return bail(FASTFCA_EINVAL);
     }

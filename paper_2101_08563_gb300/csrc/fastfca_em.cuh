@@ -898,10 +898,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Persistent form for batches of mixtures: each CTA takes items (one frequency of one mixture
-// each, all of this kernel's (M, N)) from an atomic counter, in the order they are listed
+// each, all of this kernel's (M, N) and algorithm: IP+EM, or IP+MM with MM) from an atomic counter, in the order they are listed
 // (the host lists them longest-first), until the list is exhausted.  blockDim.x * kSlots must
 // cover every item's T.  No CTA waits on another.
-template <int M, int N>
+template <int M, int N, bool MM = false>
 __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_persistent_kernel(const EmItem* __restrict__ items,
                                                                     int n_items, int n_iter,
                                                                     int* counter, int* err) {
@@ -920,7 +920,7 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_persistent_kernel(const EmIte
       continue;
     }
     const unsigned long long t0 = global_ns();
-    em_frequency<M, N>(q, err, smem_raw);
+    em_frequency<M, N, MM>(q, err, smem_raw);
     __syncthreads();
     if (threadIdx.x == 0 && q.stamp) {
       q.stamp[0] = t0;

@@ -18,11 +18,12 @@ struct FastOps {
   // B: frames per block of v (1 = per frame; frame t reads v column t / B)
   cudaError_t (*mwf)(const float2* x, const double2* P, const float2* WmH, const float* lam,
                      const float* v, float2* c, int F, int T, int N, int B, cudaStream_t s);
-  // persistent batch form: items in device memory, `bd` threads per CTA, `grid` CTAs
-  cudaError_t (*em_persistent)(const EmItem* items, int n_items, int n_iter, int* counter, int* err, int bd,
-                               int grid, cudaStream_t s);
+  // persistent batch form: items in device memory, `bd` threads per CTA, `grid` CTAs; [0] IP+EM
+  // (Algorithm 1), [1] IP+MM (Algorithm 2)
+  cudaError_t (*em_persistent[2])(const EmItem* items, int n_items, int n_iter, int* counter, int* err, int bd,
+                                  int grid, cudaStream_t s);
   size_t (*em_smem)(int bd);
-  int (*em_blocks_per_sm)(int bd);
+  int (*em_blocks_per_sm[2])(int bd);
   int max_T;
   bool cluster;          // the cluster kernel (any T it fits, runtime N); no batch form
 };
@@ -53,15 +54,15 @@ cudaError_t launch_block_stats(const float2* x, float* xh, int F, int J, int B, 
   return cudaGetLastError();
 }
 
-template <int M, int N>
+template <int M, int N, bool MM>
 cudaError_t launch_em_persistent(const EmItem* items, int n_items, int n_iter, int* counter, int* err, int bd,
                                  int grid, cudaStream_t s) {
   if (bd > kMaxThreads || bd % 32 != 0) return cudaErrorInvalidConfiguration;
   const size_t smem = EmSmem<M, N>::bytes(bd);
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_persistent_kernel<M, N>,
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_persistent_kernel<M, N, MM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fastfca_em_persistent_kernel<M, N><<<grid, bd, smem, s>>>(items, n_items, n_iter, counter, err);
+  fastfca_em_persistent_kernel<M, N, MM><<<grid, bd, smem, s>>>(items, n_items, n_iter, counter, err);
   return cudaGetLastError();
 }
 
@@ -70,14 +71,14 @@ size_t em_smem_bytes(int bd) {
   return EmSmem<M, N>::bytes(bd);
 }
 
-template <int M, int N>
+template <int M, int N, bool MM>
 int em_blocks_per_sm(int bd) {
   const size_t smem = EmSmem<M, N>::bytes(bd);
-  if (cudaFuncSetAttribute(fastfca_em_persistent_kernel<M, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(fastfca_em_persistent_kernel<M, N, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fastfca_em_persistent_kernel<M, N>, bd, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fastfca_em_persistent_kernel<M, N, MM>, bd, smem) !=
       cudaSuccess)
     return 0;
   return nb;
@@ -108,9 +109,11 @@ FastOps make_fast_ops() {
   o.block_stats = &launch_block_stats<M>;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf<M, N>;
-  o.em_persistent = &launch_em_persistent<M, N>;
+  o.em_persistent[0] = &launch_em_persistent<M, N, false>;
+  o.em_persistent[1] = &launch_em_persistent<M, N, true>;
   o.em_smem = &em_smem_bytes<M, N>;
-  o.em_blocks_per_sm = &em_blocks_per_sm<M, N>;
+  o.em_blocks_per_sm[0] = &em_blocks_per_sm<M, N, false>;
+  o.em_blocks_per_sm[1] = &em_blocks_per_sm<M, N, true>;
   o.max_T = kMaxThreads * kSlots;
   o.cluster = false;
   return o;
@@ -181,9 +184,11 @@ FastOps make_cluster_ops() {
   o.block_stats = &launch_block_stats<M>;
   o.winv = &launch_winv<M>;
   o.mwf = &launch_mwf_wide<M>;
-  o.em_persistent = nullptr;
+  o.em_persistent[0] = nullptr;
+  o.em_persistent[1] = nullptr;
   o.em_smem = nullptr;
-  o.em_blocks_per_sm = nullptr;
+  o.em_blocks_per_sm[0] = nullptr;
+  o.em_blocks_per_sm[1] = nullptr;
   o.max_T = 0;                     // set by cluster_ops for the N at hand
   o.cluster = true;
   return o;

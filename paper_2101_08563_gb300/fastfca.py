@@ -338,12 +338,14 @@ class Batch:
     """Many independent FastFCA mixtures iterated together in one CUDA-graph launch.
 
     xs: list of complex64 (F_b, T_b, M_b) arrays (host or CUDA); Ns: sources per mixture;
-    seeds: per-mixture seeds of the default initial v (default: the mixture index).
+    seeds: per-mixture seeds of the default initial v (default: the mixture index);
+    models: per-mixture "fastfca" (IP+EM, Algorithm 1, the default) or "fastfca_mm" (IP+MM,
+    Algorithm 2).
     """
 
     SCHEMES = {0: "fine", 1: "coarse", 2: "single"}
 
-    def __init__(self, xs, Ns, stream=None, seeds=None):
+    def __init__(self, xs, Ns, stream=None, seeds=None, models=None):
         self.lib = load()
         if len(xs) != len(Ns) or not xs:
             raise ValueError("xs and Ns must be non-empty and of equal length")
@@ -356,7 +358,9 @@ class Batch:
             F, T, M = (int(s) for s in x.shape)
             self.shapes.append((F, T, M, int(N)))
             seed = i if seeds is None else int(seeds[i]) & 0x7fffffff
-            cfgs[i] = Config(F, T, M, int(N), MODEL_FASTFCA, seed)
+            model = MODEL_FASTFCA if models is None else {"fastfca": MODEL_FASTFCA,
+                                                          "fastfca_mm": MODEL_FASTFCA_MM}[models[i]]
+            cfgs[i] = Config(F, T, M, int(N), model, seed)
             p, keep = _ptr(x, np.complex64, (F, T, M), f"xs[{i}]")
             ptrs[i] = p.value
             self._xs.append(keep)

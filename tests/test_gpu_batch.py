@@ -77,3 +77,29 @@ def test_batch_tuned_matches_oracle_and_resumes(ff):
         assert np.linalg.norm(c.cpu().numpy() - cr) / np.linalg.norm(cr) <= 1e-4, b
     assert np.all(ll2 >= ll1 - 1e-6 * np.abs(ll1))
     bt.close()
+
+
+def test_batch_mixed_algorithms(ff):
+    """A batch whose mixtures take Algorithm 1 or Algorithm 2 each: every mixture matches the
+    single-mixture path of its own algorithm bit for bit, and the oracle's run."""
+    items = mixed_batch(seed=11, B=8, F=4)
+    models = ["fastfca_mm" if b % 2 else "fastfca" for b in range(len(items))]
+    xs = [torch.from_numpy(m.x).cuda() for m, _, _ in items]
+    bt = ff.Batch(xs, [N for _, _, N in items], models=models)
+    for b, (m, init, N) in enumerate(items):
+        bt.set_params(b, init.P, init.lam, init.v)
+    scheme, factor = bt.tune(2)
+    for b, (m, init, N) in enumerate(items):
+        bt.set_params(b, init.P, init.lam, init.v)
+    ll, _ = bt.iterate(4)
+    for b, (m, init, N) in enumerate(items):
+        sep = ff.Separator(xs[b], N, model=models[b])
+        sep.set_params(init.P, init.lam, init.v)
+        sep.iterate(4, return_ll=False)
+        Ps, ls, vs = sep.get_params()
+        sep.close()
+        Pb, lb, vb = bt.get_params(b)
+        assert np.array_equal(Pb, Ps) and np.array_equal(lb, ls) and np.array_equal(vb, vs), (b, models[b])
+        ref = off.run(m.x, init.P, init.lam, init.v, iters=4, algorithm="mm" if b % 2 else "em")
+        assert ll[b] == pytest.approx(ref["ll"][:, -1].sum(), rel=1e-5), b
+    bt.close()
