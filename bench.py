@@ -623,9 +623,10 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
-def run_profile_case(F, iters, workload="fca_cmp"):
+def run_profile_case(F, iters, workload="fca_cmp", model="fastfca"):
     """A workload's first 8 frequencies tiled to F (so the launch has F frequencies of the
-    workload's shape), two launches of the IP+EM kernel: 2 iterations, then `iters`.
+    workload's shape), two launches of the IP+EM kernel (model "fastfca_mm": IP+MM): 2
+    iterations, then `iters`.
     workload "fastmnmf": the full M=4 N=6 K=8 F=513 T=1250 mixture, FastMNMF, 2 iterations
     then `iters` (each iteration one fastmnmf_freq_kernel and one fastmnmf_v_kernel launch)."""
     import torch
@@ -650,7 +651,7 @@ def run_profile_case(F, iters, workload="fca_cmp"):
     x = np.tile(mix.x, (F // 8 + 1, 1, 1))[:F].copy()
     init = synth.random_init(x, w.N, seed=w.seed)
     build.build()
-    sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N)
+    sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N, model=model)
     sep.set_params(init.P, init.lam, init.v)
     sep.iterate(2, return_ll=False)
     sep.set_params(init.P, init.lam, init.v)
@@ -709,6 +710,7 @@ def main():
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
     ap.add_argument("--profile-F", type=int, default=608)
     ap.add_argument("--profile-iters", type=int, default=5)
+    ap.add_argument("--profile-model", default="fastfca", choices=["fastfca", "fastfca_mm"])
     ap.add_argument("--profile-workload", default="fca_cmp", choices=["fca_cmp", "large", "fastmnmf"])
     args = ap.parse_args()
     if args.warmup < 3:
@@ -724,7 +726,7 @@ def main():
               "l2": "flushed between steps (512 MiB write, untimed)"}
 
     if args.profile:
-        run_profile_case(args.profile_F, args.profile_iters, args.profile_workload)
+        run_profile_case(args.profile_F, args.profile_iters, args.profile_workload, args.profile_model)
         return
 
     if args.impl == "reference":
