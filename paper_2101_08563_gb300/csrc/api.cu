@@ -260,9 +260,13 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
   ffca::FcaOps fops{};
   ffca::MnmfOps mops{};
   if (mnmf) {
-    if (!ffca::fast_ops(c.M, c.N, &ops) || !ffca::mnmf_ops(c.M, c.N, &mops) || c.T > mops.max_T)
-      return fail(nullptr, FASTFCA_EUNSUPPORTED, "FastMNMF runs on M in 2..4, N in 2..8 and T <= %d",
-                  ffca::kMaxThreads * ffca::kSlots);
+    // the frequency-resident per-frequency step where it fits, else the cluster form
+    const bool resident = ffca::mnmf_ops(c.M, c.N, &mops) && c.T <= mops.max_T;
+    if (!resident && !ffca::mnmf_cluster_ops(c.M, c.N, c.T, &mops))
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no FastMNMF kernel for M=%d N=%d T=%d (M in 2..%d, N in 1..%d)",
+                  c.M, c.N, c.T, kMaxM, kMaxN);
+    if (!ffca::fast_ops_for(c.M, c.N, c.T, &ops))
+      return fail(nullptr, FASTFCA_EUNSUPPORTED, "no Wiener filter for M=%d N=%d T=%d", c.M, c.N, c.T);
     if ((long long)c.F * K > ffca::kMnmfMaxFK)
       return fail(nullptr, FASTFCA_EUNSUPPORTED, "FastMNMF holds F*K <= %d bases of one source on chip (F=%d, K=%d)",
                   ffca::kMnmfMaxFK, c.F, K);
@@ -458,6 +462,7 @@ fastfca_status mnmf_freq(fastfca_ctx* ctx, int iterate, double* ll_out, int ll_s
   a.err = ctx->err;
   a.F = c.F;
   a.T = c.T;
+  a.N = c.N;
   a.ll_stride = ll_stride;
   a.iterate = iterate;
   CK(ctx, ctx->mops.freq(a, ctx->stream), "FastMNMF frequency launch");
@@ -542,7 +547,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
       if (st) return st;
       CK(ctx, ffca::launch_mnmf_t(ctx->tb, ctx->va, ctx->ab, c.F, c.N, ctx->K, c.T, ctx->stream),
          "FastMNMF basis update launch");
-      CK(ctx, ctx->mops.ab(ctx->lam, ctx->tb, ctx->va, ctx->ubuf, ctx->ab, c.F, ctx->K, c.T, ctx->err, ctx->stream),
+      CK(ctx, ctx->mops.ab(ctx->lam, ctx->tb, ctx->va, ctx->ubuf, ctx->ab, c.F, c.N, ctx->K, c.T, ctx->err, ctx->stream),
          "FastMNMF activation-update terms launch");
       CK(ctx, ffca::launch_mnmf_v(ctx->tb, ctx->ab, ctx->va, ctx->v, c.F, c.N, ctx->K, c.T, ctx->stream),
          "FastMNMF activation update launch");

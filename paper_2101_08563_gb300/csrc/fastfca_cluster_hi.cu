@@ -1,4 +1,5 @@
-// Cluster-kernel FastFCA ops (large bins) for M = 6..8 microphones, any N <= 16.
+// Cluster-kernel FastFCA and FastMNMF ops (large bins) for M = 6..8 microphones, any N <= 16.
+#include "fastmnmf_cluster.cuh"
 #include "launch.cuh"
 
 namespace ffca {
@@ -16,6 +17,17 @@ bool cluster_ops(int M, int N, int T, FastOps* o) {
   }
   o->max_T = T;
   return true;
+}
+
+bool mnmf_cluster_ops_lo(int M, int N, int T, MnmfOps* o);
+
+bool mnmf_cluster_ops(int M, int N, int T, MnmfOps* o) {
+  switch (M) {
+    case 6: return mnmf_cluster_ops_m<6>(N, T, o);
+    case 7: return mnmf_cluster_ops_m<7>(N, T, o);
+    case 8: return mnmf_cluster_ops_m<8>(N, T, o);
+    default: return mnmf_cluster_ops_lo(M, N, T, o);
+  }
 }
 
 }  // namespace ffca

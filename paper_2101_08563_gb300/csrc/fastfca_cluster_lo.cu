@@ -1,4 +1,5 @@
-// Cluster-kernel FastFCA ops (large bins) for M = 2..5 microphones, any N <= 16.
+// Cluster-kernel FastFCA and FastMNMF ops (large bins) for M = 2..5 microphones, any N <= 16.
+#include "fastmnmf_cluster.cuh"
 #include "launch.cuh"
 
 namespace ffca {
@@ -15,6 +16,16 @@ bool cluster_ops_lo(int M, int N, int T, FastOps* o) {
   }
   o->max_T = T;
   return true;
+}
+
+bool mnmf_cluster_ops_lo(int M, int N, int T, MnmfOps* o) {
+  switch (M) {
+    case 2: return mnmf_cluster_ops_m<2>(N, T, o);
+    case 3: return mnmf_cluster_ops_m<3>(N, T, o);
+    case 4: return mnmf_cluster_ops_m<4>(N, T, o);
+    case 5: return mnmf_cluster_ops_m<5>(N, T, o);
+    default: return false;
+  }
 }
 
 }  // namespace ffca

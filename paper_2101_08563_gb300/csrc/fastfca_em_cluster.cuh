@@ -20,6 +20,11 @@
 //   (BL)     piecewise-stationary input (Sec. VI-B, the BL template flag): the "frames" are
 //            blocks j with packed X^_j (M^2 floats each, as block_stats_kernel writes them);
 //            the Q pass reads them instead of forming x x^H, and U = w_m^H X^_j w_m
+//   (MN)     FastMNMF's per-frequency step (App. C, the MN template flag): H holds the given
+//            h = t v; one iteration of Q, IP, U and lambda's MM update (the L line below),
+//            then U and a = sum_m lambda U / sigma^4, b = sum_m lambda / sigma^2 (new lambda)
+//            are written for the kernels that update the bases and activations; the
+//            log-likelihood is that of the incoming parameters
 //   (MM)     IP+MM (Algorithm 2, the MM template flag) replaces the n-loop: one pass forms
 //            sum_t U sigma^-4 H_n and sum_t sigma^-2 H_n for every (m, n), one cluster
 //            exchange sums them and every CTA updates all of L; then each frame's H column
@@ -310,8 +315,9 @@ __device__ __forceinline__ void decode_entry(int e, int& a, int& b, int& kind) {
 // ------------------------------------------------------------------ the kernel
 // Grid: F * C CTAs of kCThreads threads in clusters of C (rank c of cluster f owns frames
 // [c Tc, ...) of frequency f); dynamic shared memory ClusterSmem<M>::bytes(N, Tc).
-template <int M, bool MM = false, bool BL = false>
+template <int M, bool MM = false, bool BL = false, bool MN = false>
 __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs p) {
+  static_assert(!(MN && BL), "FastMNMF takes frames");
   using SM = ClusterSmem<M>;
   constexpr int NE = SM::NE, V = SM::V, XV = SM::kXV;
   constexpr int EPL = (NE + 31) / 32;
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   // transaction barriers of the n-loop exchange: each phase expects one value per (CTA, warp,
   // m); armed here for the first two uses, re-armed after each use
   const unsigned push_bytes = (unsigned)(C * kCWarps * M * sizeof(float));
-  if (!MM && tid == 0) {
+  if (!MM && !MN && tid == 0) {
     mbar_init(&sMbar[0], 1);
     mbar_init(&sMbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -498,15 +504,18 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
   for (int m = 0; m < M; ++m) { coef[m] = 0.f; Lold[m] = 0.f; Lnew[m] = 0.f; }
   int par = 0;
 
-  if (p.n_iter == 0) {
+  if (p.n_iter == 0 || (MN && p.ll_hist)) {     // the log-likelihood of the incoming W needs its U
     pass_U();
     __syncthreads();
   }
 
 #pragma unroll 1
   for (int it = 0;; ++it) {
-    const bool have_ll = (it > 0) || (p.n_iter == 0);
+    // MN: the launch's one iteration reports the log-likelihood of the incoming parameters,
+    // into slot `it` (0); otherwise slot it - 1 holds the value after iteration it - 1
+    const bool have_ll = MN ? (p.ll_hist != nullptr || p.n_iter == 0) : ((it > 0) || (p.n_iter == 0));
     const bool do_iter = it < p.n_iter;
+    const int ll_slot = MN ? it : it - 1;
     FFCA_CMARK(it, 0);
 
     // ---- pass A: pending H[N-1,:] update, sigma^2 = L H, 1/sigma^2, log-likelihood terms
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       float llp = 0.f;
       bool bad = false;
       for (int j = tid; j < Tl; j += kCThreads) {
-        if (!MM && it > 0) {
+        if (!MM && !MN && it > 0) {
           float g = 0.f;
 #pragma unroll
           for (int m = 0; m < M; ++m) g = fmaf(sR[m * Tcp + j], coef[m], g);
@@ -557,7 +566,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       cluster_sync();
       if (crank == 0 && tid == 0) {
         const double ll = ll_from_sum(cluster_sum(xll));
-        if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+        if ((MN || it > 0) && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + ll_slot] = ll;
         if (p.ll_last) p.ll_last[f] = ll;
       }
       break;
@@ -662,7 +671,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
     }
     if (have_ll && crank == 0 && tid == 0 && p.ll_hist)
-      p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll_from_sum(cluster_sum(xll));
+      p.ll_hist[(size_t)f * p.ll_stride + ll_slot] = ll_from_sum(cluster_sum(xll));
     par ^= 1;
     __syncthreads();
     FFCA_CMARK(it, 2);
@@ -706,7 +715,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     pass_U();
     FFCA_CMARK(it, 5);
 
-    if constexpr (MM) {
+    if constexpr (MM || MN) {
       // ---- Algorithm 2, the L line: num_mn = sum_t U sigma^-4 H_nt, den_mn = sum_t sigma^-2
       // H_nt with sigma^2 of pass A (L and H unchanged since).  Warp w takes m = w % M and
       // frame phase w / M (kCWarps / M phases; warps past them idle); each lane keeps the 2N
@@ -754,37 +763,77 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
       }
       par ^= 1;
       __syncthreads();
-      // ---- the H line: H <- H (.) {L^T [U (.) sigma^-4] / L^T sigma^-2}^1/2, sigma^2 from
-      // the new L, frame by frame (this CTA's frames only)
-      for (int j = tid; j < Tl; j += kCThreads) {
-        float h[kCMaxN];
+      if constexpr (MN) {
+        // ---- FastMNMF: U and the bases' update terms with sigma^2 from the new lambda and
+        // the given h, for this CTA's frames; then the launch's one iteration is done
+        const size_t plane = (size_t)p.F * N * T;
+        for (int j = tid; j < Tl; j += kCThreads) {
+          float h[kCMaxN];
 #pragma unroll
-        for (int n = 0; n < kCMaxN; ++n) h[n] = (n < N) ? sH[n * Tcp + j] : 0.f;
-        float a[M], b[M];
+          for (int n = 0; n < kCMaxN; ++n) h[n] = (n < N) ? sH[n * Tcp + j] : 0.f;
+          float e[M], r[M];
+          bool bad = false;
 #pragma unroll
-        for (int m2 = 0; m2 < M; ++m2) {
-          float s2 = 0.f;
+          for (int m2 = 0; m2 < M; ++m2) {
+            float s2 = 0.f;
 #pragma unroll
-          for (int n = 0; n < kCMaxN; ++n)
-            if (n < N) s2 = fmaf(sL[m2 * N + n], h[n], s2);
-          const float rs = fast_rcp(s2);
-          b[m2] = rs;
-          a[m2] = sU[m2 * Tcp + j] * rs * rs;
-        }
+            for (int n = 0; n < kCMaxN; ++n)
+              if (n < N) s2 = fmaf(sL[m2 * N + n], h[n], s2);
+            bad |= !(s2 > 0.f && s2 < INFINITY);
+            r[m2] = fast_rcp(s2);
+            const float u = sU[m2 * Tcp + j];
+            e[m2] = u * r[m2] * r[m2];
+            p.mn_u[((size_t)f * M + m2) * T + t0 + j] = u;
+          }
+          if (bad) atomicOr(p.err, kErrSigma);
 #pragma unroll
-        for (int n = 0; n < kCMaxN; ++n) {
-          if (n < N) {
-            float num = 0.f, den = 0.f;
+          for (int n = 0; n < kCMaxN; ++n) {
+            if (n < N) {
+              float a = 0.f, b = 0.f;
 #pragma unroll
-            for (int m2 = 0; m2 < M; ++m2) {
-              num = fmaf(sL[m2 * N + n], a[m2], num);
-              den = fmaf(sL[m2 * N + n], b[m2], den);
+              for (int m2 = 0; m2 < M; ++m2) {
+                a = fmaf(sL[m2 * N + n], e[m2], a);
+                b = fmaf(sL[m2 * N + n], r[m2], b);
+              }
+              p.mn_ab[((size_t)f * N + n) * T + t0 + j] = a;
+              p.mn_ab[plane + ((size_t)f * N + n) * T + t0 + j] = b;
             }
-            sH[n * Tcp + j] = (den > 0.f) ? h[n] * sqrtf(num * fast_rcp(den)) : h[n];
           }
         }
+        break;                 // uniform over the cluster: every CTA leaves after one iteration
+      } else {
+        // ---- the H line: H <- H (.) {L^T [U (.) sigma^-4] / L^T sigma^-2}^1/2, sigma^2 from
+        // the new L, frame by frame (this CTA's frames only)
+        for (int j = tid; j < Tl; j += kCThreads) {
+          float h[kCMaxN];
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n) h[n] = (n < N) ? sH[n * Tcp + j] : 0.f;
+          float a[M], b[M];
+#pragma unroll
+          for (int m2 = 0; m2 < M; ++m2) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int n = 0; n < kCMaxN; ++n)
+              if (n < N) s2 = fmaf(sL[m2 * N + n], h[n], s2);
+            const float rs = fast_rcp(s2);
+            b[m2] = rs;
+            a[m2] = sU[m2 * Tcp + j] * rs * rs;
+          }
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n) {
+            if (n < N) {
+              float num = 0.f, den = 0.f;
+#pragma unroll
+              for (int m2 = 0; m2 < M; ++m2) {
+                num = fmaf(sL[m2 * N + n], a[m2], num);
+                den = fmaf(sL[m2 * N + n], b[m2], den);
+              }
+              sH[n * Tcp + j] = (den > 0.f) ? h[n] * sqrtf(num * fast_rcp(den)) : h[n];
+            }
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
     } else {
       // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's
       // H update and its change of sigma^2
@@ -868,10 +917,12 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
     }
   }
 
-  // ---- write back: this CTA's frames of H; rank 0 the per-frequency parameters
+  // ---- write back: this CTA's frames of H (FastMNMF: H is an input); rank 0 the
+  // per-frequency parameters
   __syncthreads();
-  for (int n = 0; n < N; ++n)
-    for (int j = tid; j < Tl; j += kCThreads) vf[(size_t)n * T + t0 + j] = sH[n * Tcp + j];
+  if (!MN)
+    for (int n = 0; n < N; ++n)
+      for (int j = tid; j < Tl; j += kCThreads) vf[(size_t)n * T + t0 + j] = sH[n * Tcp + j];
   if (crank == 0) {
     for (int i = tid; i < M * N; i += kCThreads) lamf[i] = sL[i];
     for (int i = tid; i < M * M; i += kCThreads) {

@@ -48,6 +48,7 @@ struct MnmfArgs {
   int* err;
   int F, T, ll_stride;
   int iterate;         // 1: one iteration; 0: log-likelihood only
+  int N;               // sources (the cluster form takes N at run time)
 };
 
 template <int M, int N>
@@ -496,7 +497,7 @@ inline size_t mnmf_ab_smem(int M, int N, int K) {
 
 template <int M, int N>
 cudaError_t launch_mnmf_ab_mn(const float* lam, const float* tb, const float* va, const float* u, float* ab, int F,
-                              int K, int T, int* err, cudaStream_t s) {
+                              int /*N, a template parameter here*/, int K, int T, int* err, cudaStream_t s) {
   const size_t smem = mnmf_ab_smem(M, N, K);
   cudaError_t e = cudaFuncSetAttribute(fastmnmf_ab_kernel<M, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -507,8 +508,8 @@ cudaError_t launch_mnmf_ab_mn(const float* lam, const float* tb, const float* va
 
 struct MnmfOps {
   cudaError_t (*freq)(const MnmfArgs& a, cudaStream_t s);
-  cudaError_t (*ab)(const float* lam, const float* tb, const float* va, const float* u, float* ab, int F, int K,
-                    int T, int* err, cudaStream_t s);
+  cudaError_t (*ab)(const float* lam, const float* tb, const float* va, const float* u, float* ab, int F, int N,
+                    int K, int T, int* err, cudaStream_t s);
   int max_T;
 };
 
@@ -523,6 +524,10 @@ inline bool mnmf_ops(int M, int N, MnmfOps* o) {
     default: return false;
   }
 }
+// The per-frequency step on thread-block clusters (the FastFCA cluster kernel's MN form) for
+// shapes the frequency-resident kernel does not take: M <= 8, N <= 16, T as the cluster
+// kernel fits (fastmnmf_cluster.cuh; defined with the cluster kernels).
+bool mnmf_cluster_ops(int M, int N, int T, MnmfOps* o);
 
 template <int M, int N>
 cudaError_t launch_mnmf_freq(const MnmfArgs& a, cudaStream_t s) {

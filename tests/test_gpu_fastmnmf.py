@@ -58,6 +58,11 @@ def run_gpu(ff, x, N, K, st, iters):
     (3, 2, 16, 2, 96, 2),       # the most bases, several (n, k) chunks
     (4, 8, 3, 2, 2048, 1),      # the most frames one CTA holds
     (3, 2, 5, 1, 333, 3),       # one frequency: the v update sums over a single bin
+    (8, 12, 4, 2, 600, 2),      # thread-block clusters from here on
+    (3, 10, 3, 3, 400, 3),
+    (4, 6, 4, 2, 3000, 2),      # more frames than one frequency-resident CTA holds
+    (2, 1, 2, 2, 200, 3),       # one source
+    (6, 16, 2, 2, 150, 2),      # the most sources
 ])
 def test_fastmnmf_parity(ff, M, N, K, F, T, iters):
     """Log-likelihood after every iteration, per-frequency log-likelihood, images, W and the
@@ -128,7 +133,7 @@ def test_fastmnmf_full_size(ff):
 
 
 @pytest.mark.parametrize("M,N,K,T,why", [
-    (5, 3, 4, 100, "M"), (3, 9, 4, 100, "N"), (3, 3, 4, 2049, "T")])
+    (9, 3, 4, 100, "M"), (3, 17, 4, 100, "N"), (3, 3, 4, 40000, "T")])
 def test_fastmnmf_unsupported_shapes(ff, M, N, K, T, why):
     x = torch.zeros((2, T, M), dtype=torch.complex64, device="cuda")
     with pytest.raises(ff.FastFCAError, match="EUNSUPPORTED"):
