@@ -800,7 +800,8 @@ def main():
     out = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 bins, f64 IP+loglik",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "dtype_detail": "complex64 bins in FP32; the IP (Eq. 34-35) and the log-likelihood sums in FP64",
         "data": "synthetic (model-generated mixtures, seeded)", "config": config,
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
