@@ -297,7 +297,7 @@ def separation_roofline(w, sep_ms, peaks):
     ms = statistics.mean(sep_ms)
     hbm = peaks.get("hbm_gbs")
     gbs = bytes_ / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "winv_kernel + fastfca_mwf_kernel", "achieved": gbs,
+    return {"bound": "hbm", "kernel": "bst_to_winv_kernel + fastfca_mwf_kernel", "achieved": gbs,
             "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
             "bytes_per_bin": per_bin, "ms": ms,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}

@@ -86,7 +86,8 @@ typedef struct {
 
 typedef struct fastfca_ctx fastfca_ctx;
 
-/* Creates a context for the mixture x (complex64 [F][T][M], host or device) on `stream`
+/* Creates a context for the mixture x (complex64 [F][T][M], host or device; a device x is
+ * borrowed and must start on a 16-byte boundary, EINVAL otherwise) on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The parameters start at W = I,
  * lambda = 1 and v[n][t] = ||x_t||^2 / (M N) * u, u ~ U[0.5, 1.5) drawn from Philox4x32-10
  * keyed by cfg->seed with counter (f, n, t, 0x1d17) (FCA: R_n = I, h = the same v).  The random
@@ -204,8 +205,9 @@ const char* fastfca_version(void);
 typedef struct fastfca_batch fastfca_batch;
 
 /* Creates a batch of B FastFCA mixtures: cfgs[b] (model FASTFCA for IP+EM, Algorithm 1, or
- * FASTFCA_MM for IP+MM, Algorithm 2; mixtures may differ) and xs[b] (complex64
- * [F][T][M], host or device; device arrays are borrowed).  Parameters start as in
+ * FASTFCA_MM for IP+MM, Algorithm 2; mixtures may differ) and xs[b] (complex64 [F][T][M],
+ * host or device; device arrays are borrowed and must start on a 16-byte boundary, EINVAL
+ * otherwise).  Parameters start as in
  * fastfca_create.  The initial schedule is the finest bucketing with one grid share per
  * class; fastfca_batch_tune picks a measured one. */
 fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const void* const* xs, void* stream,
@@ -259,6 +261,7 @@ void fastfca_batch_destroy(fastfca_batch* batch);
  *   x    complex64  [F][T][M]  device     P    complex128 [F][M][M]  device
  *   lam  float32    [F][M][N]  device     v    float32    [F][N][T]  device
  *   c    complex64  [F][T][N][M] device (output, caller-allocated)
+ * x and P must start on a 16-byte boundary (EINVAL otherwise).
  *   stream  cudaStream_t (NULL = legacy default stream)
  *
  * Returns EINVAL when F*M*M > FASTFCA_NOALLOC_MAX_FMM, a size is not positive, a pointer is

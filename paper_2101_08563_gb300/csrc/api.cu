@@ -313,6 +313,9 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
     if (e__ != cudaSuccess) return bail(cuda_fail(ctx, e__, what));  \
   } while (0)
   if (is_device_ptr(x)) {
+    // the kernels load frames as 16-byte vectors
+    if (reinterpret_cast<uintptr_t>(x) % 16 != 0)
+      return bail(fail(ctx, FASTFCA_EINVAL, "a device x must start on a 16-byte boundary"));
     ctx->x = static_cast<const float2*>(x);
   } else {
     CKC(cudaMalloc(&ctx->x_owned, sizeof(float2) * nx), "x alloc");

@@ -348,6 +348,10 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
     const fastfca_config& c = m.cfg;
     const size_t FT = (size_t)c.F * c.T;
     if (is_dev(xs[i])) {
+      if (reinterpret_cast<uintptr_t>(xs[i]) % 16 != 0) {       // frames are loaded as 16-byte vectors
+        bfail(b, FASTFCA_EINVAL, "mixture %d: a device x must start on a 16-byte boundary", i);
+        return bail(FASTFCA_EINVAL);
+      }
       m.x = static_cast<const float2*>(xs[i]);
     } else {
       BCKC(cudaMalloc(&m.x_owned, sizeof(float2) * FT * c.M), "x alloc");

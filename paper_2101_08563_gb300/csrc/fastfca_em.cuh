@@ -68,10 +68,6 @@ struct EmArgs {
   int F, T, n_iter, ll_stride;
   int N;                // sources (read by the cluster kernel; the others take N as a template)
   long long* clocks;    // phase timestamps of frequency 0 (only with FFCA_PHASE_CLOCKS)
-  // FastMNMF's per-frequency step on the cluster kernel (its MN flag): U (F x M x T) and the
-  // bases' update terms a, b (two planes F x N x T) written after the lambda update
-  float* mn_u;
-  float* mn_ab;
 };
 
 // Phase timestamps (clock64) of frequency 0, thread 0, for the first 8 iterations; compiled

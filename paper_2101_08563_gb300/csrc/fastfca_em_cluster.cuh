@@ -315,9 +315,19 @@ __device__ __forceinline__ void decode_entry(int e, int& a, int& b, int& kind) {
 // ------------------------------------------------------------------ the kernel
 // Grid: F * C CTAs of kCThreads threads in clusters of C (rank c of cluster f owns frames
 // [c Tc, ...) of frequency f); dynamic shared memory ClusterSmem<M>::bytes(N, Tc).
+// The cluster kernel's arguments: the FastFCA ones, and the FastMNMF outputs of the MN form
+// (U, F x M x T, and the bases' update terms a, b, two planes F x N x T; null otherwise).
+// They stay out of EmArgs, which the frequency-resident kernels take at their register cap.
+struct ClusterArgs {
+  EmArgs e;
+  float* mn_u;
+  float* mn_ab;
+};
+
 template <int M, bool MM = false, bool BL = false, bool MN = false>
-__global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs p) {
+__global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(ClusterArgs ca) {
   static_assert(!(MN && BL), "FastMNMF takes frames");
+  const EmArgs& p = ca.e;
   using SM = ClusterSmem<M>;
   constexpr int NE = SM::NE, V = SM::V, XV = SM::kXV;
   constexpr int EPL = (NE + 31) / 32;
@@ -783,7 +793,7 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
             r[m2] = fast_rcp(s2);
             const float u = sU[m2 * Tcp + j];
             e[m2] = u * r[m2] * r[m2];
-            p.mn_u[((size_t)f * M + m2) * T + t0 + j] = u;
+            ca.mn_u[((size_t)f * M + m2) * T + t0 + j] = u;
           }
           if (bad) atomicOr(p.err, kErrSigma);
 #pragma unroll
@@ -795,8 +805,8 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(EmArgs
                 a = fmaf(sL[m2 * N + n], e[m2], a);
                 b = fmaf(sL[m2 * N + n], r[m2], b);
               }
-              p.mn_ab[((size_t)f * N + n) * T + t0 + j] = a;
-              p.mn_ab[plane + ((size_t)f * N + n) * T + t0 + j] = b;
+              ca.mn_ab[((size_t)f * N + n) * T + t0 + j] = a;
+              ca.mn_ab[plane + ((size_t)f * N + n) * T + t0 + j] = b;
             }
           }
         }

@@ -32,10 +32,13 @@ __global__ void __launch_bounds__(32) winv_kernel(const double2* __restrict__ P,
 }
 
 constexpr int kMwfThreads = 128;
+constexpr int kMwfBatches = 2;        // frame batches of kMwfThreads per CTA
 
-// One thread per frame; grid (F, ceil(T / kMwfThreads)).  With piecewise-stationary parameters
-// (Sec. VI-B) frame t uses the powers of its block t / B.  The N x M images of a frame are
-// staged in shared memory so that each warp writes its frames' output as one contiguous span.
+// One thread per frame of each batch; grid (F, ceil(T / (kMwfThreads kMwfBatches))).  With
+// piecewise-stationary parameters (Sec. VI-B) frame t uses the powers of its block t / B.
+// The N x M images of a batch are staged in shared memory so that each warp writes its
+// frames' output as one contiguous span; a CTA runs kMwfBatches batches, so the parameter
+// prologue is paid once and one batch's stores overlap the next batch's arithmetic.
 template <int M, int N>
 __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
     const float2* __restrict__ x, const double2* __restrict__ P, const float2* __restrict__ WmH,
@@ -46,8 +49,6 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
   __shared__ float4 sOut[kMwfThreads * N * M / 2 + 1];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
-  const int t0 = blockIdx.y * kMwfThreads;
-  const int t = t0 + tid;
   for (int e = tid; e < M * M; e += kMwfThreads) {
     const int a = e / M, m = e - (e / M) * M;
     const double2 w = P[(size_t)f * M * M + e];
@@ -55,59 +56,75 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
     sWi[e] = WmH[(size_t)f * M * M + e];
   }
   for (int e = tid; e < M * N; e += kMwfThreads) sL[e] = lam[(size_t)f * M * N + e];
-  __syncthreads();
+  const int J = T / B;                 // v holds one column per block of B frames
   float2* out = reinterpret_cast<float2*>(sOut);
-  if (t < T) {
-    float2 xv[M];
+#pragma unroll 1
+  for (int bt = 0; bt < kMwfBatches; ++bt) {
+    const int t0 = (blockIdx.y * kMwfBatches + bt) * kMwfThreads;
+    if (t0 >= T) break;                                    // uniform over the CTA
+    const int t = t0 + tid;
+    __syncthreads();                   // parameters loaded; the previous batch's sOut consumed
+    if (t < T) {
+      float2 xv[M];
+      const float2* xt = x + ((size_t)f * T + t) * M;
+      if constexpr (M % 2 == 0) {
 #pragma unroll
-    for (int a = 0; a < M; ++a) xv[a] = x[((size_t)f * T + t) * M + a];
-    float2 y[M];
+        for (int a = 0; a < M; a += 2) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(xt + a));
+          xv[a] = make_float2(q.x, q.y);
+          xv[a + 1] = make_float2(q.z, q.w);
+        }
+      } else {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      float2 acc = make_float2(0.f, 0.f);
+        for (int a = 0; a < M; ++a) xv[a] = __ldg(xt + a);
+      }
+      float h[N];
 #pragma unroll
-      for (int a = 0; a < M; ++a) acc = cfmaf(sWc[m * M + a], xv[a], acc);
-      y[m] = acc;
-    }
-    float h[N];
-    const int J = T / B;                 // v holds one column per block of B frames
-#pragma unroll
-    for (int n = 0; n < N; ++n) h[n] = v[((size_t)f * N + n) * J + t / B];
-    float rs[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      float s2 = 0.f;
-#pragma unroll
-      for (int n = 0; n < N; ++n) s2 = fmaf(sL[m * N + n], h[n], s2);
-      rs[m] = 1.0f / s2;
-    }
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      float2 z[M];
+      for (int n = 0; n < N; ++n) h[n] = __ldg(v + ((size_t)f * N + n) * J + t / B);
+      float2 y[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        const float g = sL[m * N + n] * h[n] * rs[m];
-        z[m] = make_float2(g * y[m].x, g * y[m].y);
-      }
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc = cfmaf(sWi[a * M + m], z[m], acc);
-        out[(tid * N + n) * M + a] = acc;
+        for (int a = 0; a < M; ++a) acc = cfmaf(sWc[m * M + a], xv[a], acc);
+        y[m] = acc;
+      }
+      float rs[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float s2 = 0.f;
+#pragma unroll
+        for (int n = 0; n < N; ++n) s2 = fmaf(sL[m * N + n], h[n], s2);
+        rs[m] = 1.0f / s2;
+      }
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        float2 z[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float g = sL[m * N + n] * h[n] * rs[m];
+          z[m] = make_float2(g * y[m].x, g * y[m].y);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc = cfmaf(sWi[a * M + m], z[m], acc);
+          out[(tid * N + n) * M + a] = acc;
+        }
       }
     }
-  }
-  __syncthreads();
-  // contiguous write-out of the CTA's frames: (nt * N * M) complex64 values
-  const int nt = min(kMwfThreads, T - t0);
-  const int total = nt * N * M;                     // float2 count
-  float2* dst = c + ((size_t)f * T + t0) * N * M;
-  if (((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (total % 2 == 0)) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int i = tid; i < total / 2; i += kMwfThreads) d4[i] = sOut[i];
-  } else {
-    for (int i = tid; i < total; i += kMwfThreads) dst[i] = out[i];
+    __syncthreads();
+    // contiguous write-out of the batch's frames: (nt * N * M) complex64 values
+    const int nt = min(kMwfThreads, T - t0);
+    const int total = nt * N * M;                     // float2 count
+    float2* dst = c + ((size_t)f * T + t0) * N * M;
+    if (((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (total % 2 == 0)) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      for (int i = tid; i < total / 2; i += kMwfThreads) d4[i] = sOut[i];
+    } else {
+      for (int i = tid; i < total; i += kMwfThreads) dst[i] = out[i];
+    }
   }
 }
 

@@ -27,8 +27,7 @@ cudaError_t launch_mnmf_cluster(const MnmfArgs& m, cudaStream_t s) {
   a.ll_stride = m.ll_stride;
   a.N = m.N;
   a.clocks = nullptr;
-  a.mn_u = m.u;
-  a.mn_ab = m.ab;
+  ClusterArgs ca{a, m.u, m.ab};
   int C = 0;
   size_t smem = 0;
   if (!cluster_shape<M>(a.T, a.N, &C, &smem)) return cudaErrorInvalidConfiguration;
@@ -47,7 +46,7 @@ cudaError_t launch_mnmf_cluster(const MnmfArgs& m, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, true, false, true>, a);
+  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, true, false, true>, ca);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ template <int M, int N>
 cudaError_t launch_mwf(const float2* x, const double2* P, const float2* WmH, const float* lam,
                        const float* v, float2* c, int F, int T, int /*N*/, int B, cudaStream_t s) {
   if (B < 1 || T % B != 0) return cudaErrorInvalidValue;
-  dim3 grid(F, (T + kMwfThreads - 1) / kMwfThreads);
+  dim3 grid(F, (T + kMwfThreads * kMwfBatches - 1) / (kMwfThreads * kMwfBatches));
   fastfca_mwf_kernel<M, N><<<grid, kMwfThreads, 0, s>>>(x, P, WmH, lam, v, c, F, T, B);
   return cudaGetLastError();
 }
@@ -161,7 +161,8 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM, BL>, a);
+  ClusterArgs ca{a, nullptr, nullptr};
+  e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM, BL>, ca);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

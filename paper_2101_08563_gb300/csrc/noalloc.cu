@@ -64,6 +64,8 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
   if (!x || !P || !lam || !v || !c) return noalloc_fail(FASTFCA_EINVAL, "x, P, lam, v and c are required");
   if (!device_pointer(x) || !device_pointer(P) || !device_pointer(lam) || !device_pointer(v) || !device_pointer(c))
     return noalloc_fail(FASTFCA_EINVAL, "x, P, lam, v and c must be device pointers");
+  if (reinterpret_cast<uintptr_t>(x) % 16 != 0 || reinterpret_cast<uintptr_t>(P) % 16 != 0)
+    return noalloc_fail(FASTFCA_EINVAL, "x and P must start on a 16-byte boundary");
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

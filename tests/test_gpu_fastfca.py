@@ -350,3 +350,17 @@ def test_block_input_errors(ff):
     P, lam, v = sep.get_params()
     assert v.shape == (4, 3, 30) and np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
     sep.close()
+
+
+def test_misaligned_device_mixture_is_rejected(ff):
+    """The kernels load frames as 16-byte vectors: a borrowed device x that starts mid-vector
+    is refused at creation, not faulted on."""
+    F, T, M = 2, 64, 2
+    buf = torch.zeros(F * T * M + 1, dtype=torch.complex64, device="cuda")
+    x = buf[1:].view(F, T, M)                           # 8 bytes past a 16-byte boundary
+    assert x.data_ptr() % 16 == 8
+    with pytest.raises(ff.FastFCAError, match="EINVAL"):
+        ff.Separator(x, 3)
+    xs = [x]
+    with pytest.raises(ff.FastFCAError, match="EINVAL"):
+        ff.Batch(xs, [3])
