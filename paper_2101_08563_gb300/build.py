@@ -4,12 +4,15 @@
 
 Translation units compile in parallel, one -gencode (sm_103a), then link into a shared
 library next to this file.  A rebuild happens only when a source or header is newer than
-the library.
+the library.  ptxas's per-kernel resource report (registers, spills, stack) is kept in
+_build/ptxas_report.json.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import json
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -20,6 +23,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libfastfca.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
+REPORT_PATH = os.path.join(BUILD_DIR, "ptxas_report.json")
 
 SOURCES = ["fastfca_m4_hi.cu", "fastfca_m4.cu", "fastfca_m3.cu", "fastfca_m2.cu", "api.cu", "fca_ops.cu", "noalloc.cu", "batch.cu",
            "fastmnmf_m2.cu", "fastmnmf_m3.cu", "fastmnmf_m4.cu", "fastmnmf_common.cu",
@@ -51,6 +55,27 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
+def parse_ptxas(text: str) -> dict:
+    """{mangled kernel name: {"registers", "spill_stores", "spill_loads", "stack"}} from the
+    output of ptxas -v."""
+    out, cur = {}, None
+    for line in text.splitlines():
+        m = re.search(r"Compiling entry function '(\S+)'", line)
+        if m:
+            cur = m.group(1)
+            out[cur] = {"registers": None, "spill_stores": 0, "spill_loads": 0, "stack": 0}
+            continue
+        if cur is None:
+            continue
+        m = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m:
+            out[cur]["stack"], out[cur]["spill_stores"], out[cur]["spill_loads"] = (int(g) for g in m.groups())
+        m = re.search(r"Used (\d+) registers", line)
+        if m:
+            out[cur]["registers"] = int(m.group(1))
+    return out
+
+
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     """Compile every translation unit for sm_103a and link libfastfca.so; returns its path."""
     if not force and up_to_date():
@@ -60,19 +85,23 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
+        cmd = [nvcc, "-Xptxas=-v", *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):
             sys.stderr.write(r.stdout + r.stderr)
-        return obj
+        return obj, parse_ptxas(r.stdout + r.stderr)
 
     jobs = jobs or min(len(SOURCES), os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+        results = list(ex.map(compile_one, SOURCES))
+    objs = [o for o, _ in results]
+    report = {}
+    for _, rep in results:
+        report.update(rep)
+    with open(REPORT_PATH, "w") as f:
+        json.dump(report, f, indent=0, sort_keys=True)
     tmp = LIB_PATH + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
