@@ -126,7 +126,8 @@ fastfca_status fastfca_get_params(fastfca_ctx* ctx, void* P, float* lam, float* 
  * updates of lambda, t and v in that order (the rules Algorithm 2 gives for L and H, applied to
  * each factor; sigma^2 recomputed before each); the v update sums over all frequencies.
  * cfg->model must be FASTFCA_MODEL_FASTMNMF; K is the number of bases per source, 1..16;
- * M 2..4, N 2..8, T <= 2048, F*K <= 36864.  x as for fastfca_create.  The default start is W = I,
+ * the shapes fastfca_create takes (M 2..8, N 1..16, T as the kernels fit), F*K <= 36864.
+ * x as for fastfca_create.  The default start is W = I,
  * lambda = 1, t_ikn = (mean_j p_ij / K) u, v_jkn = (mean_i p_ij / mean p) u', p_ij =
  * ||x_ij||^2 / (M N), u and u' ~ U[0.5, 1.5) from Philox4x32-10 keyed by cfg->seed.
  * fastfca_iterate, fastfca_loglik (Eq. 53 negated, with -M T ln(pi) per frequency),
