@@ -78,8 +78,8 @@ typedef enum {
 typedef struct {
   int32_t F;      /* frequency bins, >= 1 */
   int32_t T;      /* frames, >= 1 (FastFCA: up to what eight CTAs' shared memory holds, ~11k at M=8, N=12) */
-  int32_t M;      /* microphones: FastFCA 2..8, FCA 2..4 */
-  int32_t N;      /* sources: FastFCA 1..16, FCA 2..8 */
+  int32_t M;      /* microphones: FastFCA and FastMNMF 2..8, FCA 2..4 */
+  int32_t N;      /* sources: FastFCA and FastMNMF 1..16, FCA 2..8 */
   int32_t model;  /* fastfca_model */
   int32_t seed;   /* seed of the default initial v (Philox4x32-10); any value */
 } fastfca_config;
