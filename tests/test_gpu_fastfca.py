@@ -364,3 +364,21 @@ def test_misaligned_device_mixture_is_rejected(ff):
     xs = [x]
     with pytest.raises(ff.FastFCAError, match="EINVAL"):
         ff.Batch(xs, [3])
+
+
+@pytest.mark.parametrize("model,M,N,T", [("fastfca", 4, 6, 1250), ("fastfca", 8, 12, 1000), ("fastfca", 2, 3, 250)])
+def test_long_run_stays_finite_and_monotone(ff, model, M, N, T):
+    """500 IP+EM iterations (Algorithm 1 never lowers the likelihood: IP and each EM step are
+    ascent steps): every iteration's log-likelihood finite and non-decreasing within FP32
+    rounding, across both kernels (the M = 8 case runs on clusters)."""
+    mix = synth.generate_mixture(M, N, 6, T, 8, seed=900 + M, array="circular" if M >= 5 else "linear",
+                                 spacing=0.05 if M >= 5 else 0.03)
+    init = synth.random_init(mix.x, N, seed=900 + M)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N, model=model)
+    sep.set_params(init.P, init.lam, init.v)
+    ll = np.concatenate([sep.iterate(100) for _ in range(5)])
+    c = sep.separate()
+    sep.close()
+    assert np.all(np.isfinite(ll))
+    assert np.all(np.diff(ll) >= -2e-6 * np.abs(ll[1:])), np.min(np.diff(ll) / np.abs(ll[1:]))
+    assert np.all(np.isfinite(c)) and rel(c.sum(axis=2), mix.x) < 1e-5
