@@ -37,10 +37,22 @@
  * parameter copies) belong to the caller.
  *
  * Errors: every call returns a fastfca_status.  No C++ exception crosses the ABI.  A
- * FASTFCA_ECUDA status is sticky (later calls on the context return it); a FASTFCA_ENUMERIC
- * status is cleared by fastfca_set_params.  fastfca_last_error gives a one-line message.
- * Numerical trouble found by a kernel (a non-positive sigma^2, a non-positive-definite Q_m)
- * is recorded on the device and reported by the next call that synchronises.
+ * FASTFCA_ECUDA status is sticky (later calls on the context return it).  A FASTFCA_ENUMERIC
+ * status stays until fastfca_set_params (or set_params_fca / set_params_mnmf) replaces the
+ * parameters: meanwhile fastfca_iterate, fastfca_loglik and fastfca_separate return it
+ * without launching, and the get_params calls still work.  fastfca_last_error gives a
+ * one-line message.  Numerical trouble found by a kernel (a non-finite or non-positive
+ * sigma^2, a Q_m that is not numerically positive definite, a singular W) is recorded on the
+ * device and reported by the next call that synchronises.
+ *
+ * Input that makes the model degenerate: a non-finite x (NaN or Inf) gives FASTFCA_ENUMERIC
+ * within the first iterations.  An x_ft that is exactly zero (digital silence) has no
+ * maximum-likelihood variance, since sigma^2 -> 0 raises the likelihood without bound.  IP+EM
+ * and FCA by EM shrink that bin's power geometrically and stay finite for many iterations.
+ * IP+MM and FCA by MM set it to exactly zero in their first update, and FastMNMF does the
+ * same for a frame that is zero at every frequency (its v is shared across frequencies); all
+ * three then report FASTFCA_ENUMERIC in the next iteration.  Drop such frames or add dither at
+ * the noise floor.
  *
  * Threads: a context may be used by one host thread at a time.
  */
@@ -194,6 +206,16 @@ void fastfca_destroy(fastfca_ctx* ctx);
 /* Library version string. */
 const char* fastfca_version(void);
 
+/* Fault injection for the error paths, decided on the host (nothing reaches the GPU).  After
+ * n further device allocations by the library succeed, the next one fails as an out of memory
+ * would: the call that made it returns FASTFCA_ENOMEM and frees what it had allocated, and a
+ * context or batch it was called on stays usable.  One-shot; n < 0 disarms.  Process-wide. */
+void fastfca_debug_fail_alloc(int64_t n);
+
+/* Device allocations the library holds now, over all contexts, batches and networks of the
+ * process (with fastfca_debug_fail_alloc: a failed call leaves this count where it was). */
+int64_t fastfca_debug_live_allocs(void);
+
 /* ------------------------------------------------------------------------------------------
  * Batches: many independent mixtures (mixed M, N, T) iterated together in one CUDA-graph
  * launch.  Each (mixture, frequency) pair is one work item run by one CTA with the same code
@@ -221,11 +243,15 @@ fastfca_status fastfca_batch_set_params(fastfca_batch* batch, int32_t b, const v
 /* Copies mixture b's parameters out (host or device; NULL skips).  Synchronises. */
 fastfca_status fastfca_batch_get_params(fastfca_batch* batch, int32_t b, void* P, float* lam, float* v);
 
-/* Runs n_iter IP+EM iterations (Algorithm 1) on every frequency of every mixture with one
- * graph launch (the graph is captured on first use of each n_iter and reused).  Optional host
- * outputs: ll_per_mixture[b] = sum_f l_f after the last iteration; seconds_per_mixture[b] =
- * the span between the first start and the last end of mixture b's items inside the launch
- * (%globaltimer).  With either output the call synchronises; otherwise it is asynchronous. */
+/* Runs n_iter iterations (IP+EM, Algorithm 1, or IP+MM, Algorithm 2, as each mixture's
+ * config.model says) on every frequency of every mixture with one graph launch (the graph is
+ * captured on first use of each n_iter and reused).  Optional host outputs: ll_per_mixture[b]
+ * = sum_f l_f after the last iteration; seconds_per_mixture[b] = the span between the first
+ * start and the last end of mixture b's items inside the launch (%globaltimer).  With either
+ * output the call synchronises; otherwise it is asynchronous.  Mixtures are independent: on
+ * FASTFCA_ENUMERIC the outputs are still filled, ll_per_mixture[b] is non-finite for each
+ * mixture that failed, and the others' results are valid.  A failed mixture keeps reporting
+ * ENUMERIC until fastfca_batch_set_params replaces its parameters. */
 fastfca_status fastfca_batch_iterate(fastfca_batch* batch, int32_t n_iter, double* ll_per_mixture,
                                      double* seconds_per_mixture);
 

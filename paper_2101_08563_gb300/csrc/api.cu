@@ -3,6 +3,7 @@
 // the kernels; this file only moves data and launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -10,10 +11,12 @@
 #include <vector>
 
 #include "../../include/fastfca.h"
+#include "alloc.h"
 #include "fca.cuh"
 #include "fastmnmf.cuh"
 #include "init.cuh"
 #include "launch.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -26,6 +29,48 @@ thread_local char g_create_error[512] = "";
 
 namespace ffca {
 void set_thread_error(const char* msg) { snprintf(g_create_error, sizeof g_create_error, "%s", msg); }
+
+std::atomic<long long> g_fail_countdown{-1};   // allocations left before the injected failure
+std::atomic<long long> g_live_allocs{0};
+
+namespace {
+// True for the one allocation the armed countdown selects (and disarms it).
+bool injected_failure() {
+  long long c = g_fail_countdown.load();
+  while (c >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_allocs.fetch_sub(1);
+}
+
+void dev_free_async(void* p, cudaStream_t s) {
+  if (!p) return;
+  cudaFreeAsync(p, s);
+  g_live_allocs.fetch_sub(1);
+}
 }  // namespace ffca
 
 struct fastfca_ctx {
@@ -132,6 +177,17 @@ fastfca_status check_ready(fastfca_ctx* c) {
   return FASTFCA_OK;
 }
 
+// check_ready for the calls that run the model: after a numerical failure the parameters
+// may hold NaN or Inf, so no kernel starts from them until set_params replaces them.
+fastfca_status check_params_usable(fastfca_ctx* c) {
+  fastfca_status st = check_ready(c);
+  if (st) return st;
+  if (c->sticky == FASTFCA_ENUMERIC)
+    return fail(c, FASTFCA_ENUMERIC,
+                "the parameters are unusable after a numerical failure; set_params replaces them");
+  return FASTFCA_OK;
+}
+
 // Reads and clears the device status word; maps set bits to ENUMERIC.
 fastfca_status collect_device_status(fastfca_ctx* c) {
   int bits = 0;
@@ -193,37 +249,37 @@ __global__ void init_fca_params_kernel(double2* __restrict__ R, int F, int N, in
 }
 
 void free_all(fastfca_ctx* c) {
-  cudaFree(c->x_owned);
-  cudaFree(c->xh);
-  cudaFree(c->P);
-  cudaFree(c->lam);
-  cudaFree(c->v);
-  cudaFree(c->winv);
-  cudaFree(c->Bst);
-  cudaFree(c->detst);
-  cudaFree(c->tb);
-  cudaFree(c->va);
-  cudaFree(c->ab);
-  cudaFree(c->ubuf);
-  cudaFree(c->mscratch);
-  cudaFree(c->R);
-  cudaFree(c->h);
+  ffca::dev_free(c->x_owned);
+  ffca::dev_free(c->xh);
+  ffca::dev_free(c->P);
+  ffca::dev_free(c->lam);
+  ffca::dev_free(c->v);
+  ffca::dev_free(c->winv);
+  ffca::dev_free(c->Bst);
+  ffca::dev_free(c->detst);
+  ffca::dev_free(c->tb);
+  ffca::dev_free(c->va);
+  ffca::dev_free(c->ab);
+  ffca::dev_free(c->ubuf);
+  ffca::dev_free(c->mscratch);
+  ffca::dev_free(c->R);
+  ffca::dev_free(c->h);
   ffca::fca_work_free(&c->fca);
-  cudaFree(c->ll_hist);
-  cudaFree(c->ll_last);
-  cudaFree(c->ll_sum);
-  cudaFree(c->err);
+  ffca::dev_free(c->ll_hist);
+  ffca::dev_free(c->ll_last);
+  ffca::dev_free(c->ll_sum);
+  ffca::dev_free(c->err);
 }
 
 fastfca_status ensure_ll_capacity(fastfca_ctx* c, int n) {
   if (n <= c->ll_cap) return FASTFCA_OK;
-  cudaFree(c->ll_hist);
-  cudaFree(c->ll_sum);
+  ffca::dev_free(c->ll_hist);
+  ffca::dev_free(c->ll_sum);
   c->ll_hist = nullptr;
   c->ll_sum = nullptr;
   c->ll_cap = 0;
-  CK(c, cudaMalloc(&c->ll_hist, sizeof(double) * (size_t)c->cfg.F * n), "ll history alloc");
-  CK(c, cudaMalloc(&c->ll_sum, sizeof(double) * n), "ll sum alloc");
+  CK(c, ffca::dev_malloc(&c->ll_hist, sizeof(double) * (size_t)c->cfg.F * n), "ll history alloc");
+  CK(c, ffca::dev_malloc(&c->ll_sum, sizeof(double) * n), "ll sum alloc");
   c->ll_cap = n;
   return FASTFCA_OK;
 }
@@ -235,6 +291,10 @@ extern "C" {
 const char* fastfca_version(void) { return "fastfca-gb300 0.1 (sm_103a)"; }
 
 const char* fastfca_last_error(const fastfca_ctx* ctx) { return ctx ? ctx->msg : g_create_error; }
+
+void fastfca_debug_fail_alloc(int64_t n) { ffca::g_fail_countdown.store(n < 0 ? -1 : (long long)n); }
+
+int64_t fastfca_debug_live_allocs(void) { return ffca::g_live_allocs.load(); }
 
 static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const void* x, void* stream,
                                   fastfca_ctx** out) {
@@ -318,39 +378,39 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
       return bail(fail(ctx, FASTFCA_EINVAL, "a device x must start on a 16-byte boundary"));
     ctx->x = static_cast<const float2*>(x);
   } else {
-    CKC(cudaMalloc(&ctx->x_owned, sizeof(float2) * nx), "x alloc");
+    CKC(ffca::dev_malloc(&ctx->x_owned, sizeof(float2) * nx), "x alloc");
     CKC(cudaMemcpyAsync(ctx->x_owned, x, sizeof(float2) * nx, cudaMemcpyHostToDevice, ctx->stream), "x upload");
     ctx->x = ctx->x_owned;
   }
-  CKC(cudaMalloc(&ctx->err, sizeof(int)), "status alloc");
+  CKC(ffca::dev_malloc(&ctx->err, sizeof(int)), "status alloc");
   CKC(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "status clear");
-  CKC(cudaMalloc(&ctx->ll_last, sizeof(double) * c.F), "ll alloc");
+  CKC(ffca::dev_malloc(&ctx->ll_last, sizeof(double) * c.F), "ll alloc");
   const int threads = 256;
   if (mnmf) {
-    CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "W alloc");
-    CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
-    CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "h alloc");
-    CKC(cudaMalloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
-    CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
-    CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
-    CKC(cudaMalloc(&ctx->tb, sizeof(float) * (size_t)c.F * c.N * K), "t alloc");
-    CKC(cudaMalloc(&ctx->va, sizeof(float) * (size_t)c.N * K * c.T), "v alloc");
-    CKC(cudaMalloc(&ctx->ab, sizeof(float) * 2 * FT(c) * c.N), "update terms alloc");
-    CKC(cudaMalloc(&ctx->ubuf, sizeof(float) * FT(c) * c.M), "U alloc");
-    CKC(cudaMalloc(&ctx->mscratch, sizeof(float) * ((size_t)c.F + c.T + 1)), "scratch alloc");
+    CKC(ffca::dev_malloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "W alloc");
+    CKC(ffca::dev_malloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    CKC(ffca::dev_malloc(&ctx->v, sizeof(float) * FT(c) * c.N), "h alloc");
+    CKC(ffca::dev_malloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    CKC(ffca::dev_malloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    CKC(ffca::dev_malloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    CKC(ffca::dev_malloc(&ctx->tb, sizeof(float) * (size_t)c.F * c.N * K), "t alloc");
+    CKC(ffca::dev_malloc(&ctx->va, sizeof(float) * (size_t)c.N * K * c.T), "v alloc");
+    CKC(ffca::dev_malloc(&ctx->ab, sizeof(float) * 2 * FT(c) * c.N), "update terms alloc");
+    CKC(ffca::dev_malloc(&ctx->ubuf, sizeof(float) * FT(c) * c.M), "U alloc");
+    CKC(ffca::dev_malloc(&ctx->mscratch, sizeof(float) * ((size_t)c.F + c.T + 1)), "scratch alloc");
     CKC(ffca::launch_mnmf_default(ctx->x, ctx->P, ctx->lam, ctx->tb, ctx->va, ctx->mscratch, c.F, c.T, c.M, c.N, K,
                                   (uint32_t)c.seed, ctx->stream),
         "init launch");
   } else if (fastfca_family(c.model)) {
-    CKC(cudaMalloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
-    CKC(cudaMalloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
-    CKC(cudaMalloc(&ctx->v, sizeof(float) * FT(c) * c.N), "v alloc");
-    CKC(cudaMalloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
-    CKC(cudaMalloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
-    CKC(cudaMalloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    CKC(ffca::dev_malloc(&ctx->P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
+    CKC(ffca::dev_malloc(&ctx->lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    CKC(ffca::dev_malloc(&ctx->v, sizeof(float) * FT(c) * c.N), "v alloc");
+    CKC(ffca::dev_malloc(&ctx->winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    CKC(ffca::dev_malloc(&ctx->Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    CKC(ffca::dev_malloc(&ctx->detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
     const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
     if (B > 1) {
-      CKC(cudaMalloc(&ctx->xh, sizeof(float) * FT(c) * c.M * c.M), "block statistics alloc");
+      CKC(ffca::dev_malloc(&ctx->xh, sizeof(float) * FT(c) * c.M * c.M), "block statistics alloc");
       CKC(ctx->ops.block_stats(ctx->x, ctx->xh, c.F, c.T, B, ctx->stream), "block statistics launch");
       default_params_blocks_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
           ctx->xh, ctx->P, ctx->lam, ctx->v, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
@@ -360,23 +420,25 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
     }
     CKC(cudaGetLastError(), "init launch");
   } else {
-    CKC(cudaMalloc(&ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M), "R alloc");
-    CKC(cudaMalloc(&ctx->h, sizeof(float) * FT(c) * c.N), "h alloc");
+    CKC(ffca::dev_malloc(&ctx->R, sizeof(double2) * (size_t)c.F * c.N * c.M * c.M), "R alloc");
+    CKC(ffca::dev_malloc(&ctx->h, sizeof(float) * FT(c) * c.N), "h alloc");
     // FastFCA's initial v is also FCA's initial h
     double2* Ptmp = nullptr;
     float* lamtmp = nullptr;
-    CKC(cudaMalloc(&Ptmp, sizeof(double2) * (size_t)c.F * c.M * c.M), "tmp alloc");
-    CKC(cudaMalloc(&lamtmp, sizeof(float) * (size_t)c.F * c.M * c.N), "tmp alloc");
-    const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
-    ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        ctx->x, Ptmp, lamtmp, ctx->h, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
-    const size_t nr = (size_t)c.F * c.N * c.M * c.M;
-    init_fca_params_kernel<<<(unsigned)((nr + threads - 1) / threads), threads, 0, ctx->stream>>>(ctx->R, c.F, c.N, c.M);
-    cudaError_t e = cudaGetLastError();
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(Ptmp);
-    cudaFree(lamtmp);
-    CKC(e, "init launch");
+    cudaError_t e = ffca::dev_malloc(&Ptmp, sizeof(double2) * (size_t)c.F * c.M * c.M);
+    if (e == cudaSuccess) e = ffca::dev_malloc(&lamtmp, sizeof(float) * (size_t)c.F * c.M * c.N);
+    if (e == cudaSuccess) {
+      const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
+      ffca::default_params_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+          ctx->x, Ptmp, lamtmp, ctx->h, c.F, c.T, c.M, c.N, (uint32_t)c.seed);
+      const size_t nr = (size_t)c.F * c.N * c.M * c.M;
+      init_fca_params_kernel<<<(unsigned)((nr + threads - 1) / threads), threads, 0, ctx->stream>>>(ctx->R, c.F, c.N, c.M);
+      e = cudaGetLastError();
+      cudaStreamSynchronize(ctx->stream);
+    }
+    ffca::dev_free(Ptmp);     // both temporaries, whichever step failed
+    ffca::dev_free(lamtmp);
+    CKC(e, "FCA start");
     CKC(ffca::fca_work_alloc(&ctx->fca, c.F, c.T, c.M, c.N), "FCA workspace alloc");
   }
   CKC(cudaStreamSynchronize(ctx->stream), "create synchronize");
@@ -386,16 +448,19 @@ static fastfca_status create_impl(const fastfca_config* cfg, int B, int K, const
 }
 
 fastfca_status fastfca_create(const fastfca_config* cfg, const void* x, void* stream, fastfca_ctx** out) {
+  FFCA_TRACE("fastfca_create");
   return create_impl(cfg, 1, 0, x, stream, out);
 }
 
 fastfca_status fastfca_create_blocks(const fastfca_config* cfg, int32_t B, const void* x, void* stream,
                                      fastfca_ctx** out) {
+  FFCA_TRACE("fastfca_create_blocks");
   return create_impl(cfg, B, 0, x, stream, out);
 }
 
 fastfca_status fastfca_create_mnmf(const fastfca_config* cfg, int32_t K, const void* x, void* stream,
                                    fastfca_ctx** out) {
+  FFCA_TRACE("fastfca_create_mnmf");
   if (K < 1) {
     if (out) *out = nullptr;
     return fail(nullptr, FASTFCA_EINVAL, "K=%d bases per source is outside 1..%d", K, ffca::kMnmfMaxK);
@@ -532,7 +597,8 @@ fastfca_status fastfca_get_params_fca(fastfca_ctx* ctx, void* R, float* h) {
 }
 
 fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_iter) {
-  fastfca_status st = check_ready(ctx);
+  FFCA_TRACE("fastfca_iterate");
+  fastfca_status st = check_params_usable(ctx);
   if (st) return st;
   if (n_iter < 1) return fail(ctx, FASTFCA_EINVAL, "n_iter must be >= 1 (got %d)", n_iter);
   const fastfca_config& c = ctx->cfg;
@@ -606,7 +672,8 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
 }
 
 fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per_f) {
-  fastfca_status st = check_ready(ctx);
+  FFCA_TRACE("fastfca_loglik");
+  fastfca_status st = check_params_usable(ctx);
   if (st) return st;
   const fastfca_config& c = ctx->cfg;
   if (c.model == FASTFCA_MODEL_FASTMNMF) {
@@ -656,7 +723,8 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
 }
 
 fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
-  fastfca_status st = check_ready(ctx);
+  FFCA_TRACE("fastfca_separate");
+  fastfca_status st = check_params_usable(ctx);
   if (st) return st;
   if (!c_out) return fail(ctx, FASTFCA_EINVAL, "c is required");
   const fastfca_config& c = ctx->cfg;
@@ -665,7 +733,7 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   float2* dst = static_cast<float2*>(c_out);
   float2* tmp = nullptr;
   if (!dev) {
-    CK(ctx, cudaMallocAsync(&tmp, bytes, ctx->stream), "c staging alloc");
+    CK(ctx, ffca::dev_malloc_async(&tmp, bytes, ctx->stream), "c staging alloc");
     dst = tmp;
   }
   cudaError_t e = cudaSuccess;
@@ -688,25 +756,26 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
     e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
   }
   if (e != cudaSuccess) {
-    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (tmp) ffca::dev_free_async(tmp, ctx->stream);
     return cuda_fail(ctx, e, "separate launch");
   }
   if (!dev) {
     // stream-ordered download and release of the staging buffer: no synchronisation here,
     // kernel status is collected by the next synchronising call
     e = cudaMemcpyAsync(c_out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-    cudaFreeAsync(tmp, ctx->stream);
+    ffca::dev_free_async(tmp, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "c download");
   }
   return FASTFCA_OK;
 }
 
 fastfca_status fastfca_set_mixture(fastfca_ctx* ctx, const void* x) {
+  FFCA_TRACE("fastfca_set_mixture");
   fastfca_status st = check_ready(ctx);
   if (st) return st;
   if (!x) return fail(ctx, FASTFCA_EINVAL, "x is required");
   const size_t bytes = sizeof(float2) * (size_t)ctx->cfg.F * ctx->Tf * ctx->cfg.M;
-  if (!ctx->x_owned) CK(ctx, cudaMalloc(&ctx->x_owned, bytes), "x alloc");
+  if (!ctx->x_owned) CK(ctx, ffca::dev_malloc(&ctx->x_owned, bytes), "x alloc");
   CK(ctx, cudaMemcpyAsync(ctx->x_owned, x, bytes, cudaMemcpyDefault, ctx->stream), "x upload");
   ctx->x = ctx->x_owned;
   if (ctx->B > 1)

@@ -21,8 +21,10 @@
 #include <vector>
 
 #include "../../include/fastfca.h"
+#include "alloc.h"
 #include "init.cuh"
 #include "launch.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -110,6 +112,14 @@ fastfca_status bfail(fastfca_batch* b, fastfca_status st, const char* fmt, ...) 
     }                                                                                  \
   } while (0)
 
+// The status BCK would return for e, without returning: for paths that must clean up.
+fastfca_status bcheck(fastfca_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FASTFCA_OK;
+  cudaGetLastError();
+  return bfail(b, e == cudaErrorMemoryAllocation ? FASTFCA_ENOMEM : FASTFCA_ECUDA, "%s: %s", what,
+               cudaGetErrorString(e));
+}
+
 bool is_dev(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -138,8 +148,8 @@ void free_graphs(fastfca_batch* b) {
 
 void free_classes(fastfca_batch* b) {
   for (auto& c : b->classes) {
-    cudaFree(c.d_items);
-    cudaFree(c.d_counter);
+    ffca::dev_free(c.d_items);
+    ffca::dev_free(c.d_counter);
   }
   b->classes.clear();
 }
@@ -148,18 +158,18 @@ void free_batch(fastfca_batch* b) {
   free_graphs(b);
   free_classes(b);
   for (auto& m : b->mix) {
-    cudaFree(m.x_owned);
-    cudaFree(m.P);
-    cudaFree(m.lam);
-    cudaFree(m.v);
-    cudaFree(m.Bst);
-    cudaFree(m.detst);
-    cudaFree(m.ll_last);
-    cudaFree(m.flags);
-    cudaFree(m.winv);
+    ffca::dev_free(m.x_owned);
+    ffca::dev_free(m.P);
+    ffca::dev_free(m.lam);
+    ffca::dev_free(m.v);
+    ffca::dev_free(m.Bst);
+    ffca::dev_free(m.detst);
+    ffca::dev_free(m.ll_last);
+    ffca::dev_free(m.flags);
+    ffca::dev_free(m.winv);
   }
-  cudaFree(b->d_stamps);
-  cudaFree(b->d_err);
+  ffca::dev_free(b->d_stamps);
+  ffca::dev_free(b->d_err);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -170,7 +180,7 @@ double item_cost(const ffca::EmItem& it, int M, int N) { return (double)it.T * (
 
 // Builds the classes of a schedule: bucket the items, order each class longest first, size
 // each class's persistent grid by its share of the work and the occupancy of its kernel.
-fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
+fastfca_status build_classes_once(fastfca_batch* b, int scheme, double grid_factor) {
   free_graphs(b);
   free_classes(b);
   std::map<std::pair<int, int>, int> group_max_T;
@@ -218,10 +228,10 @@ fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
     std::vector<ffca::EmItem> h;
     h.reserve(c.items.size());
     for (size_t id : c.items) h.push_back(b->items[id]);
-    BCK(b, cudaMalloc(&c.d_items, sizeof(ffca::EmItem) * h.size()), "batch item alloc");
+    BCK(b, ffca::dev_malloc(&c.d_items, sizeof(ffca::EmItem) * h.size()), "batch item alloc");
     BCK(b, cudaMemcpyAsync(c.d_items, h.data(), sizeof(ffca::EmItem) * h.size(), cudaMemcpyHostToDevice, b->stream),
         "batch item upload");
-    BCK(b, cudaMalloc(&c.d_counter, sizeof(int)), "batch counter alloc");
+    BCK(b, ffca::dev_malloc(&c.d_counter, sizeof(int)), "batch counter alloc");
   }
   while (b->side.size() < b->classes.size()) {
     cudaStream_t s;
@@ -236,6 +246,26 @@ fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor) {
   b->grid_factor = grid_factor;
   BCK(b, cudaStreamSynchronize(b->stream), "batch schedule upload");
   return FASTFCA_OK;
+}
+
+// Builds the schedule (scheme, grid_factor).  On failure the schedule (fallback_scheme,
+// fallback_factor) is rebuilt when fallback_scheme >= 0; if that fails too, or there is none,
+// the batch is left with no classes and fastfca_batch_iterate refuses it.  The first
+// failure's status and message are returned.
+fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor, int fallback_scheme,
+                             double fallback_factor) {
+  const fastfca_status st = build_classes_once(b, scheme, grid_factor);
+  if (st == FASTFCA_OK) return st;
+  char msg[sizeof b->msg];
+  snprintf(msg, sizeof msg, "%s", b->msg);
+  free_graphs(b);
+  free_classes(b);
+  if (fallback_scheme >= 0 && build_classes_once(b, fallback_scheme, fallback_factor) != FASTFCA_OK) {
+    free_graphs(b);
+    free_classes(b);
+  }
+  snprintf(b->msg, sizeof b->msg, "%s", msg);
+  return st;
 }
 
 // Enqueues every class launch: fork from `origin` onto side streams, join back onto it.
@@ -296,6 +326,7 @@ extern "C" {
 
 fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const void* const* xs, void* stream,
                                     fastfca_batch** out) {
+  FFCA_TRACE("fastfca_batch_create");
   if (!out) return bfail(nullptr, FASTFCA_EINVAL, "out is NULL");
   *out = nullptr;
   if (B < 1 || !cfgs || !xs) return bfail(nullptr, FASTFCA_EINVAL, "B >= 1, cfgs and xs are required");
@@ -338,9 +369,9 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
       return bail(e__ == cudaErrorMemoryAllocation ? FASTFCA_ENOMEM : FASTFCA_ECUDA); \
     }                                                     \
   } while (0)
-  BCKC(cudaMalloc(&b->d_stamps, sizeof(unsigned long long) * 2 * n_items), "stamps alloc");
+  BCKC(ffca::dev_malloc(&b->d_stamps, sizeof(unsigned long long) * 2 * n_items), "stamps alloc");
   BCKC(cudaMemsetAsync(b->d_stamps, 0, sizeof(unsigned long long) * 2 * n_items, b->stream), "stamps clear");
-  BCKC(cudaMalloc(&b->d_err, sizeof(int)), "status alloc");
+  BCKC(ffca::dev_malloc(&b->d_err, sizeof(int)), "status alloc");
   BCKC(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "status clear");
   b->items.resize(n_items);
   for (int i = 0; i < B; ++i) {
@@ -354,18 +385,18 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
       }
       m.x = static_cast<const float2*>(xs[i]);
     } else {
-      BCKC(cudaMalloc(&m.x_owned, sizeof(float2) * FT * c.M), "x alloc");
+      BCKC(ffca::dev_malloc(&m.x_owned, sizeof(float2) * FT * c.M), "x alloc");
       BCKC(cudaMemcpyAsync(m.x_owned, xs[i], sizeof(float2) * FT * c.M, cudaMemcpyHostToDevice, b->stream), "x upload");
       m.x = m.x_owned;
     }
-    BCKC(cudaMalloc(&m.P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
-    BCKC(cudaMalloc(&m.lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
-    BCKC(cudaMalloc(&m.v, sizeof(float) * FT * c.N), "v alloc");
-    BCKC(cudaMalloc(&m.Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
-    BCKC(cudaMalloc(&m.detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
-    BCKC(cudaMalloc(&m.ll_last, sizeof(double) * (size_t)c.F), "ll alloc");
-    BCKC(cudaMalloc(&m.flags, sizeof(int) * (size_t)c.F), "flag alloc");
-    BCKC(cudaMalloc(&m.winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
+    BCKC(ffca::dev_malloc(&m.P, sizeof(double2) * (size_t)c.F * c.M * c.M), "P alloc");
+    BCKC(ffca::dev_malloc(&m.lam, sizeof(float) * (size_t)c.F * c.M * c.N), "lam alloc");
+    BCKC(ffca::dev_malloc(&m.v, sizeof(float) * FT * c.N), "v alloc");
+    BCKC(ffca::dev_malloc(&m.Bst, sizeof(double2) * (size_t)c.F * c.M * c.M), "B alloc");
+    BCKC(ffca::dev_malloc(&m.detst, sizeof(double) * 2 * (size_t)c.F), "det alloc");
+    BCKC(ffca::dev_malloc(&m.ll_last, sizeof(double) * (size_t)c.F), "ll alloc");
+    BCKC(ffca::dev_malloc(&m.flags, sizeof(int) * (size_t)c.F), "flag alloc");
+    BCKC(ffca::dev_malloc(&m.winv, sizeof(float2) * (size_t)c.F * c.M * c.M), "winv alloc");
     BCKC(cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "flag clear");
     const size_t n = ffca::default_params_elems(c.F, c.T, c.M, c.N);
     ffca::default_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(m.x, m.P, m.lam, m.v, c.F, c.T,
@@ -391,7 +422,7 @@ fastfca_status fastfca_batch_create(int32_t B, const fastfca_config* cfgs, const
   }
   BCKC(cudaStreamSynchronize(b->stream), "create synchronize");
 #undef BCKC
-  st = build_classes(b, kFine, 1.0);
+  st = build_classes(b, kFine, 1.0, -1, 0.0);
   if (st != FASTFCA_OK) return bail(st);
   *out = b;
   return FASTFCA_OK;
@@ -434,16 +465,21 @@ fastfca_status fastfca_batch_get_params(fastfca_batch* b, int32_t i, void* P, fl
 
 fastfca_status fastfca_batch_iterate(fastfca_batch* b, int32_t n_iter, double* ll_per_mixture,
                                      double* seconds_per_mixture) {
+  FFCA_TRACE("fastfca_batch_iterate");
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
+  if (b->classes.empty())
+    return bfail(b, FASTFCA_EINVAL, "the batch has no schedule (building one failed); call fastfca_batch_schedule");
   cudaGraphExec_t exec = nullptr;
   fastfca_status st = graph_for(b, n_iter, &exec);
   if (st) return st;
   BCK(b, cudaGraphLaunch(exec, b->stream), "graph launch");
   if (!ll_per_mixture && !seconds_per_mixture) return FASTFCA_OK;
-  st = check_err(b);
-  if (st) return st;
+  // ENUMERIC still fills the outputs: mixtures are independent, the failed ones read
+  // non-finite there and the others are valid.
+  const fastfca_status num = check_err(b);
+  if (num && num != FASTFCA_ENUMERIC) return num;
   if (ll_per_mixture) {
     for (size_t i = 0; i < b->mix.size(); ++i) {
       const Mix& m = b->mix[i];
@@ -468,48 +504,58 @@ fastfca_status fastfca_batch_iterate(fastfca_batch* b, int32_t n_iter, double* l
       seconds_per_mixture[i] = hi > lo ? (double)(hi - lo) * 1e-9 : 0.0;
     }
   }
-  return FASTFCA_OK;
+  return num;
 }
 
 fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* chosen_scheme, double* chosen_factor) {
+  FFCA_TRACE("fastfca_batch_tune");
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
-  // snapshot the parameters: the probes iterate on them
-  struct Saved { double2* P; float* lam; float* v; };
+  const int orig_scheme = b->classes.empty() ? -1 : b->scheme;
+  const double orig_factor = b->grid_factor;
+  // snapshot the parameters: the probes iterate on them.  Every exit below frees the
+  // snapshot and the events, and puts the parameters back once the snapshot is complete.
+  struct Saved { double2* P = nullptr; float* lam = nullptr; float* v = nullptr; };
   std::vector<Saved> saved(b->mix.size());
-  for (size_t i = 0; i < b->mix.size(); ++i) {
-    Mix& m = b->mix[i];
-    const fastfca_config& c = m.cfg;
-    BCK(b, cudaMalloc(&saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M), "tune snapshot");
-    BCK(b, cudaMalloc(&saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N), "tune snapshot");
-    BCK(b, cudaMalloc(&saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N), "tune snapshot");
-    BCK(b, cudaMemcpyAsync(saved[i].P, m.P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "snap");
-    BCK(b, cudaMemcpyAsync(saved[i].lam, m.lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "snap");
-    BCK(b, cudaMemcpyAsync(saved[i].v, m.v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "snap");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fastfca_status st = FASTFCA_OK;
+  bool snapped = false;
+  for (size_t i = 0; i < b->mix.size() && !st; ++i) {
+    const fastfca_config& c = b->mix[i].cfg;
+    st = bcheck(b, ffca::dev_malloc(&saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M), "tune snapshot");
+    if (!st) st = bcheck(b, ffca::dev_malloc(&saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N), "tune snapshot");
+    if (!st) st = bcheck(b, ffca::dev_malloc(&saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N), "tune snapshot");
   }
+  for (size_t i = 0; i < b->mix.size() && !st; ++i) {
+    const Mix& m = b->mix[i];
+    const fastfca_config& c = m.cfg;
+    st = bcheck(b, cudaMemcpyAsync(saved[i].P, m.P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "snapshot");
+    if (!st) st = bcheck(b, cudaMemcpyAsync(saved[i].lam, m.lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "snapshot");
+    if (!st) st = bcheck(b, cudaMemcpyAsync(saved[i].v, m.v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "snapshot");
+  }
+  snapped = !st;
   auto restore = [&]() -> fastfca_status {
-    for (size_t i = 0; i < b->mix.size(); ++i) {
+    fastfca_status r = FASTFCA_OK;
+    for (size_t i = 0; i < b->mix.size() && !r; ++i) {
       Mix& m = b->mix[i];
       const fastfca_config& c = m.cfg;
-      BCK(b, cudaMemcpyAsync(m.P, saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "restore");
-      BCK(b, cudaMemcpyAsync(m.lam, saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
-      BCK(b, cudaMemcpyAsync(m.v, saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
-      BCK(b, cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "restore");
+      r = bcheck(b, cudaMemcpyAsync(m.P, saved[i].P, sizeof(double2) * (size_t)c.F * c.M * c.M, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      if (!r) r = bcheck(b, cudaMemcpyAsync(m.lam, saved[i].lam, sizeof(float) * (size_t)c.F * c.M * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      if (!r) r = bcheck(b, cudaMemcpyAsync(m.v, saved[i].v, sizeof(float) * (size_t)c.F * c.T * c.N, cudaMemcpyDeviceToDevice, b->stream), "restore");
+      if (!r) r = bcheck(b, cudaMemsetAsync(m.flags, 0, sizeof(int) * (size_t)c.F, b->stream), "restore");
     }
-    return FASTFCA_OK;
+    return r;
   };
+  if (!st) st = bcheck(b, cudaEventCreate(&e0), "tune event");
+  if (!st) st = bcheck(b, cudaEventCreate(&e1), "tune event");
   const double factors[] = {1.0, 2.0, 4.0};
   float best_ms = 1e30f;
   int best_scheme = kFine;
   double best_factor = 1.0;
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0), "tune event");
-  BCK(b, cudaEventCreate(&e1), "tune event");
-  fastfca_status st = FASTFCA_OK;
-  for (int scheme = 0; scheme < kNumSchemes && st == FASTFCA_OK; ++scheme) {
+  for (int scheme = 0; scheme < kNumSchemes && !st; ++scheme) {
     for (double fac : factors) {
-      st = build_classes(b, scheme, fac);
+      st = build_classes(b, scheme, fac, -1, 0.0);
       if (st) break;
       st = restore();
       if (st) break;
@@ -523,12 +569,28 @@ fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* cho
       if (ms < best_ms) { best_ms = ms; best_scheme = scheme; best_factor = fac; }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st == FASTFCA_OK) st = restore();
-  for (auto& s : saved) { cudaFree(s.P); cudaFree(s.lam); cudaFree(s.v); }
-  if (st) return st;
-  st = build_classes(b, best_scheme, best_factor);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (snapped) {
+    const fastfca_status r = restore();
+    if (!st) st = r;
+    if (!st) st = bcheck(b, cudaStreamSynchronize(b->stream), "restore synchronize");
+    else cudaStreamSynchronize(b->stream);     // the snapshot is read until here
+  }
+  for (auto& sv : saved) {
+    ffca::dev_free(sv.P);
+    ffca::dev_free(sv.lam);
+    ffca::dev_free(sv.v);
+  }
+  if (st) {
+    // back to the schedule the batch had before tuning (a failed probe may have replaced it)
+    char msg[sizeof b->msg];
+    snprintf(msg, sizeof msg, "%s", b->msg);
+    if (orig_scheme >= 0) build_classes(b, orig_scheme, orig_factor, -1, 0.0);
+    snprintf(b->msg, sizeof b->msg, "%s", msg);
+    return st;
+  }
+  st = build_classes(b, best_scheme, best_factor, orig_scheme, orig_factor);
   if (st) return st;
   if (chosen_scheme) *chosen_scheme = best_scheme;
   if (chosen_factor) *chosen_factor = best_factor;
@@ -536,12 +598,15 @@ fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* cho
 }
 
 fastfca_status fastfca_batch_schedule(fastfca_batch* b, int32_t scheme, double grid_factor) {
+  FFCA_TRACE("fastfca_batch_schedule");
   if (!b) return FASTFCA_EINVAL;
+  if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (scheme < 0 || scheme >= kNumSchemes || !(grid_factor > 0.0)) return bfail(b, FASTFCA_EINVAL, "bad schedule");
-  return build_classes(b, scheme, grid_factor);
+  return build_classes(b, scheme, grid_factor, b->classes.empty() ? -1 : b->scheme, b->grid_factor);
 }
 
 fastfca_status fastfca_batch_separate(fastfca_batch* b, int32_t i, void* c) {
+  FFCA_TRACE("fastfca_batch_separate");
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (i < 0 || i >= (int)b->mix.size() || !c) return bfail(b, FASTFCA_EINVAL, "bad mixture index or NULL c");

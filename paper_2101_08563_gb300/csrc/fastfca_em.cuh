@@ -207,6 +207,9 @@ __device__ void warp_inverse_pivot(const double2* src, double2* work, double2* d
     if (lane >= k && lane < M) {
       const double2 a = work[lane * C + k];
       mag = (float)(a.x * a.x + a.y * a.y);
+      // NaN compares false both ways: ranked as 0 so that the argmax is a total order, every
+      // lane agrees on piv and piv stays in [k, M); a NaN pivot is then flagged below.
+      if (!(mag >= 0.f)) mag = 0.f;
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {

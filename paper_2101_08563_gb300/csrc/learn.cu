@@ -14,8 +14,10 @@
 #include <vector>
 
 #include "../../include/fastfca.h"
+#include "alloc.h"
 #include "launch.cuh"
 #include "learn.cuh"
+#include "trace.h"
 
 using namespace ffca;
 using namespace ffca::learn;
@@ -756,6 +758,7 @@ extern "C" {
 
 fastfca_status fastfca_generate_mixtures(int32_t B, int32_t F, int32_t T, int32_t M, int32_t N, int32_t K,
                                          double spacing, uint64_t seed, void* x, void* stream) {
+  FFCA_TRACE("fastfca_generate_mixtures");
   if (B < 1 || F < 1 || T < 1 || M < 1 || M > kMaxM || N < 1 || N > kMaxN || K < 1 || !x)
     return nfail(nullptr, FASTFCA_EINVAL, "generate: sizes out of range (M <= %d, N <= %d)", kMaxM, kMaxN);
   const size_t n = (size_t)B * F * T;
@@ -768,6 +771,7 @@ fastfca_status fastfca_generate_mixtures(int32_t B, int32_t F, int32_t T, int32_
 
 fastfca_status fastfca_net_features(int32_t rows, int32_t F, int32_t T, int32_t M, const void* x, float* feats, float* q,
                                     void* stream) {
+  FFCA_TRACE("fastfca_net_features");
   if (rows < 1 || F < 1 || T < 1 || M < 1 || M > kMaxM || !x || !feats || !q)
     return nfail(nullptr, FASTFCA_EINVAL, "features: bad arguments (M <= %d)", kMaxM);
   features_kernel<<<rows, 128, 0, (cudaStream_t)stream>>>(F, T, M, static_cast<const float2*>(x), feats, q);
@@ -777,6 +781,7 @@ fastfca_status fastfca_net_features(int32_t rows, int32_t F, int32_t T, int32_t 
 
 fastfca_status fastfca_net_targets(int32_t rows, int32_t T, int32_t M, int32_t N, const void* P, const float* lam,
                                    const float* v, float* wt, float* lt, float* ht, void* stream) {
+  FFCA_TRACE("fastfca_net_targets");
   if (rows < 1 || T < 1 || M < 1 || M > kMaxM || N < 1 || N > kMaxN || !P || !lam || !v || !wt || !lt || !ht)
     return nfail(nullptr, FASTFCA_EINVAL, "targets: bad arguments");
   const size_t n = (size_t)rows * N * T;
@@ -820,17 +825,17 @@ fastfca_status fastfca_net_create(int32_t M, int32_t N, int32_t max_rows, int32_
   };
   cudaError_t e;
   const size_t act = sizeof(float) * (size_t)max_rows * kHidden;
-  if ((e = cudaMalloc(&n->params, sizeof(float) * c)) != cudaSuccess) return bail("params", e);
-  if ((e = cudaMalloc(&n->grads, sizeof(float) * c)) != cudaSuccess) return bail("grads", e);
-  if ((e = cudaMalloc(&n->adam_m, sizeof(float) * c)) != cudaSuccess) return bail("adam", e);
-  if ((e = cudaMalloc(&n->adam_v, sizeof(float) * c)) != cudaSuccess) return bail("adam", e);
+  if ((e = ffca::dev_malloc(&n->params, sizeof(float) * c)) != cudaSuccess) return bail("params", e);
+  if ((e = ffca::dev_malloc(&n->grads, sizeof(float) * c)) != cudaSuccess) return bail("grads", e);
+  if ((e = ffca::dev_malloc(&n->adam_m, sizeof(float) * c)) != cudaSuccess) return bail("adam", e);
+  if ((e = ffca::dev_malloc(&n->adam_v, sizeof(float) * c)) != cudaSuccess) return bail("adam", e);
   for (float** p : {&n->z1, &n->h1, &n->z2, &n->h2, &n->d2, &n->d1})
-    if ((e = cudaMalloc(p, act)) != cudaSuccess) return bail("activations", e);
-  if ((e = cudaMalloc(&n->o, sizeof(float) * (size_t)max_rows * kOutPad)) != cudaSuccess) return bail("out", e);
-  if ((e = cudaMalloc(&n->dout, sizeof(float) * (size_t)max_rows * kOutPad)) != cudaSuccess) return bail("dout", e);
-  if ((e = cudaMalloc(&n->dconv, sizeof(float) * (size_t)max_rows * (N * kConvK + N))) != cudaSuccess) return bail("dconv", e);
-  if ((e = cudaMalloc(&n->loss, sizeof(float) * (size_t)max_rows)) != cudaSuccess) return bail("loss", e);
-  if ((e = cudaMalloc(&n->scal, sizeof(float) * 4)) != cudaSuccess) return bail("scalar", e);
+    if ((e = ffca::dev_malloc(p, act)) != cudaSuccess) return bail("activations", e);
+  if ((e = ffca::dev_malloc(&n->o, sizeof(float) * (size_t)max_rows * kOutPad)) != cudaSuccess) return bail("out", e);
+  if ((e = ffca::dev_malloc(&n->dout, sizeof(float) * (size_t)max_rows * kOutPad)) != cudaSuccess) return bail("dout", e);
+  if ((e = ffca::dev_malloc(&n->dconv, sizeof(float) * (size_t)max_rows * (N * kConvK + N))) != cudaSuccess) return bail("dconv", e);
+  if ((e = ffca::dev_malloc(&n->loss, sizeof(float) * (size_t)max_rows)) != cudaSuccess) return bail("loss", e);
+  if ((e = ffca::dev_malloc(&n->scal, sizeof(float) * 4)) != cudaSuccess) return bail("scalar", e);
   cudaMemsetAsync(n->adam_m, 0, sizeof(float) * c, n->stream);
   cudaMemsetAsync(n->adam_v, 0, sizeof(float) * c, n->stream);
   cudaMemsetAsync(n->grads, 0, sizeof(float) * c, n->stream);
@@ -860,7 +865,7 @@ void fastfca_net_destroy(fastfca_net* n) {
   if (n->stream) cudaStreamSynchronize(n->stream);
   for (float* p : {n->params, n->grads, n->adam_m, n->adam_v, n->z1, n->h1, n->z2, n->h2, n->o, n->dout, n->d2, n->d1,
                    n->dconv, n->loss, n->scal})
-    cudaFree(p);
+    ffca::dev_free(p);
   delete n;
 }
 
@@ -883,6 +888,7 @@ fastfca_status fastfca_net_set_params(fastfca_net* n, const float* in) {
 }
 
 fastfca_status fastfca_net_forward(fastfca_net* n, int32_t rows, const float* feats, float* out) {
+  FFCA_TRACE("fastfca_net_forward");
   if (!n || !feats || !out || rows < 1 || rows > n->max_rows) return FASTFCA_EINVAL;
   fastfca_status st = net_forward(n, rows, feats);
   if (st) return st;
@@ -893,6 +899,7 @@ fastfca_status fastfca_net_forward(fastfca_net* n, int32_t rows, const float* fe
 
 fastfca_status fastfca_net_loss_grad(fastfca_net* n, int32_t rows, int32_t T, const float* feats, const float* q,
                                      const float* wt, const float* lt, const float* ht, double* loss, float* grads) {
+  FFCA_TRACE("fastfca_net_loss_grad");
   if (!n || !feats || !q || !wt || !lt || !ht) return FASTFCA_EINVAL;
   fastfca_status st = net_loss_grad(n, rows, T, feats, q, wt, lt, ht, loss);
   if (st) return st;
@@ -905,6 +912,7 @@ fastfca_status fastfca_net_loss_grad(fastfca_net* n, int32_t rows, int32_t T, co
 
 fastfca_status fastfca_net_train_step(fastfca_net* n, int32_t rows, int32_t T, const float* feats, const float* q,
                                       const float* wt, const float* lt, const float* ht, float lr, double* loss) {
+  FFCA_TRACE("fastfca_net_train_step");
   if (!n || !feats || !q || !wt || !lt || !ht || !(lr > 0.f)) return FASTFCA_EINVAL;
   fastfca_status st = net_loss_grad(n, rows, T, feats, q, wt, lt, ht, loss);
   if (st) return st;
@@ -919,6 +927,7 @@ fastfca_status fastfca_net_train_step(fastfca_net* n, int32_t rows, int32_t T, c
 
 fastfca_status fastfca_net_predict(fastfca_net* n, int32_t rows, int32_t T, const float* feats, const float* q, void* P,
                                    float* lam, float* v) {
+  FFCA_TRACE("fastfca_net_predict");
   if (!n || !feats || !q || !P || !lam || !v || rows < 1 || rows > n->max_rows || T < 1 || T > n->max_T)
     return FASTFCA_EINVAL;
   fastfca_status st = net_forward(n, rows, feats);

@@ -19,6 +19,7 @@
 
 #include "../../include/fastfca.h"
 #include "launch.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -51,6 +52,7 @@ bool device_pointer(const void* p) {
 extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t N,
                                                    const void* x, const void* P, const float* lam,
                                                    const float* v, void* c, void* stream) {
+  FFCA_TRACE("fastfca_separate_noalloc");
   if (F < 1 || T < 1 || M < 1 || N < 1) return noalloc_fail(FASTFCA_EINVAL, "F, T, M, N must be positive");
   ffca::FastOps ops{};
   if (!ffca::fast_ops(M, N, &ops) && !ffca::cluster_ops(M, N, T, &ops))

@@ -22,6 +22,7 @@ except Exception:  # pragma: no cover
     torch = None
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "EUNSUPPORTED"}
+STATUS_ENUMERIC = 4
 MODEL_FASTFCA = 0
 MODEL_FCA = 1
 MODEL_FASTFCA_MM = 2
@@ -48,6 +49,8 @@ _SIGNATURES = {
     "fastfca_last_error": (ctypes.c_char_p, [_P]),
     "fastfca_destroy": (None, [_P]),
     "fastfca_version": (ctypes.c_char_p, []),
+    "fastfca_debug_fail_alloc": (None, [ctypes.c_int64]),
+    "fastfca_debug_live_allocs": (ctypes.c_int64, []),
     "fastfca_separate_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 _P, _P, _P, _P, _P, _P]),
     "fastfca_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]),
@@ -325,6 +328,17 @@ class Separator:
         self._check(self.lib.fastfca_sync(self._h))
 
 
+def fail_allocation_after(n: int):
+    """Fault injection: after n more device allocations by the library succeed, the next one
+    fails as an out of memory would (one-shot; n < 0 disarms)."""
+    load().fastfca_debug_fail_alloc(int(n))
+
+
+def live_allocations() -> int:
+    """Device allocations the library holds now (all contexts, batches and networks)."""
+    return int(load().fastfca_debug_live_allocs())
+
+
 def abi_symbols_from_header(path: str | None = None):
     """Names of the functions declared in include/fastfca.h."""
     import re
@@ -410,8 +424,14 @@ class Batch:
             return None
         ll = np.empty(self.B, np.float64)
         sec = np.empty(self.B, np.float64)
-        self._check(self.lib.fastfca_batch_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p),
-                                                   sec.ctypes.data_as(ctypes.c_void_p)))
+        st = self.lib.fastfca_batch_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p),
+                                            sec.ctypes.data_as(ctypes.c_void_p))
+        if st == STATUS_ENUMERIC:
+            # the log-likelihoods are filled anyway: non-finite for the mixtures that failed
+            err = FastFCAError(st, self.lib.fastfca_batch_last_error(self._h).decode())
+            err.ll_per_mixture = ll
+            raise err
+        self._check(st)
         return ll, sec
 
     def tune(self, n_iter):

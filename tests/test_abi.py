@@ -55,3 +55,12 @@ def test_create_rejects_null_arguments_without_touching_the_gpu(lib):
 
 def test_config_struct_matches_header():
     assert ctypes.sizeof(fastfca.Config) == 24
+
+
+def test_allocation_fault_injection_is_host_state(lib):
+    """The allocation counters live on the host: nothing is held before any context exists,
+    and arming or disarming the injected failure touches no device."""
+    assert fastfca.live_allocations() == 0
+    fastfca.fail_allocation_after(3)
+    fastfca.fail_allocation_after(-1)          # disarmed again: later tests allocate normally
+    assert fastfca.live_allocations() == 0
