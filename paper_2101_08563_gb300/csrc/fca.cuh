@@ -87,14 +87,16 @@ __device__ __forceinline__ float herm_inverse_f32(float2 (&A)[M][M], bool& ok) {
 #pragma unroll
     for (int i = 0; i < M; ++i) {
       if (i == k) continue;
-      const float2 aik = A[i][k];
+      // a_ik / d first: it is O(1) whatever the matrix's scale, whereas a_ik a_kj would
+      // underflow for entries below ~1e-19 (a frame whose power is near zero)
+      const float2 g = make_float2(A[i][k].x * rd, A[i][k].y * rd);
 #pragma unroll
       for (int j = 0; j < M; ++j) {
         if (j == k) {
-          A[i][j] = make_float2(-aik.x * rd, -aik.y * rd);
+          A[i][j] = make_float2(-g.x, -g.y);
         } else {
-          const float2 pr = cmulf(aik, rowk[j]);
-          A[i][j] = make_float2(fmaf(-pr.x, rd, A[i][j].x), fmaf(-pr.y, rd, A[i][j].y));
+          const float2 pr = cmulf(g, rowk[j]);
+          A[i][j] = make_float2(A[i][j].x - pr.x, A[i][j].y - pr.y);
         }
       }
     }
@@ -583,7 +585,8 @@ __global__ void __launch_bounds__(kFcaMaxThreads) fca_em_kernel(FcaArgs p) {
             for (int b = 0; b < M; ++b) s = cfmaf(sRif[(n * M + a) * M + b], mu[b], s);
             q = fmaf(mu[a].x, s.x, fmaf(mu[a].y, s.y, q));
           }
-          const float hnew = (q + hn * (float)M - hn * hn * trB) * (1.0f / (float)M);
+          // h (h tr B), not h^2 tr B: h tr B is O(1) while h^2 underflows for h below ~1e-19
+          const float hnew = (q + hn * (float)M - hn * (hn * trB)) * (1.0f / (float)M);
           ok &= (hnew > 0.f) && (hnew < INFINITY);
           sh[n * Tp + t] = hnew;
           const float ih = 1.0f / hnew;
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(kFcaMaxThreads) fca_em_kernel(FcaArgs p) {
             float2 br = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < M; ++c) br = cfmaf(B[a][c], Rn[c][a], br);
-            const float psi = fmaf(mu[a].x, mu[a].x, mu[a].y * mu[a].y) + hn * Rn[a][a].x - hn * hn * br.x;
+            const float psi = fmaf(mu[a].x, mu[a].x, mu[a].y * mu[a].y) + hn * Rn[a][a].x - hn * (hn * br.x);
             acc[a] = fmaf(psi, ih, acc[a]);
           }
           e = M;
@@ -609,8 +612,8 @@ __global__ void __launch_bounds__(kFcaMaxThreads) fca_em_kernel(FcaArgs p) {
               // mu_a conj(mu_b)
               const float mre = fmaf(mu[a].x, mu[b].x, mu[a].y * mu[b].y);
               const float mim = fmaf(mu[a].y, mu[b].x, -mu[a].x * mu[b].y);
-              const float pre = mre + hn * Rn[a][b].x - hn * hn * br.x;
-              const float pim = mim + hn * Rn[a][b].y - hn * hn * br.y;
+              const float pre = mre + hn * Rn[a][b].x - hn * (hn * br.x);
+              const float pim = mim + hn * Rn[a][b].y - hn * (hn * br.y);
               acc[e] = fmaf(pre, ih, acc[e]);
               acc[e + 1] = fmaf(pim, ih, acc[e + 1]);
               e += 2;
