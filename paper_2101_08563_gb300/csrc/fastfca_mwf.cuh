@@ -129,16 +129,22 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
 }
 
 // Wide form of the filter for large bins (any M <= 8, runtime N <= kMwfWMaxN).  A CTA of
-// M x 32 threads takes kMwfWFrames frames.  Phase 1 (thread per (frame, m)) forms
+// M x 32 threads takes kMwfWBatches batches of kMwfWFrames frames, so that the parameter
+// prologue (W, W^{-H}, lambda) is paid once per 256 frames; one batch's stores overlap the
+// next batch's loads.  Per batch, phase 1 (thread per (frame, m)) forms
 // z_nm(t) = g_nm(t) y_m(t) for every source in shared memory.  Phase 2 gives thread
 // (task slot s, row a) = (tid / M, tid % M) the fixed row a of W^{-H}, held in registers, and
 // walks the tasks (frame, n) s, s + 32, ...: each output c_tn[a] = sum_m W^{-H}[a][m] z_nm(t)
 // reads only the M values of z of its task (shared by the M threads of the task), and
 // consecutive threads write consecutive complex values of the output span (coalesced).
-// Rows of sZ are padded to M + 1 values so that the tasks of a warp fall in distinct banks.
+// Rows of sZ are padded to M + 1 values so that the tasks of a warp fall in distinct banks;
+// sZ is dynamic shared memory of kMwfWFrames N (M + 1) complex values (mwf_wide_smem).
 // With blocks of B frames (Sec. VI-B) v has J = T / B columns and frame t takes column t / B.
 constexpr int kMwfWFrames = 32;
+constexpr int kMwfWBatches = 8;
 constexpr int kMwfWMaxN = 16;
+
+constexpr size_t mwf_wide_smem(int M, int N) { return sizeof(float2) * kMwfWFrames * N * (M + 1); }
 
 template <int M>
 __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
@@ -149,11 +155,9 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
   const int J = T / B;
   __shared__ float2 sWc[M * M];                                   // conj(W[a][m]) at [m*M + a]
   __shared__ float sL[M * kMwfWMaxN];
-  __shared__ float2 sZ[kMwfWFrames * kMwfWMaxN * (M + 1)];        // [(tl*N + n)][m], padded
+  extern __shared__ float2 sZ[];                                  // [(tl*N + n)][m], padded
   const int f = blockIdx.x, tid = threadIdx.x;
-  const int t0 = blockIdx.y * kMwfWFrames;
-  if (f >= F || t0 >= T || N > kMwfWMaxN) return;
-  const int nt = min(kMwfWFrames, T - t0);
+  if (f >= F || N > kMwfWMaxN) return;
   for (int e = tid; e < M * M; e += kThreads) {
     const int a = e / M, m = e - (e / M) * M;
     const double2 w = P[(size_t)f * M * M + e];
@@ -165,7 +169,12 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
   float2 wi[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) wi[m] = WmH[(size_t)f * M * M + a_row * M + m];
-  __syncthreads();
+#pragma unroll 1
+  for (int bt = 0; bt < kMwfWBatches; ++bt) {
+  const int t0 = (blockIdx.y * kMwfWBatches + bt) * kMwfWFrames;
+  if (t0 >= T) break;                                             // uniform over the CTA
+  const int nt = min(kMwfWFrames, T - t0);
+  __syncthreads();                     // parameters loaded; the previous batch's sZ consumed
   // phase 1: thread (tl, m) for tl < nt (32 frames x M rows = the CTA)
   {
     const int tl = tid / M, m = tid - (tid / M) * M;
@@ -204,6 +213,7 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
 #pragma unroll
     for (int m = 0; m < M; ++m) acc = cfmaf(wi[m], z[m], acc);
     dst[(size_t)task * M + a_row] = acc;
+  }
   }
 }
 

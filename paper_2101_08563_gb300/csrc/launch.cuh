@@ -170,8 +170,8 @@ template <int M>
 cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
                             float2* c, int F, int T, int N, int B, cudaStream_t s) {
   if (N < 1 || N > kMwfWMaxN || B < 1 || T % B != 0) return cudaErrorInvalidValue;
-  dim3 grid(F, (T + kMwfWFrames - 1) / kMwfWFrames);
-  fastfca_mwf_wide_kernel<M><<<grid, M * 32, 0, s>>>(x, P, WmH, lam, v, c, F, T, N, B);
+  dim3 grid(F, (T + kMwfWFrames * kMwfWBatches - 1) / (kMwfWFrames * kMwfWBatches));
+  fastfca_mwf_wide_kernel<M><<<grid, M * 32, mwf_wide_smem(M, N), s>>>(x, P, WmH, lam, v, c, F, T, N, B);
   return cudaGetLastError();
 }
 
