@@ -626,7 +626,7 @@ def run_gpu(args, rank, world, local_rank):
     }
 
 
-def run_profile_case(F, iters, workload="fca_cmp", model="fastfca"):
+def run_profile_case(F, iters, workload="fca_cmp", model="fastfca", separate=False):
     """A workload's first 8 frequencies tiled to F (so the launch has F frequencies of the
     workload's shape), two launches of the IP+EM kernel (model "fastfca_mm": IP+MM): 2
     iterations, then `iters`.
@@ -659,6 +659,10 @@ def run_profile_case(F, iters, workload="fca_cmp", model="fastfca"):
     sep.iterate(2, return_ll=False)
     sep.set_params(init.P, init.lam, init.v)
     sep.iterate(iters, return_ll=False)
+    if separate:                          # two separations into a device buffer
+        out = torch.empty((F, w.T, w.N, w.M), dtype=torch.complex64, device="cuda")
+        for _ in range(2):
+            sep.separate(out)
     torch.cuda.synchronize()
     sep.close()
     print("profile case done")
@@ -719,6 +723,8 @@ def main():
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
     ap.add_argument("--profile-F", type=int, default=608)
     ap.add_argument("--profile-iters", type=int, default=5)
+    ap.add_argument("--profile-separate", action="store_true",
+                    help="with --profile: end with two separations (the Wiener filter kernels)")
     ap.add_argument("--profile-model", default="fastfca", choices=["fastfca", "fastfca_mm"])
     ap.add_argument("--profile-workload", default="fca_cmp", choices=["fca_cmp", "large", "fastmnmf"])
     args = ap.parse_args()
@@ -735,7 +741,8 @@ def main():
               "l2": "flushed between steps (512 MiB write, untimed)"}
 
     if args.profile:
-        run_profile_case(args.profile_F, args.profile_iters, args.profile_workload, args.profile_model)
+        run_profile_case(args.profile_F, args.profile_iters, args.profile_workload, args.profile_model,
+                         args.profile_separate)
         return
 
     if args.impl == "reference":

@@ -130,21 +130,53 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
 
 // Wide form of the filter for large bins (any M <= 8, runtime N <= kMwfWMaxN).  A CTA of
 // M x 32 threads takes kMwfWBatches batches of kMwfWFrames frames, so that the parameter
-// prologue (W, W^{-H}, lambda) is paid once per 256 frames; one batch's stores overlap the
-// next batch's loads.  Per batch, phase 1 (thread per (frame, m)) forms
-// z_nm(t) = g_nm(t) y_m(t) for every source in shared memory.  Phase 2 gives thread
-// (task slot s, row a) = (tid / M, tid % M) the fixed row a of W^{-H}, held in registers, and
-// walks the tasks (frame, n) s, s + 32, ...: each output c_tn[a] = sum_m W^{-H}[a][m] z_nm(t)
-// reads only the M values of z of its task (shared by the M threads of the task), and
-// consecutive threads write consecutive complex values of the output span (coalesced).
-// Rows of sZ are padded to M + 1 values so that the tasks of a warp fall in distinct banks;
-// sZ is dynamic shared memory of kMwfWFrames N (M + 1) complex values (mwf_wide_smem).
+// prologue (W, W^{-H}, lambda) is paid once per 256 frames.  Per batch:
+//  0. the batch's x (contiguous) and h values (one column of v per frame or block) are
+//     staged in shared memory with coalesced loads, double-buffered: the next batch's loads
+//     are issued before this batch's phase 2 and stored after it;
+//  1. thread (frame, m) forms y_m = w_m^H x, sigma^2_m and z_nm = g_nm y_m for every
+//     source, g_nm = L[m,n] h_n / sigma^2_m, into shared memory;
+//  2. thread (task slot s, row a) = (tid / M, tid % M), holding row a of W^{-H} in registers,
+//     walks the tasks (frame, n) s, s + 32, ...: c_tn[a] = sum_m W^{-H}[a][m] z_nm, so that
+//     consecutive threads write consecutive complex values of the output span (coalesced).
+// Layout of z: one row of kMwfWRow(M) complex values per task (frame, n), at task * row, the
+// row even so that it starts on 16 bytes and phase 2 reads it as float4 pairs (one broadcast
+// per quarter-warp) with no division by N.  conj(W) rows are padded to M + 1 so that the M
+// threads of a frame read distinct banks.
 // With blocks of B frames (Sec. VI-B) v has J = T / B columns and frame t takes column t / B.
 constexpr int kMwfWFrames = 32;
 constexpr int kMwfWBatches = 8;
 constexpr int kMwfWMaxN = 16;
 
-constexpr size_t mwf_wide_smem(int M, int N) { return sizeof(float2) * kMwfWFrames * N * (M + 1); }
+__host__ __device__ constexpr int kMwfWRow(int M) { return (M + 2) & ~1; }
+constexpr size_t mwf_wide_smem(int M, int N) { return sizeof(float2) * kMwfWFrames * N * kMwfWRow(M); }
+
+// Staging of one batch (t0, nt frames) for the wide filter: thread tid loads x value tid and
+// h values tid + j M 32 of the N x kMwfWFrames block into registers (mwf_wide_load), and later
+// stores them to one of the two shared buffers (mwf_wide_store).
+template <int M, int HPER>
+__device__ __forceinline__ void mwf_wide_load(const float2* __restrict__ x, const float* __restrict__ v, int f,
+                                              int T, int N, int J, int B, int t0, int nt, int tid, float2& xr,
+                                              float (&hr)[HPER]) {
+  if (tid < nt * M) xr = __ldg(x + ((size_t)f * T + t0) * M + tid);
+#pragma unroll
+  for (int j = 0; j < HPER; ++j) {
+    const int i = tid + j * M * 32;
+    const int n = i / kMwfWFrames, tl = i - (i / kMwfWFrames) * kMwfWFrames;
+    hr[j] = (n < N && tl < nt) ? __ldg(v + ((size_t)f * N + n) * J + (t0 + tl) / B) : 0.f;
+  }
+}
+
+template <int M, int HPER>
+__device__ __forceinline__ void mwf_wide_store(float2* sXb, float* sHb, int N, int nt, int tid, float2 xr,
+                                               const float (&hr)[HPER]) {
+  if (tid < nt * M) sXb[tid] = xr;
+#pragma unroll
+  for (int j = 0; j < HPER; ++j) {
+    const int i = tid + j * M * 32;
+    if (i < N * kMwfWFrames) sHb[i] = hr[j];
+  }
+}
 
 template <int M>
 __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
@@ -152,68 +184,88 @@ __global__ void __launch_bounds__(M * 32) fastfca_mwf_wide_kernel(
     const float* __restrict__ lam, const float* __restrict__ v, float2* __restrict__ c, int F, int T, int N,
     int B) {
   constexpr int kThreads = M * 32;
+  constexpr int RS = kMwfWRow(M);
   const int J = T / B;
-  __shared__ float2 sWc[M * M];                                   // conj(W[a][m]) at [m*M + a]
+  __shared__ float2 sWc[M * (M + 1)];                             // conj(W[a][m]) at [m*(M+1) + a]
   __shared__ float sL[M * kMwfWMaxN];
-  extern __shared__ float2 sZ[];                                  // [(tl*N + n)][m], padded
+  __shared__ __align__(16) float2 sX[2][kMwfWFrames * M];         // a batch's x, frame-major
+  __shared__ float sH[2][kMwfWMaxN * kMwfWFrames];                // a batch's h_n, [n][tl]
+  extern __shared__ __align__(16) float2 sZ[];                    // [(tl*N + n)*RS + m]
   const int f = blockIdx.x, tid = threadIdx.x;
   if (f >= F || N > kMwfWMaxN) return;
   for (int e = tid; e < M * M; e += kThreads) {
     const int a = e / M, m = e - (e / M) * M;
     const double2 w = P[(size_t)f * M * M + e];
-    sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    sWc[m * (M + 1) + a] = make_float2((float)w.x, (float)-w.y);
   }
   for (int e = tid; e < M * N; e += kThreads) sL[e] = lam[(size_t)f * M * N + e];
-  // this thread's row of W^{-H}
+  // this thread's row of W^{-H} (phase 2) and (frame, m) (phase 1)
   const int a_row = tid % M, slot = tid / M;
   float2 wi[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) wi[m] = WmH[(size_t)f * M * M + a_row * M + m];
-#pragma unroll 1
-  for (int bt = 0; bt < kMwfWBatches; ++bt) {
-  const int t0 = (blockIdx.y * kMwfWBatches + bt) * kMwfWFrames;
-  if (t0 >= T) break;                                             // uniform over the CTA
-  const int nt = min(kMwfWFrames, T - t0);
-  __syncthreads();                     // parameters loaded; the previous batch's sZ consumed
-  // phase 1: thread (tl, m) for tl < nt (32 frames x M rows = the CTA)
+  const int tl1 = tid / M, m1 = tid - (tid / M) * M;
+  // staging of a batch: thread tid takes x value tid (kThreads = kMwfWFrames M of them) and h
+  // values tid + j kThreads of the N x kMwfWFrames block; loads go to registers first, so that
+  // the next batch's loads are in flight while this batch is computed
+  constexpr int kHPer = (kMwfWMaxN * kMwfWFrames + kThreads - 1) / kThreads;
+  float2 xr = make_float2(0.f, 0.f);
+  float hr[kHPer];
   {
-    const int tl = tid / M, m = tid - (tid / M) * M;
-    if (tl < nt) {
-      const int t = t0 + tl;
-      const int tb = t / B;
-      const float2* xt = x + ((size_t)f * T + t) * M;
-      float2 y = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xt[a], y);
-      float h[kMwfWMaxN];
-      float s2 = 0.f;
-#pragma unroll
-      for (int n = 0; n < kMwfWMaxN; ++n) {
-        const int nn = (n < N) ? n : 0;                  // index kept inside the arrays
-        const float hv = v[((size_t)f * N + nn) * J + tb], lv = sL[m * N + nn];
-        h[n] = (n < N) ? hv : 0.f;
-        s2 = fmaf((n < N) ? lv : 0.f, h[n], s2);
-      }
-      const float rs = 1.0f / s2;
-#pragma unroll
-      for (int n = 0; n < kMwfWMaxN; ++n)
-        if (n < N) {
-          const float g = sL[m * N + n] * h[n] * rs;
-          sZ[(tl * N + n) * (M + 1) + m] = make_float2(g * y.x, g * y.y);
-        }
+    const int t0 = blockIdx.y * kMwfWBatches * kMwfWFrames;
+    if (t0 < T) {
+      const int nt = min(kMwfWFrames, T - t0);
+      mwf_wide_load<M, kHPer>(x, v, f, T, N, J, B, t0, nt, tid, xr, hr);
+      mwf_wide_store<M, kHPer>(sX[0], sH[0], N, nt, tid, xr, hr);
     }
   }
-  __syncthreads();
-  // phase 2: outputs in memory order, task-major (task = tl*N + n), row a minor
-  const int tasks = nt * N;
-  float2* dst = c + ((size_t)f * T + t0) * N * M;
-  for (int task = slot; task < tasks; task += 32) {
-    const float2* z = sZ + task * (M + 1);
-    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int bt = 0; bt < kMwfWBatches; ++bt) {
+    const int t0 = (blockIdx.y * kMwfWBatches + bt) * kMwfWFrames;
+    if (t0 >= T) break;                                           // uniform over the CTA
+    const int nt = min(kMwfWFrames, T - t0);
+    const int buf = bt & 1;
+    const float2* sXb = sX[buf];
+    const float* sHb = sH[buf];
+    // parameters and this batch's inputs stored; the previous batch's sZ consumed
+    __syncthreads();
+    // 1. thread (tl1, m1): y, sigma^2, z for every source
+    if (tl1 < nt) {
+      float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < M; ++m) acc = cfmaf(wi[m], z[m], acc);
-    dst[(size_t)task * M + a_row] = acc;
-  }
+      for (int a = 0; a < M; ++a) y = cfmaf(sWc[m1 * (M + 1) + a], sXb[tl1 * M + a], y);
+      float s2 = 0.f;
+      for (int n = 0; n < N; ++n) s2 = fmaf(sL[m1 * N + n], sHb[n * kMwfWFrames + tl1], s2);
+      const float rs = 1.0f / s2;
+      float2* zt = sZ + tl1 * N * RS + m1;
+      for (int n = 0; n < N; ++n) {
+        const float g = sL[m1 * N + n] * sHb[n * kMwfWFrames + tl1] * rs;
+        zt[n * RS] = make_float2(g * y.x, g * y.y);
+      }
+    }
+    // the next batch's loads, in flight during the barrier and phase 2
+    const int t1 = t0 + kMwfWFrames;
+    const bool more = bt + 1 < kMwfWBatches && t1 < T;
+    if (more) mwf_wide_load<M, kHPer>(x, v, f, T, N, J, B, t1, min(kMwfWFrames, T - t1), tid, xr, hr);
+    __syncthreads();
+    // 2. outputs in memory order, task-major (task = tl*N + n), row a minor
+    const int tasks = nt * N;
+    float2* dst = c + ((size_t)f * T + t0) * N * M;
+    for (int task = slot; task < tasks; task += 32) {
+      const float4* z4 = reinterpret_cast<const float4*>(sZ + task * RS);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int mm = 0; mm < M / 2; ++mm) {
+        const float4 q = z4[mm];
+        acc = cfmaf(wi[2 * mm], make_float2(q.x, q.y), acc);
+        acc = cfmaf(wi[2 * mm + 1], make_float2(q.z, q.w), acc);
+      }
+      if constexpr (M % 2 == 1) acc = cfmaf(wi[M - 1], sZ[task * RS + M - 1], acc);
+      dst[(size_t)task * M + a_row] = acc;
+    }
+    // the other buffer was last read by the previous batch's phase 1, before this batch's
+    // first barrier; the next iteration's first barrier publishes these stores
+    if (more) mwf_wide_store<M, kHPer>(sX[buf ^ 1], sH[buf ^ 1], N, min(kMwfWFrames, T - t1), tid, xr, hr);
   }
 }
 

@@ -171,7 +171,11 @@ cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH
                             float2* c, int F, int T, int N, int B, cudaStream_t s) {
   if (N < 1 || N > kMwfWMaxN || B < 1 || T % B != 0) return cudaErrorInvalidValue;
   dim3 grid(F, (T + kMwfWFrames * kMwfWBatches - 1) / (kMwfWFrames * kMwfWBatches));
-  fastfca_mwf_wide_kernel<M><<<grid, M * 32, mwf_wide_smem(M, N), s>>>(x, P, WmH, lam, v, c, F, T, N, B);
+  const size_t smem = mwf_wide_smem(M, N);
+  cudaError_t e = cudaFuncSetAttribute(fastfca_mwf_wide_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  fastfca_mwf_wide_kernel<M><<<grid, M * 32, smem, s>>>(x, P, WmH, lam, v, c, F, T, N, B);
   return cudaGetLastError();
 }
 

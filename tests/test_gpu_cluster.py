@@ -68,6 +68,33 @@ def test_cluster_parity(ff, M, N, F, T, iters):
                  spacing=0.05 if M >= 5 else 0.03)
 
 
+def max_frames(ff, M, N):
+    """The largest T a context accepts for (M, N), found by bisection on creation (a T beyond
+    what eight CTAs hold is rejected with EUNSUPPORTED before any kernel runs)."""
+    def accepted(T):
+        try:
+            ff.Separator(torch.zeros((1, T, M), dtype=torch.complex64, device="cuda"), N).close()
+            return True
+        except ff.FastFCAError as e:
+            assert "EUNSUPPORTED" in str(e), str(e)
+            return False
+    lo, hi = 4000, 65536
+    assert accepted(lo) and not accepted(hi)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (mid, hi) if accepted(mid) else (lo, mid)
+    return lo
+
+
+@pytest.mark.parametrize("M,N", [(8, 16), (3, 4)])
+def test_cluster_parity_at_the_most_frames(ff, M, N):
+    """Parity at the largest T the cluster kernel takes for (M, N): the last CTA of the
+    eight is full or nearly so, and shared memory is at its carve-out."""
+    T = max_frames(ff, M, N)
+    check_parity(ff, M, N, 2, T, 2, array="circular" if M >= 5 else "linear",
+                 spacing=0.05 if M >= 5 else 0.03)
+
+
 def test_cluster_loglik_resume_and_monotone(ff):
     M, N, F, T = 8, 12, 2, 1500
     mix = synth.generate_mixture(M, N, F, T, 8, seed=4, array="circular", spacing=0.05)
