@@ -34,6 +34,11 @@ __global__ void __launch_bounds__(32) winv_kernel(const double2* __restrict__ P,
 constexpr int kMwfThreads = 128;
 constexpr int kMwfBatches = 2;        // frame batches of kMwfThreads per CTA
 
+// Stride of one frame's N x M images in the staging buffer, in complex values: N M rounded so
+// that it is 2 (mod 4).  Frames then start on 16 bytes when N M is even, and the 8-byte stores
+// of a half-warp (16 frames) meet at most 2 to a bank instead of 8 (N M = 24: 48 words apart).
+__host__ __device__ constexpr int mwf_frame_stride(int N, int M) { return (N * M) % 2 ? N * M : (N * M) % 4 ? N * M : N * M + 2; }
+
 // One thread per frame of each batch; grid (F, ceil(T / (kMwfThreads kMwfBatches))).  With
 // piecewise-stationary parameters (Sec. VI-B) frame t uses the powers of its block t / B.
 // The N x M images of a batch are staged in shared memory so that each warp writes its
@@ -46,7 +51,8 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
   __shared__ float2 sWc[M * M];       // conj(W[a][m]) at [m*M + a]
   __shared__ float2 sWi[M * M];       // W^{-H}[a][m] at [a*M + m]
   __shared__ float sL[M * N];
-  __shared__ float4 sOut[kMwfThreads * N * M / 2 + 1];
+  constexpr int FSn = mwf_frame_stride(N, M);
+  __shared__ float4 sOut[(kMwfThreads * FSn + 1) / 2];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
   for (int e = tid; e < M * M; e += kMwfThreads) {
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
           float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
           for (int m = 0; m < M; ++m) acc = cfmaf(sWi[a * M + m], z[m], acc);
-          out[(tid * N + n) * M + a] = acc;
+          out[tid * FSn + n * M + a] = acc;
         }
       }
     }
@@ -119,11 +125,20 @@ __global__ void __launch_bounds__(kMwfThreads) fastfca_mwf_kernel(
     const int nt = min(kMwfThreads, T - t0);
     const int total = nt * N * M;                     // float2 count
     float2* dst = c + ((size_t)f * T + t0) * N * M;
-    if (((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (total % 2 == 0)) {
-      float4* d4 = reinterpret_cast<float4*>(dst);
-      for (int i = tid; i < total / 2; i += kMwfThreads) d4[i] = sOut[i];
-    } else {
-      for (int i = tid; i < total; i += kMwfThreads) dst[i] = out[i];
+    if constexpr ((N * M) % 2 == 0) {
+      if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        constexpr int Q = N * M / 2;                  // float4 per frame
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int i = tid; i < total / 2; i += kMwfThreads) {
+          const int fr = i / Q;
+          d4[i] = sOut[fr * (FSn / 2) + (i - fr * Q)];
+        }
+        continue;
+      }
+    }
+    for (int i = tid; i < total; i += kMwfThreads) {
+      const int fr = i / (N * M);
+      dst[i] = out[fr * FSn + (i - fr * (N * M))];
     }
   }
 }
