@@ -231,13 +231,25 @@ __global__ void default_params_blocks_kernel(const float* __restrict__ xh, doubl
   }
 }
 
-__global__ void sum_over_f_kernel(const double* __restrict__ hist, int F, int stride, int n, double* __restrict__ out) {
-  // one thread per column (iteration), fixed summation order over f
-  const int it = blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= n) return;
+// out[it] = sum_f hist[f * stride + it] for it < n: one CTA of kSumThreads per column, each
+// thread summing f = tid, tid + kSumThreads, ... in order, then a fixed-shape tree over the
+// threads, so that the total is the same bits on every call.
+constexpr int kSumThreads = 256;
+
+__global__ void __launch_bounds__(kSumThreads) sum_over_f_kernel(const double* __restrict__ hist, int F, int stride,
+                                                                 int n, double* __restrict__ out) {
+  __shared__ double red[kSumThreads];
+  const int it = blockIdx.x, tid = threadIdx.x;
+  if (it >= n) return;                                  // uniform over the CTA
   double s = 0.0;
-  for (int f = 0; f < F; ++f) s += hist[(size_t)f * stride + it];
-  out[it] = s;
+  for (int f = tid; f < F; f += kSumThreads) s += hist[(size_t)f * stride + it];
+  red[tid] = s;
+#pragma unroll
+  for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+    __syncthreads();
+    if (tid < w) red[tid] += red[tid + w];
+  }
+  if (tid == 0) out[it] = red[0];
 }
 
 __global__ void init_fca_params_kernel(double2* __restrict__ R, int F, int N, int M) {
@@ -663,7 +675,7 @@ fastfca_status fastfca_iterate(fastfca_ctx* ctx, int32_t n_iter, double* ll_per_
     CK(ctx, launch(a, &ctx->fca, ctx->stream), "FCA EM/MM launch");
   }
   if (!ll_per_iter) return FASTFCA_OK;
-  sum_over_f_kernel<<<(n_iter + 127) / 128, 128, 0, ctx->stream>>>(ctx->ll_hist, c.F, n_iter, n_iter, ctx->ll_sum);
+  sum_over_f_kernel<<<n_iter, kSumThreads, 0, ctx->stream>>>(ctx->ll_hist, c.F, n_iter, n_iter, ctx->ll_sum);
   CK(ctx, cudaGetLastError(), "ll sum launch");
   // stream-ordered download; kernel status is collected by the next synchronising call
   CK(ctx, cudaMemcpyAsync(ll_per_iter, ctx->ll_sum, sizeof(double) * n_iter, cudaMemcpyDefault, ctx->stream),
@@ -714,7 +726,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
   if (ll_total) {
     st = ensure_ll_capacity(ctx, 1);
     if (st) return st;
-    sum_over_f_kernel<<<1, 32, 0, ctx->stream>>>(ctx->ll_last, c.F, 1, 1, ctx->ll_sum);
+    sum_over_f_kernel<<<1, kSumThreads, 0, ctx->stream>>>(ctx->ll_last, c.F, 1, 1, ctx->ll_sum);
     CK(ctx, cudaGetLastError(), "ll sum launch");
     CK(ctx, cudaMemcpyAsync(ll_total, ctx->ll_sum, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "ll download");
   }
