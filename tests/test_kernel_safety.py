@@ -1,7 +1,8 @@
-"""Source checks of the kernels' failure policy (CPU, no build needed): a kernel reports a
+"""Source checks of the library's failure policy (CPU, no build needed): a kernel reports a
 problem through the context's status word and returns; it never traps, never fails a device
 assert, and never waits without a bound.  These are the properties that keep a GPU usable
-for the next call after a numerical or configuration failure."""
+for the next call after a numerical or configuration failure.  Every device allocation goes
+through the counted allocator, which the fault-injection tests rely on."""
 import os
 import re
 
@@ -43,3 +44,18 @@ def test_every_open_ended_loop_is_bounded():
     assert re.search(r"if \(i >= n_items\) return;", loop[:400])
     spins = [m.group(0) for _, t in sources() for m in re.finditer(r"while \(!mbar_try_wait[^\n]*", strip_comments(t))]
     assert spins and all("kMbarSpinLimit" in s for s in spins)
+
+
+def test_device_allocations_go_through_the_counted_allocator():
+    """cudaMalloc and cudaMallocAsync appear only in dev_malloc_raw / dev_malloc_async_raw, so
+    the library's live-allocation count and its injected allocation failures see every
+    device allocation (the allocation-free separation is checked against that count)."""
+    calls = []
+    for name, text in sources():
+        code = strip_comments(text)
+        for m in re.finditer(r"\bcuda(Malloc|MallocAsync|MallocManaged|MallocPitch|Malloc3D)\s*\(", code):
+            head = code[:m.start()]
+            fn = re.findall(r"cudaError_t (\w+)\(", head)
+            calls.append((name, fn[-1] if fn else None, m.group(1)))
+    assert sorted(calls) == [("api.cu", "dev_malloc_async_raw", "MallocAsync"),
+                             ("api.cu", "dev_malloc_raw", "Malloc")], calls

@@ -4,8 +4,10 @@ Code that separates audio inside a real-time callback (or any section where an a
 call may block the thread or synchronise the device) cannot call cudaMalloc there.  The
 library gives such callers one entry point that takes every input and output from them and
 keeps its single intermediate in a fixed array compiled into the library.  This test calls it
-through the C ABI, twice in a row, and checks both outputs against the context-based
-fastfca_separate on the same parameters.  It lives in its own file, collected last.
+through the C ABI, twice in a row, with the library's next device allocation armed to fail
+(so any allocation inside the call would surface as an error), and checks both outputs
+against the context-based fastfca_separate on the same parameters.  It lives in its own
+file, collected last.
 """
 import ctypes
 
@@ -50,11 +52,18 @@ def test_noalloc_separation_matches_context_separation():
     vd = torch.from_numpy(v).cuda()
     c = torch.empty((F, T, N, M), dtype=torch.complex64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
+    live = fastfca.live_allocations()
     for call in range(2):
         c.fill_(float("nan"))
-        st = lib.fastfca_separate_noalloc(F, T, M, N, _p(xd), _p(Pd), _p(lamd), _p(vd), _p(c),
-                                          ctypes.c_void_p(stream))
+        # the next device allocation of the library would fail: this call must make none
+        fastfca.fail_allocation_after(0)
+        try:
+            st = lib.fastfca_separate_noalloc(F, T, M, N, _p(xd), _p(Pd), _p(lamd), _p(vd), _p(c),
+                                              ctypes.c_void_p(stream))
+        finally:
+            fastfca.fail_allocation_after(-1)
         assert st == 0, lib.fastfca_last_error(None)
+        assert fastfca.live_allocations() == live
         torch.cuda.synchronize()
         got = c.cpu().numpy()
         assert np.all(np.isfinite(got)), f"call {call}: output not fully written"
