@@ -755,8 +755,15 @@ __global__ void __launch_bounds__(128) fca_mwf_kernel(const float2* __restrict__
   }
 }
 
+// Threads per CTA: about two frames per thread, up to kFcaMaxThreads (512 x 128 registers is
+// the register file).  Shared memory (X^{-1} per frame) holds the kernel to one CTA per SM,
+// so the CTA takes as many warps as fit to hide latency; kFcaSlots frames per thread still
+// bound T.
 inline int fca_threads(int T) {
-  const int warps = (T + 32 * kFcaSlots - 1) / (32 * kFcaSlots);
+  const int need = (T + 32 * kFcaSlots - 1) / (32 * kFcaSlots);     // warps for kFcaSlots frames each
+  int warps = (T + 63) / 64;                                         // warps for two frames each
+  if (warps > kFcaMaxThreads / 32) warps = kFcaMaxThreads / 32;
+  if (warps < need) warps = need;
   return (warps < 1 ? 1 : warps) * 32;
 }
 
