@@ -1,0 +1,120 @@
+// Host-side check of the launch geometry the library computes, for every shape it accepts:
+// threads per CTA, frames per thread and the shared memory each kernel asks for, against the
+// GB300 limits (227 KB of dynamic shared memory per CTA, 48 KB of static, 1024 threads,
+// clusters of at most 8).  It includes the library's own launch headers and calls their
+// host functions; it makes no CUDA call, so it runs without a GPU.  Prints "ok" or the first
+// violation (and exits 1).
+#include <cstdio>
+#include <cstdlib>
+
+#include "../paper_2101_08563_gb300/csrc/fca.cuh"
+#include "../paper_2101_08563_gb300/csrc/launch.cuh"
+
+using namespace ffca;
+
+namespace {
+
+constexpr size_t kDynMax = 227 * 1024;
+constexpr size_t kStaticMax = 48 * 1024;
+int failures = 0;
+
+void fail(const char* what, int M, int N, int T, size_t value) {
+  if (failures++ < 10) std::printf("FAIL %s: M=%d N=%d T=%d value=%zu\n", what, M, N, T, value);
+}
+
+// frequency-resident IP+EM kernel: T <= kMaxThreads * kSlots
+template <int M, int N>
+void check_em() {
+  for (int T = 1; T <= kMaxThreads * kSlots; ++T) {
+    const int th = em_threads(T);
+    if (th % 32 || th > kMaxThreads || th * kSlots < T) fail("em threads", M, N, T, th);
+    const size_t b = EmSmem<M, N>::bytes(th);
+    if (b > kDynMax) fail("em smem", M, N, T, b);
+  }
+}
+
+// full-rank FCA kernel (EM and MM): T <= kFcaMaxThreads * kFcaSlots
+template <int M, int N, bool MM>
+void check_fca() {
+  for (int T = 1; T <= kFcaMaxThreads * kFcaSlots; ++T) {
+    const int th = fca_threads(T);
+    if (th % 32 || th > kFcaMaxThreads || th * kFcaSlots < T) fail("fca threads", M, N, T, th);
+    const size_t b = FcaSmem<M, N, MM>::bytes(th);
+    if (b > kDynMax) fail("fca smem", M, N, T, b);
+  }
+}
+
+// frequency-resident Wiener filter: its image staging buffer is static shared memory
+template <int M, int N>
+void check_mwf() {
+  constexpr int FSn = mwf_frame_stride(N, M);
+  const size_t b = sizeof(float4) * ((kMwfThreads * FSn + 1) / 2 + 1) + sizeof(float2) * 2 * M * M +
+                   sizeof(float) * M * N;
+  if (FSn < N * M || ((N * M) % 2 == 0 && FSn % 2)) fail("mwf frame stride", M, N, 0, FSn);
+  if (b > kStaticMax) fail("mwf static smem", M, N, 0, b);
+}
+
+// cluster kernel (runtime N <= kCMaxN) and the wide filter, for every T a cluster takes
+template <int M>
+void check_cluster() {
+  for (int N = 1; N <= kCMaxN; ++N) {
+    int accepted = 0;
+    for (int T = 1; T <= 65536; ++T) {
+      int C = 0;
+      size_t smem = 0;
+      if (!cluster_shape<M>(T, N, &C, &smem)) continue;
+      ++accepted;
+      const int Tc = (T + C - 1) / C;
+      if (C != 1 && C != 2 && C != 4 && C != 8) fail("cluster size", M, N, T, C);
+      if ((C - 1) * Tc >= T) fail("cluster CTA without frames", M, N, T, C);
+      if (smem > kDynMax || smem != ClusterSmem<M>::bytes(N, Tc)) fail("cluster smem", M, N, T, smem);
+    }
+    if (accepted < 4000) fail("cluster accepts fewer than 4000 frames", M, N, accepted, accepted);
+    const size_t wide_dyn = mwf_wide_smem(M, N);
+    const size_t wide_static = sizeof(float2) * M * (M + 1) + sizeof(float) * M * kMwfWMaxN +
+                               sizeof(float2) * 2 * kMwfWFrames * M + sizeof(float) * 2 * kMwfWMaxN * kMwfWFrames;
+    if (wide_dyn + wide_static > kDynMax || wide_static > kStaticMax) fail("wide filter smem", M, N, 0, wide_dyn);
+    if (kMwfWRow(M) % 2 || kMwfWRow(M) < M) fail("wide filter z row", M, N, 0, kMwfWRow(M));
+  }
+  if (kCThreads > 1024 || kCThreads % 32) fail("cluster threads", M, 0, 0, kCThreads);
+}
+
+template <int M, int N>
+void check_frequency_resident() {
+  check_em<M, N>();
+  check_fca<M, N, false>();
+  check_fca<M, N, true>();
+  check_mwf<M, N>();
+}
+
+template <int M>
+void check_all_n() {
+  check_frequency_resident<M, 2>();
+  check_frequency_resident<M, 3>();
+  check_frequency_resident<M, 4>();
+  check_frequency_resident<M, 5>();
+  check_frequency_resident<M, 6>();
+  check_frequency_resident<M, 7>();
+  check_frequency_resident<M, 8>();
+}
+
+}  // namespace
+
+int main() {
+  check_all_n<2>();
+  check_all_n<3>();
+  check_all_n<4>();
+  check_cluster<2>();
+  check_cluster<3>();
+  check_cluster<4>();
+  check_cluster<5>();
+  check_cluster<6>();
+  check_cluster<7>();
+  check_cluster<8>();
+  if (failures) {
+    std::printf("%d violations\n", failures);
+    return 1;
+  }
+  std::printf("ok\n");
+  return 0;
+}
