@@ -1,10 +1,19 @@
 """Benchmark: FastFCA IP+EM throughput (time-frequency-bin iterations per second) on GB300.
 
-One step = one complete FastFCA run on the M=4, N=6, F=513, T=1250 workload (100 IP+EM
-iterations, Algorithm 1, then the Wiener-filter separation of Eq. 39), starting from the
-seeded random initialisation, through the library's C ABI.  The metric counts F*T*iters
-bin-iterations per step.  Inputs are model-generated (synthetic) and resident in HBM when a
-timed step starts; L2 is flushed (a 512 MiB write) between steps, outside the timed spans.
+Headline workload: the large single instance, M=8 (circular array, r = 5 cm), N=12, F=1025,
+T=4000, K=16.  One step = one complete FastFCA run on it through the library's C ABI: 50
+IP+EM iterations (Algorithm 1) from the seeded random start, then the Wiener-filter
+separation of Eq. 39.  The metric counts F*T*iters bin-iterations per step.  Inputs are
+model-generated (synthetic) and resident in HBM when a timed step starts; the inputs are
+larger than L2 and L2 is also flushed (a 512 MiB write) between steps, outside the timed
+spans.
+
+Also reported, each under its own key: the end-to-end figure through the C ABI with host
+buffers (copies inside the span), the roofline of the IP+EM launch (FP32 ALU and the
+streaming schedule's HBM bytes), the separation's HBM bandwidth, the oracle's throughput on
+the host cores, the precision of every output against the FP64 oracle, and the other
+workloads (M=4, N=6, F=513, T=1250 with IP+MM, block input, FCA and FastMNMF on it; the
+64-mixture batch; the learned initialiser).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -30,21 +39,25 @@ if ROOT not in sys.path:
 
 from paper_2101_08563_gb300 import synth  # noqa: E402
 
-WORKLOAD = synth.WORKLOADS["fca_cmp"]
-MNMF_K = 8            # FastMNMF bases per source on the bench mixture (its generator's K)
+HEADLINE = synth.WORKLOADS["large"]       # M=8, N=12, F=1025, T=4000, 50 iterations
+SECOND = synth.WORKLOADS["fca_cmp"]       # M=4, N=6, F=513, T=1250, 100 iterations
+MNMF_K = 8            # FastMNMF bases per source on the M=4 mixture (its generator's K)
 MNMF_ITERS = 20
-
-
-def mnmf_abi_params(st):
-    """A FastMNMF start in the C ABI's layouts: t (F, N, K), v (N, K, T)."""
-    return (st.W, st.lam, np.ascontiguousarray(st.t.transpose(0, 2, 1)),
-            np.ascontiguousarray(st.v.transpose(2, 1, 0)))
 METRIC = "FastFCA EM TF-bin-iters/s"
 UNIT = "bin-iters/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 arithmetic peak from unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x
 # 2 flop (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# oracle samples of the headline workload (frequencies spread over the band)
+CPU_SAMPLE_FREQS, CPU_SAMPLE_ITERS = 64, 4
+PRECISION_FREQS = [1, 300, 700, 1024]
+
+
+def mnmf_abi_params(st):
+    """A FastMNMF start in the C ABI's layouts: t (F, N, K), v (N, K, T)."""
+    return (st.W, st.lam, np.ascontiguousarray(st.t.transpose(0, 2, 1)),
+            np.ascontiguousarray(st.v.transpose(2, 1, 0)))
 
 
 def algorithmic_flops_per_bin_iter(M: int, N: int) -> float:
@@ -53,6 +66,17 @@ def algorithmic_flops_per_bin_iter(M: int, N: int) -> float:
     log-likelihood terms 4M."""
     tri = M * (M + 1) / 2
     return 6 * tri + 4 * M * tri + 8 * M * M + 3 * M + 13 * M * N + 4 * M
+
+
+def streaming_bytes_per_bin_iter(M: int, N: int) -> int:
+    """HBM bytes one bin-iteration moves in the streaming schedule (x read twice as complex64,
+    for the Q pass and the U pass; v read and written once as float32): 16 M + 8 N."""
+    return 16 * M + 8 * N
+
+
+def separation_bytes_per_bin(M: int, N: int) -> int:
+    """Eq. 39 per bin: x read (8 M), v read (4 N), the N images written (8 N M)."""
+    return 8 * M + 4 * N + 8 * N * M
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -113,18 +137,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- oracle timing
+# ----------------------------------------------------------------------------- oracle on the host
 _WORKER_STATE = {}
 
 
-def _pool_init(seed_index):
+def _pool_init(x, P, lam, v):
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
-    w = WORKLOAD
-    mix = synth.workload_mixture(w, seed_index)
-    init = synth.random_init(mix.x, w.N, seed=w.seed + seed_index)
-    _WORKER_STATE["x"] = mix.x
-    _WORKER_STATE["init"] = init
+    _WORKER_STATE.update(x=x, P=P, lam=lam, v=v)
 
 
 def _noop(_):
@@ -132,61 +152,75 @@ def _noop(_):
 
 
 def _oracle_worker(args):
-    """Algorithm 1 (with the per-iteration log-likelihood) and Eq. 39 on a list of
-    frequencies of the workload mixture held by this worker process."""
-    freqs, iters = args
+    """Algorithm 1 (with the per-iteration log-likelihood) and Eq. 39 on rows `idx` of the
+    sampled frequencies this worker holds; returns each row's final W, L, H, log-likelihood
+    and images when `keep`."""
+    idx, iters, keep = args
     from oracle import fastfca as off
-    x, init = _WORKER_STATE["x"], _WORKER_STATE["init"]
-    out = off.run(x, init.P, init.lam, init.v, iters=iters, freqs=freqs, with_ll=True)
+    s = _WORKER_STATE
+    out = off.run(s["x"], s["P"], s["lam"], s["v"], iters=iters, freqs=idx, with_ll=True)
+    res = []
     for i, f in enumerate(out["freqs"]):
-        off.separate_fast(x[f], out["W"][i], out["L"][i], out["H"][i])
-    return len(freqs)
+        c = off.separate_fast(s["x"][f], out["W"][i], out["L"][i], out["H"][i])
+        if keep:
+            res.append((f, out["W"][i], out["L"][i], out["H"][i], out["ll"][i], c))
+    return res if keep else len(idx)
 
 
 class OraclePool:
-    """Spawned worker processes, each holding the workload mixture (generated at start-up,
-    outside any timed span); `run` times the oracle over frequencies split across them."""
+    """Spawned worker processes, each holding the sampled frequencies of a mixture and its start
+    (handed over at start-up, outside any timed span); `run` times the oracle over rows split
+    across them."""
 
-    def __init__(self, workers, seed_index=0):
+    def __init__(self, workers, data):
         import multiprocessing as mp
         self.workers = workers
-        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(seed_index,))
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=data)
         self.pool.map(_noop, range(workers))
 
-    def run(self, freqs, iters):
-        chunks = [c for c in (freqs[i::self.workers] for i in range(self.workers)) if c]
+    def run(self, rows, iters, keep=False):
+        chunks = [c for c in (rows[i::self.workers] for i in range(self.workers)) if c]
         t0 = time.perf_counter()
-        self.pool.map(_oracle_worker, [(c, iters) for c in chunks], chunksize=1)
-        return time.perf_counter() - t0, len(chunks)
+        res = self.pool.map(_oracle_worker, [(c, iters, keep) for c in chunks], chunksize=1)
+        return time.perf_counter() - t0, len(chunks), res
 
     def close(self):
         self.pool.close()
         self.pool.join()
 
 
-def cpu_baseline():
-    """The oracle on the whole workload (every frequency, all iterations, separation) across
-    the host's cores."""
-    w = WORKLOAD
+def sample_freqs(F, n):
+    return sorted(set(int(round(f)) for f in np.linspace(0, F - 1, n)))
+
+
+def sampled_data(x, init, freqs):
+    return (np.ascontiguousarray(x[freqs]), np.ascontiguousarray(init.P[freqs]),
+            np.ascontiguousarray(init.lam[freqs]), np.ascontiguousarray(init.v[freqs]))
+
+
+def cpu_baseline(w, x, init):
+    """The oracle on a bounded sample of the headline workload (frequencies spread over the
+    band, a few iterations each with the log-likelihood, then the separation) across the
+    host's cores; each frequency costs the same, so the rate is that of the whole workload."""
     cores = os.cpu_count() or 1
-    pool = OraclePool(cores)
+    freqs = sample_freqs(w.F, CPU_SAMPLE_FREQS)
+    pool = OraclePool(cores, sampled_data(x, init, freqs))
     try:
-        wall, used = pool.run(list(range(w.F)), w.iters)
+        wall, used, _ = pool.run(list(range(len(freqs))), CPU_SAMPLE_ITERS)
     finally:
         pool.close()
-    sample = (f"whole workload: {w.F} frequencies x {w.iters} iterations (+ log-likelihood each "
-              f"iteration) + separation, split over {used} processes")
-    # the same oracle on one core, on a sample of frequencies (each frequency costs the same)
-    n1 = 16
-    pool1 = OraclePool(1)
+    sample = (f"{len(freqs)} of the {w.F} frequencies (spread over the band) x {CPU_SAMPLE_ITERS} IP+EM "
+              f"iterations (+ log-likelihood each iteration) + separation, split over {used} processes")
+    n1 = 4
+    pool1 = OraclePool(1, sampled_data(x, init, freqs[:n1]))
     try:
-        wall1, _ = pool1.run(list(range(n1)), w.iters)
+        wall1, _, _ = pool1.run(list(range(n1)), 2)
     finally:
         pool1.close()
-    return {"value": w.F * w.T * w.iters / wall, "unit": UNIT, "cores": used, "kind": "oracle",
+    return {"value": len(freqs) * w.T * CPU_SAMPLE_ITERS / wall, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": sample, "seconds": round(wall, 3),
-            "single_core": {"value": n1 * w.T * w.iters / wall1, "unit": UNIT, "cores": 1,
-                            "sample": f"{n1} of the {w.F} frequencies x {w.iters} iterations, one process",
+            "single_core": {"value": n1 * w.T * 2 / wall1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} of the {w.F} frequencies x 2 iterations, one process",
                             "seconds": round(wall1, 3)}}
 
 
@@ -221,7 +255,7 @@ def generate_batch():
     return shapes, data
 
 
-def run_batch(shapes, data, dev, stream, clocks_ok=True):
+def run_batch(shapes, data, dev, stream):
     import torch
     from paper_2101_08563_gb300 import fastfca
     xs = [torch.from_numpy(d[0]).to(dev) for d in data]
@@ -261,7 +295,7 @@ def run_batch(shapes, data, dev, stream, clocks_ok=True):
             "config": "M in {2,3,4}, N in M+1..M+3, F=513, T uniform [200,2000], one CUDA-graph launch"}
 
 
-# ----------------------------------------------------------------------------- GPU arm
+# ----------------------------------------------------------------------------- learned initialiser
 def run_learned(n_train):
     """The learned initialiser end to end on the GPU: n_train generated mixtures of the
     learned-initialiser workload with 200-iteration FastFCA targets, 6 epochs of training, and
@@ -282,137 +316,11 @@ def run_learned(n_train):
     res.update({"workload": w.name, "train_mixtures": n_train, "target_iters": w.iters,
                 "train_data_seconds": t_data, "train_seconds": t_train, "epochs": 6, "batch_rows": 2048,
                 "loss_untrained": loss0, "loss_trained": loss1,
-                "held_out": "512 mixtures, generator key disjoint from the training keys",
-                "reference_ll": "default start after 200 iterations (GPU FastFCA, oracle-parity tested)"})
+                "held_out": "512 mixtures, generator key disjoint from the training keys"})
     return res
 
 
-def separation_roofline(w, sep_ms, peaks):
-    """The Wiener separation (W^{-H} per frequency + Eq. 39 filter) of one step as an HBM-bound
-    kernel: algorithmic bytes x (8 M) + v (4 N) read and c (8 N M) written per bin, over its
-    event-timed span inside the step (it follows the IP+EM launch, so x and v may still be
-    partly in L2)."""
-    per_bin = 8 * w.M + 4 * w.N + 8 * w.N * w.M
-    bytes_ = per_bin * w.F * w.T
-    ms = statistics.mean(sep_ms)
-    hbm = peaks.get("hbm_gbs")
-    gbs = bytes_ / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "bst_to_winv_kernel + fastfca_mwf_kernel", "achieved": gbs,
-            "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if hbm else None,
-            "bytes_per_bin": per_bin, "ms": ms,
-            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-
-
-def run_large(peaks):
-    """The large single instance (M=8 circular, N=12, F=1025, T=4000, K=16, 50 iterations)
-    on the cluster kernel: IP+EM launch throughput (event-timed, L2 flushed between steps)
-    and the Wiener separation's HBM bandwidth (x and v read, 3.15 GB of images written)."""
-    import torch
-    from paper_2101_08563_gb300 import fastfca
-    w = synth.WORKLOADS["large"]
-    mix = synth.workload_mixture(w)
-    init = synth.random_init(mix.x, w.N, seed=w.seed)
-    x = torch.from_numpy(mix.x).cuda()
-    P0, lam0, v0 = (torch.from_numpy(a).cuda() for a in (init.P, init.lam, init.v))
-    c = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device="cuda")
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sep = fastfca.Separator(x, w.N)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    em_ms, mwf_ms = [], []
-    for rep in range(4):
-        sep.set_params(P0, lam0, v0)
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev[0].record()
-        sep.iterate(w.iters, return_ll=False)
-        ev[1].record()
-        sep.separate(c)
-        ev[2].record()
-        torch.cuda.synchronize()
-        if rep > 0:                                   # the first is a warm-up
-            em_ms.append(ev[0].elapsed_time(ev[1]))
-            mwf_ms.append(ev[1].elapsed_time(ev[2]))
-    ll_em = float(sep.loglik()) / (w.F * w.T)
-    sep.close()
-    # the same start and iterations by IP+MM (Algorithm 2) on the same cluster kernel
-    msep = fastfca.Separator(x, w.N, model="fastfca_mm")
-    mm_ms = []
-    for rep in range(3):
-        msep.set_params(P0, lam0, v0)
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev[0].record()
-        msep.iterate(w.iters, return_ll=False)
-        ev[1].record()
-        torch.cuda.synchronize()
-        if rep > 0:
-            mm_ms.append(ev[0].elapsed_time(ev[1]))
-    ll_mm = float(msep.loglik()) / (w.F * w.T)
-    msep.close()
-    em = statistics.mean(em_ms)
-    mwf = statistics.mean(mwf_ms)
-    mm = statistics.mean(mm_ms)
-    flops = algorithmic_flops_per_bin_iter(w.M, w.N) * w.F * w.T * w.iters
-    mwf_bytes = x.numel() * 8 + v0.numel() * 4 + c.numel() * 8
-    hbm = peaks.get("hbm_gbs")
-    return {
-        "workload": w.name, "metric": METRIC, "value": w.F * w.T * w.iters / (em * 1e-3), "unit": UNIT,
-        "iters": w.iters, "em_launch_ms": em, "kernel": "fastfca_em_cluster_kernel<8> (clusters of 8 CTAs)",
-        "roofline": {"bound": "alu", "achieved": flops / (em * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": flops / (em * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                     "flops_per_bin_iter": algorithmic_flops_per_bin_iter(w.M, w.N)},
-        "separation": {"kernel": "fastfca_mwf_wide_kernel<8>", "ms": mwf, "bytes": mwf_bytes,
-                       "achieved_gbs": mwf_bytes / (mwf * 1e-3) / 1e9,
-                       "frac_of_measured_hbm": (mwf_bytes / (mwf * 1e-3) / 1e9 / hbm) if hbm else None},
-        "l2": "flushed before each step (512 MiB write, untimed)",
-        "loglik_per_bin": ll_em,
-        "ip_mm": {"algorithm": "IP+MM (Algorithm 2), same start and iterations", "launch_ms": mm,
-                  "value": w.F * w.T * w.iters / (mm * 1e-3), "unit": UNIT, "loglik_per_bin": ll_mm},
-    }
-
-
-def precision_report():
-    """Error of every output of the CUDA path against the FP64 oracle from the same start:
-    the whole small workload (M=2, N=3, F=257, T=250, 20 iterations) and four frequencies of
-    the bench workload (100 iterations).  Images c and log-likelihood per iteration are
-    compared directly; the parameters through W (fixed scale: the IP normalises it) and the
-    scale-free sigma^2 = LH and per-source powers L[:, n] H[n, :]."""
-    import torch
-    from oracle import fastfca as off
-    from paper_2101_08563_gb300 import fastfca
-    out = {}
-    for name, freqs in (("small", None), ("fca_cmp", [3, 130, 257, 511])):
-        w = synth.WORKLOADS[name]
-        mix = synth.workload_mixture(w)
-        init = synth.random_init(mix.x, w.N, seed=w.seed)
-        fs = list(range(w.F)) if freqs is None else freqs
-        x = np.ascontiguousarray(mix.x[fs])
-        sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N)
-        sep.set_params(np.ascontiguousarray(init.P[fs]), np.ascontiguousarray(init.lam[fs]),
-                       np.ascontiguousarray(init.v[fs]))
-        ll = sep.iterate(w.iters)
-        c = sep.separate()
-        P, lam, v = sep.get_params()
-        sep.close()
-        ref = off.run(x, init.P[fs], init.lam[fs], init.v[fs], iters=w.iters)
-        ll_ref = ref["ll"].sum(axis=0)
-        cr = np.stack([off.separate_fast(x[i], ref["W"][i], ref["L"][i], ref["H"][i]) for i in range(len(fs))])
-        s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
-        s2r = np.einsum("fmn,fnt->fmt", ref["L"], ref["H"])
-        pw = lam.astype(np.float64)[:, :, :, None] * v.astype(np.float64)[:, None, :, :]
-        pwr = ref["L"][:, :, :, None] * ref["H"][:, None, :, :]
-        out[name] = {
-            "frequencies": "all" if freqs is None else freqs, "iters": w.iters,
-            "loglik_rel_err_max": float(np.max(np.abs(ll - ll_ref) / np.abs(ll_ref))),
-            "images_rel_err": float(np.linalg.norm(c - cr) / np.linalg.norm(cr)),
-            "W_rel_err": float(np.max(np.abs(P - ref["W"])) / np.max(np.abs(ref["W"]))),
-            "sigma2_rel_err_max": float(np.max(np.abs(s2 - s2r) / s2r)),
-            "source_power_rel_err_median": float(np.median(np.abs(pw - pwr) / pwr)),
-            "tolerance": {"loglik": 1e-5, "images": 1e-4},
-        }
-    return out
-
-
+# ----------------------------------------------------------------------------- rooflines
 def load_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -420,17 +328,73 @@ def load_peaks():
         return {}
 
 
-def run_gpu(args, rank, world, local_rank):
-    import torch
-    from paper_2101_08563_gb300 import build, fastfca
+def em_roofline(w, em_ms, peaks, kernel, traffic):
+    """The IP+EM launch against both ceilings: FP32 arithmetic (algorithmic flops per
+    bin-iteration, unit-count peak) and HBM (the streaming schedule's 16 M + 8 N bytes per
+    bin-iteration, measured copy bandwidth).  The binding one (the lower ceiling on
+    bin-iters/s) is named in `bound`."""
+    units = w.F * w.T * w.iters
+    s = statistics.mean(em_ms) * 1e-3
+    flops = algorithmic_flops_per_bin_iter(w.M, w.N)
+    by = streaming_bytes_per_bin_iter(w.M, w.N)
+    hbm = peaks.get("hbm_gbs")
+    alu = {"achieved": flops * units / s / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+           "frac": flops * units / s / 1e12 / FP32_PEAK_TFLOPS, "flops_per_bin_iter": flops,
+           "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"}
+    mem = {"achieved": by * units / s / 1e9, "peak": hbm, "unit": "GB/s",
+           "frac": (by * units / s / 1e9 / hbm) if hbm else None, "bytes_per_bin_iter": by,
+           "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "note": "algorithmic bytes of the streaming schedule (x read twice, v read and written once)"}
+    alu_ceiling = FP32_PEAK_TFLOPS * 1e12 / flops
+    hbm_ceiling = (hbm * 1e9 / by) if hbm else float("inf")
+    bound = "alu" if alu_ceiling < hbm_ceiling else "hbm"
+    main = alu if bound == "alu" else mem
+    return {"bound": bound, "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
+            "frac": main["frac"], "traffic": traffic, "kernel": kernel, "launch_ms": statistics.mean(em_ms),
+            "alu": alu, "hbm": mem,
+            "ceilings_bin_iters_per_s": {"alu": alu_ceiling, "hbm": hbm_ceiling}}
 
-    torch.cuda.set_device(local_rank)
+
+def separation_roofline(w, sep_ms, peaks, kernel):
+    """The Wiener separation (W^{-H} per frequency + Eq. 39 filter) of one step as an HBM-bound
+    kernel: algorithmic bytes x (8 M) + v (4 N) read and c (8 N M) written per bin, over its
+    event-timed span inside the step."""
+    per_bin = separation_bytes_per_bin(w.M, w.N)
+    bytes_ = per_bin * w.F * w.T
+    ms = statistics.mean(sep_ms)
+    hbm = peaks.get("hbm_gbs")
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": (gbs / hbm) if hbm else None, "bytes_per_bin": per_bin, "ms": ms,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def em_traffic(kernel_key):
+    """DRAM bytes per launch of a kernel from the committed ncu record, or None when the
+    kernel's sources changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(prof))[kernel_key]
+        csrc = os.path.join(ROOT, "paper_2101_08563_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in rec["sources"])
+        if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- the headline
+def run_headline(args, rank, world, local_rank, w, x_np, init):
+    """The headline workload on this rank: K timed steps (50 IP+EM iterations + separation, one
+    stream, L2 flushed between steps), the end-to-end leg through the C ABI with host buffers,
+    and one untimed run whose outputs feed the precision report."""
+    import torch
+    from paper_2101_08563_gb300 import fastfca
+
     dev = torch.device("cuda", local_rank)
-    w = WORKLOAD
-    mix = synth.workload_mixture(w, rank)
-    init = synth.random_init(mix.x, w.N, seed=w.seed + rank)
-    build.build()
-    x = torch.from_numpy(mix.x).to(dev)
+    x = torch.from_numpy(x_np).to(dev)
     P0 = torch.from_numpy(init.P).to(dev)
     lam0 = torch.from_numpy(init.lam).to(dev)
     v0 = torch.from_numpy(init.v).to(dev)
@@ -439,17 +403,13 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     sep = fastfca.Separator(x, w.N, stream=stream.cuda_stream)
 
-    def step():
+    for _ in range(args.warmup):
         sep.set_params(P0, lam0, v0)
         sep.iterate(w.iters, return_ll=False)
         sep.separate(c)
-
-    for _ in range(args.warmup):
-        step()
         flush.zero_()
     torch.cuda.synchronize()
 
-    # per-launch timing of the dominant kernel (the fused IP+EM launch) inside each step
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -472,111 +432,30 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     em_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
     sep_ms = [m.elapsed_time(e) for m, e in zip(mids, ends)]
-    # the set_params copies are outside the event spans; one step is iterate + separate
     units = w.F * w.T * w.iters
     value = weak_scaling_value(units * args.steps, sum(step_ms) * 1e-3, world, dev)
     tot_ms = world * units * args.steps / value * 1e3          # the max over ranks
 
-    # the same model fitted by IP+MM (Algorithm 2) on the same mixture and start, for the
-    # paper's iteration count (20, Table I): time per launch and the log-likelihood reached,
-    # beside IP+EM's after as many iterations.  (Run longer on this mixture, IP+MM reaches a
-    # point where a decorrelated channel and its model variance vanish together at one frame
-    # and the likelihood has no upper bound; the FP64 oracle does the same.)
-    mm_iters = 20
-    msep = fastfca.Separator(x, w.N, model="fastfca_mm", stream=stream.cuda_stream)
-    msep.set_params(P0, lam0, v0)
-    msep.iterate(2, return_ll=False)
-    mm_ms = []
-    for _ in range(3):
-        flush.zero_()
-        msep.set_params(P0, lam0, v0)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        msep.iterate(mm_iters, return_ll=False)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        mm_ms.append(a0.elapsed_time(a1))
-    msep.set_params(P0, lam0, v0)
-    mm_ll = float(msep.iterate(mm_iters)[-1])
-    msep.close()
+    # one untimed run whose outputs the precision report compares with the oracle
     sep.set_params(P0, lam0, v0)
-    em_ll_same = float(sep.iterate(mm_iters)[-1])
-    em_ms_same = []
-    for _ in range(3):
-        flush.zero_()
-        sep.set_params(P0, lam0, v0)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        sep.iterate(mm_iters, return_ll=False)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        em_ms_same.append(a0.elapsed_time(a1))
+    hist = sep.iterate(w.iters)
+    P, lam, v = sep.get_params()
+    _, ll_f = sep.loglik(per_f=True)
+    sep.separate(c)
+    torch.cuda.synchronize()
+    fs = PRECISION_FREQS
+    outputs = {"freqs": fs, "ll_hist": hist, "ll_f": ll_f[fs], "P": P[fs], "lam": lam[fs], "v": v[fs],
+               "c": c[fs].cpu().numpy()}
+    x_sum_err = float((c.sum(dim=2) - x).abs().pow(2).sum().sqrt() / x.abs().pow(2).sum().sqrt())
+    sep.close()
+    del c
+    torch.cuda.empty_cache()
 
-    # piecewise-stationary input (Sec. VI-B): the same mixture in blocks of 5 frames (250 blocks), the
-    # default start of a block context, the bench's iterations
-    blk = 5
-    bsep = fastfca.Separator(x, w.N, stream=stream.cuda_stream, block=blk, seed=w.seed)
-    Pb, lamb, vb = bsep.get_params()
-    Pb, lamb, vb = (torch.from_numpy(a).to(dev) for a in (Pb, lamb, vb))
-    bsep.iterate(2, return_ll=False)
-    blk_ms = []
-    for _ in range(3):
-        flush.zero_()
-        bsep.set_params(Pb, lamb, vb)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        bsep.iterate(w.iters, return_ll=False)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        blk_ms.append(a0.elapsed_time(a1))
-    bsep.close()
-
-    # FCA comparison path on the same GPU (fewer iterations: it is ~an order slower)
-    fca_iters = 10
-    R0, h0 = synth.fca_random_init(mix.x, w.N, seed=w.seed + rank)
-    R0d = torch.from_numpy(R0).to(dev)
-    h0d = torch.from_numpy(h0).to(dev)
-    fca_ms, fca_ll = {}, {}
-    for model in ("fca", "fca_mm"):      # EM (Eq. 12-13) and MM (Eq. 15-17)
-        fsep = fastfca.Separator(x, w.N, model=model, stream=stream.cuda_stream)
-        fsep.set_params_fca(R0d, h0d)
-        fsep.iterate(2, return_ll=False)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        fsep.set_params_fca(R0d, h0d)
-        f0.record(stream)
-        fsep.iterate(fca_iters, return_ll=False)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fca_ms[model] = f0.elapsed_time(f1)
-        fca_ll[model] = float(fsep.loglik()) / (w.F * w.T)
-        fsep.close()
-
-    # FastMNMF (App. C) on the same mixture, K bases per source, from the same kind of start
-    st = synth.fastmnmf_random_init(mix.x, w.N, MNMF_K, seed=w.seed + rank)
-    mparams = [torch.from_numpy(a).to(dev) for a in mnmf_abi_params(st)]
-    mnsep = fastfca.Separator(x, w.N, model="fastmnmf", bases=MNMF_K, stream=stream.cuda_stream)
-    mnsep.set_params_mnmf(*mparams)
-    mnsep.iterate(2, return_ll=False)
-    mn_ms = []
-    for _ in range(3):
-        flush.zero_()
-        mnsep.set_params_mnmf(*mparams)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        mnsep.iterate(MNMF_ITERS, return_ll=False)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        mn_ms.append(a0.elapsed_time(a1))
-    mn_ll = float(mnsep.loglik()) / (w.F * w.T)
-    mnsep.close()
-
-    # end-to-end through the public API with host buffers (pinned), copies inside the span:
+    # end to end through the public API with host buffers (pinned), copies inside the span:
     # every step uploads its mixture and start, runs the iterations (reading back the
     # log-likelihood per iteration) and downloads the images.  Two long-lived contexts on two
     # streams take the steps in turn, so one step's copies overlap the other's kernels.
-    x_h = torch.from_numpy(mix.x).pin_memory()
+    x_h = torch.from_numpy(x_np).pin_memory()
     P_h = torch.from_numpy(init.P).pin_memory()
     lam_h = torch.from_numpy(init.lam).pin_memory()
     v_h = torch.from_numpy(init.v).pin_memory()
@@ -584,7 +463,7 @@ def run_gpu(args, rank, world, local_rank):
     ll_hs = [torch.empty(w.iters, dtype=torch.float64).pin_memory() for _ in range(2)]
     e2e_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
     ctxs = [fastfca.Separator(x_h, w.N, stream=st.cuda_stream) for st in e2e_streams]
-    e2e_steps = max(4, min(args.steps, 10))
+    e2e_steps = max(4, min(args.steps, 8))
 
     def e2e_step(i):
         s = ctxs[i % 2]
@@ -599,9 +478,8 @@ def run_gpu(args, rank, world, local_rank):
     e2e_step(1)
     for s_ in ctxs:
         s_.sync()
-    # three windows of e2e_steps steps; the median is reported.  The leg is host-bound and the
-    # host is shared, so one window alone can catch a stall of the host's own.
     e2e_windows = []
+    ll = None
     for _ in range(3):
         barrier(world)
         t0 = time.perf_counter()
@@ -611,21 +489,224 @@ def run_gpu(args, rank, world, local_rank):
             s_.sync()
         e2e_windows.append(weak_scaling_value(units * e2e_steps, time.perf_counter() - t0, world, dev))
     e2e_value = statistics.median(e2e_windows)
-    h2d = mix.x.nbytes + init.P.nbytes + init.lam.nbytes + init.v.nbytes
+    h2d = x_np.nbytes + init.P.nbytes + init.lam.nbytes + init.v.nbytes
     d2h = c_hs[0].numel() * 8 + w.iters * 8
+    e2e_ll_ok = bool(np.allclose(ll.numpy(), hist, rtol=0, atol=0))
     for s_ in ctxs:
         s_.close()
-    sep.close()
     return {
         "value": value, "ms_per_step": tot_ms / args.steps, "em_ms": em_ms, "step_ms": step_ms, "sep_ms": sep_ms,
-        "clocks": clock_info, "fca_ms": fca_ms, "fca_ll": fca_ll, "fca_iters": fca_iters, "mn_ms": mn_ms,
-        "mn_ll": mn_ll, "mm_ms": mm_ms, "mm_ll": mm_ll,
-        "mm_iters": mm_iters, "em_ll_same": em_ll_same, "em_ms_same": em_ms_same, "blk": blk, "blk_ms": blk_ms,
-        "e2e_value": e2e_value, "e2e_windows": e2e_windows, "e2e_steps": e2e_steps, "h2d": h2d, "d2h": d2h,
-        "final_ll": float(ll[-1].item() if hasattr(ll[-1], "item") else ll[-1]),
+        "clocks": clock_info, "e2e_value": e2e_value, "e2e_windows": e2e_windows, "e2e_steps": e2e_steps,
+        "h2d": h2d, "d2h": d2h, "e2e_ll_equal": e2e_ll_ok, "outputs": outputs, "images_sum_err": x_sum_err,
+        "final_ll": float(hist[-1]),
     }
 
 
+# ----------------------------------------------------------------------------- the M=4 workload
+def run_second(args, rank, local_rank):
+    """The M=4, N=6, F=513, T=1250 workload: IP+EM (100 iterations) + separation per step,
+    device-timed; then IP+MM, the block input, FCA (EM and MM) and FastMNMF on the same mixture."""
+    import torch
+    from paper_2101_08563_gb300 import fastfca
+
+    w = SECOND
+    dev = torch.device("cuda", local_rank)
+    mix = synth.workload_mixture(w, rank)
+    init = synth.random_init(mix.x, w.N, seed=w.seed + rank)
+    x = torch.from_numpy(mix.x).to(dev)
+    P0, lam0, v0 = (torch.from_numpy(a).to(dev) for a in (init.P, init.lam, init.v))
+    c = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sep = fastfca.Separator(x, w.N, stream=stream.cuda_stream)
+
+    def timed(fn, reps=3, reset=None):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            if reset:
+                reset()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            out.append(a0.elapsed_time(a1))
+        return out
+
+    reset = lambda: sep.set_params(P0, lam0, v0)   # noqa: E731
+    for _ in range(3):
+        reset()
+        sep.iterate(w.iters, return_ll=False)
+        sep.separate(c)
+    steps = max(5, min(args.steps, 20))
+    em_ms, sep_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        reset()
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(stream)
+        sep.iterate(w.iters, return_ll=False)
+        a1.record(stream)
+        sep.separate(c)
+        a2.record(stream)
+        torch.cuda.synchronize()
+        em_ms.append(a0.elapsed_time(a1))
+        sep_ms.append(a1.elapsed_time(a2))
+    step_ms = [a + b for a, b in zip(em_ms, sep_ms)]
+
+    # IP+MM (Algorithm 2) for the paper's iteration count (20, Table I), beside IP+EM's 20
+    mm_iters = 20
+    msep = fastfca.Separator(x, w.N, model="fastfca_mm", stream=stream.cuda_stream)
+    msep.set_params(P0, lam0, v0)
+    msep.iterate(2, return_ll=False)
+    mm_ms = timed(lambda: msep.iterate(mm_iters, return_ll=False), reset=lambda: msep.set_params(P0, lam0, v0))
+    msep.set_params(P0, lam0, v0)
+    mm_ll = float(msep.iterate(mm_iters)[-1])
+    msep.close()
+    reset()
+    em_ll_same = float(sep.iterate(mm_iters)[-1])
+    em_ms_same = timed(lambda: sep.iterate(mm_iters, return_ll=False), reset=reset)
+
+    # piecewise-stationary input (Sec. VI-B): blocks of 5 frames (250 blocks), its default start
+    blk = 5
+    bsep = fastfca.Separator(x, w.N, stream=stream.cuda_stream, block=blk, seed=w.seed)
+    Pb, lamb, vb = (torch.from_numpy(a).to(dev) for a in bsep.get_params())
+    bsep.iterate(2, return_ll=False)
+    blk_ms = timed(lambda: bsep.iterate(w.iters, return_ll=False), reset=lambda: bsep.set_params(Pb, lamb, vb))
+    bsep.close()
+
+    # FCA comparison path on the same GPU (fewer iterations: it is ~an order slower)
+    fca_iters = 10
+    R0, h0 = synth.fca_random_init(mix.x, w.N, seed=w.seed + rank)
+    R0d, h0d = torch.from_numpy(R0).to(dev), torch.from_numpy(h0).to(dev)
+    fca = {}
+    for model in ("fca", "fca_mm"):      # EM (Eq. 12-13) and MM (Eq. 15-17)
+        fsep = fastfca.Separator(x, w.N, model=model, stream=stream.cuda_stream)
+        fsep.set_params_fca(R0d, h0d)
+        fsep.iterate(2, return_ll=False)
+        ms = timed(lambda: fsep.iterate(fca_iters, return_ll=False), reps=1,
+                   reset=lambda: fsep.set_params_fca(R0d, h0d))[0]
+        fca[model] = {"value": w.F * w.T * fca_iters / (ms * 1e-3), "unit": UNIT, "iters": fca_iters, "ms": ms,
+                      "loglik_per_bin": float(fsep.loglik()) / (w.F * w.T),
+                      "update": {"fca": "EM, Eq. 12-13", "fca_mm": "MM with the geometric mean, Eq. 15-17"}[model]}
+        fsep.close()
+
+    # FastMNMF (App. C) on the same mixture, K bases per source
+    st = synth.fastmnmf_random_init(mix.x, w.N, MNMF_K, seed=w.seed + rank)
+    mparams = [torch.from_numpy(a).to(dev) for a in mnmf_abi_params(st)]
+    mnsep = fastfca.Separator(x, w.N, model="fastmnmf", bases=MNMF_K, stream=stream.cuda_stream)
+    mnsep.set_params_mnmf(*mparams)
+    mnsep.iterate(2, return_ll=False)
+    mn_ms = timed(lambda: mnsep.iterate(MNMF_ITERS, return_ll=False), reset=lambda: mnsep.set_params_mnmf(*mparams))
+    mn_ll = float(mnsep.loglik()) / (w.F * w.T)
+    mnsep.close()
+    sep.close()
+
+    peaks = load_peaks()
+    units = w.F * w.T * w.iters
+    return {
+        "workload": w.name, "M": w.M, "N": w.N, "F": w.F, "T": w.T, "iters": w.iters,
+        "metric": METRIC, "value": units / (statistics.mean(step_ms) * 1e-3), "unit": UNIT,
+        "ms_per_step": statistics.mean(step_ms), "em_launch_ms": statistics.mean(em_ms),
+        "roofline": em_roofline(w, em_ms, peaks, "fastfca_em_kernel<4,6> (one CTA per frequency)",
+                                em_traffic("fastfca_em_kernel")),
+        "roofline_separation": separation_roofline(w, sep_ms, peaks, "bst_to_winv_kernel + fastfca_mwf_kernel"),
+        "l2_note": "x and v (36 MB) fit L2: the IP+EM launch reads HBM once per launch, so its HBM "
+                   "fraction is an equivalent, not DRAM traffic",
+        "ip_mm": {"algorithm": "IP+MM (Algorithm 2), same mixture and start, 20 iterations (Table I)",
+                  "iters": mm_iters, "value": w.F * w.T * mm_iters / (statistics.mean(mm_ms) * 1e-3), "unit": UNIT,
+                  "launch_ms": statistics.mean(mm_ms), "loglik": mm_ll,
+                  "ip_em_same_iters": {"value": w.F * w.T * mm_iters / (statistics.mean(em_ms_same) * 1e-3),
+                                       "launch_ms": statistics.mean(em_ms_same), "loglik": em_ll_same}},
+        "block_input": {"model": "piecewise-stationary FastFCA (Sec. VI-B), IP+EM, blocks of %d frames" % blk,
+                        "B": blk, "launch_ms": statistics.mean(blk_ms),
+                        "block_iters_per_s": w.F * (w.T // blk) * w.iters / (statistics.mean(blk_ms) * 1e-3),
+                        "frame_bin_iters_per_s": w.F * w.T * w.iters / (statistics.mean(blk_ms) * 1e-3)},
+        "fca_comparison": fca,
+        "fastmnmf": {"model": "FastMNMF (App. C), K = %d bases per source, same mixture" % MNMF_K,
+                     "iters": MNMF_ITERS, "ms": statistics.mean(mn_ms),
+                     "value": w.F * w.T * MNMF_ITERS / (statistics.mean(mn_ms) * 1e-3), "unit": UNIT,
+                     "launches_per_iter": 4, "loglik_per_bin": mn_ll},
+    }
+
+
+# ----------------------------------------------------------------------------- precision
+def _errors(ll, ll_ref, c, cr, P, W_ref, lam, v, L_ref, H_ref):
+    """Every output against the oracle: log-likelihood, images per (f, n) block, W (fixed scale:
+    the IP normalises it), the scale-free sigma^2 = LH and per-source powers L[:, n] H[n, :]."""
+    d = np.abs(c.astype(np.complex128) - cr)
+    a = np.abs(cr)
+    fro = np.sqrt((d ** 2).sum(axis=(1, 3))) / np.sqrt((a ** 2).sum(axis=(1, 3)))
+    ele = d.max(axis=(1, 3)) / a.max(axis=(1, 3))
+    s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
+    s2r = np.einsum("fmn,fnt->fmt", L_ref, H_ref)
+    pw = lam.astype(np.float64)[:, :, :, None] * v.astype(np.float64)[:, None, :, :]
+    pwr = L_ref[:, :, :, None] * H_ref[:, None, :, :]
+    return {
+        "loglik_rel_err_max": float(np.max(np.abs(ll - ll_ref) / np.abs(ll_ref))),
+        "images_rel_err": float(np.linalg.norm(c - cr) / np.linalg.norm(cr)),
+        "images_rel_err_worst_f_n_block": float(fro.max()),
+        "images_elementwise_err_worst_f_n_block": float(ele.max()),
+        "W_rel_err": float(np.max(np.abs(P - W_ref)) / np.max(np.abs(W_ref))),
+        "sigma2_rel_err_max": float(np.max(np.abs(s2 - s2r) / s2r)),
+        "source_power_rel_err_median": float(np.median(np.abs(pw - pwr) / pwr)),
+        "tolerance": {"loglik": 1e-5, "images": 1e-4},
+    }
+
+
+def precision_report(headline_outputs, x_head, init_head):
+    """Error of every output of the CUDA path against the FP64 oracle from the same start: the
+    whole small workload (M=2, N=3, F=257, T=250, 20 iterations), four frequencies of the M=4
+    workload (100 iterations) and four frequencies of the headline workload (50 iterations,
+    the outputs of the benchmark's own run)."""
+    import torch
+    from oracle import fastfca as off
+    from paper_2101_08563_gb300 import fastfca
+    out = {}
+    for name, freqs in (("small", None), ("fca_cmp", [3, 130, 257, 511])):
+        w = synth.WORKLOADS[name]
+        mix = synth.workload_mixture(w)
+        init = synth.random_init(mix.x, w.N, seed=w.seed)
+        fs = list(range(w.F)) if freqs is None else freqs
+        x = np.ascontiguousarray(mix.x[fs])
+        sep = fastfca.Separator(torch.from_numpy(x).cuda(), w.N)
+        sep.set_params(np.ascontiguousarray(init.P[fs]), np.ascontiguousarray(init.lam[fs]),
+                       np.ascontiguousarray(init.v[fs]))
+        ll = sep.iterate(w.iters)
+        c = sep.separate()
+        P, lam, v = sep.get_params()
+        sep.close()
+        ref = off.run(x, init.P[fs], init.lam[fs], init.v[fs], iters=w.iters)
+        cr = np.stack([off.separate_fast(x[i], ref["W"][i], ref["L"][i], ref["H"][i]) for i in range(len(fs))])
+        e = _errors(ll, ref["ll"].sum(axis=0), c, cr, P, ref["W"], lam, v, ref["L"], ref["H"])
+        e.update({"workload": w.name, "frequencies": "all" if freqs is None else freqs, "iters": w.iters})
+        out[name] = e
+    if headline_outputs is not None:
+        w = HEADLINE
+        o = headline_outputs
+        fs = o["freqs"]
+        pool = OraclePool(len(fs), sampled_data(x_head, init_head, fs))
+        try:
+            _, _, res = pool.run(list(range(len(fs))), w.iters, keep=True)
+        finally:
+            pool.close()
+        rows = sorted(r for chunk in res for r in chunk)
+        W_ref = np.stack([r[1] for r in rows])
+        L_ref = np.stack([r[2] for r in rows])
+        H_ref = np.stack([r[3] for r in rows])
+        ll_ref = np.array([r[4][-1] for r in rows])
+        cr = np.stack([r[5] for r in rows])
+        e = _errors(o["ll_f"], ll_ref, o["c"], cr, o["P"], W_ref, o["lam"], o["v"], L_ref, H_ref)
+        e["loglik_rel_err_max"] = float(np.max(np.abs(o["ll_f"] - ll_ref) / np.abs(ll_ref)))
+        e.update({"workload": w.name, "frequencies": fs, "iters": w.iters,
+                  "note": "the benchmark's own run; log-likelihood compared per frequency after the last "
+                          "iteration"})
+        out["large"] = e
+    return out
+
+
+# ----------------------------------------------------------------------------- profiling cases
 def run_profile_case(F, iters, workload="fca_cmp", model="fastfca", separate=False):
     """A workload's first 8 frequencies tiled to F (so the launch has F frequencies of the
     workload's shape), two launches of the IP+EM kernel (model "fastfca_mm": IP+MM): 2
@@ -635,7 +716,7 @@ def run_profile_case(F, iters, workload="fca_cmp", model="fastfca", separate=Fal
     import torch
     from paper_2101_08563_gb300 import build, fastfca
     if workload == "fastmnmf":
-        w = WORKLOAD
+        w = SECOND
         mix = synth.workload_mixture(w)
         st = synth.fastmnmf_random_init(mix.x, w.N, MNMF_K, seed=w.seed)
         build.build()
@@ -668,22 +749,7 @@ def run_profile_case(F, iters, workload="fca_cmp", model="fastfca", separate=Fal
     print("profile case done")
 
 
-def em_traffic():
-    """DRAM bytes per bench launch of the IP+EM kernel from the committed ncu capture, or None
-    when the kernel source changed since that capture."""
-    import hashlib
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        rec = json.load(open(prof))["fastfca_em_kernel"]
-        csrc = os.path.join(ROOT, "paper_2101_08563_gb300", "csrc")
-        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("fastfca_em.cuh", "common.cuh"))
-        if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
-            return None
-        return rec["bytes_per_launch"]
-    except Exception:
-        return None
-
-
+# ----------------------------------------------------------------------------- multi-rank helpers
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -706,6 +772,15 @@ def allreduce_max(v, world, dev):
     return float(t.item())
 
 
+def headline_config(w):
+    return {"workload": w.name, "M": w.M, "N": w.N, "F": w.F, "T": w.T, "iters": w.iters,
+            "K_nmf": w.K, "array": f"{w.array} r = {w.spacing * 100:.0f} cm" if w.array == "circular"
+            else f"{w.array} {w.spacing * 100:.0f} cm",
+            "step": "IP+EM (Algorithm 1) x iters + Wiener separation (Eq. 39), from the seeded random start",
+            "l2": "inputs larger than L2 (x 262 MB, v 197 MB); L2 also flushed between steps (512 MiB write, "
+                  "untimed)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,10 +791,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-second", action="store_true")
     ap.add_argument("--learned-mixtures", type=int, default=20000)
     ap.add_argument("--profile", action="store_true",
-                    help="only run the IP+EM kernel on the bench mixture's first frequencies tiled to "
+                    help="only run the IP+EM kernel on a workload's first frequencies tiled to "
                          "--profile-F, once untimed then once with --profile-iters iterations (for ncu)")
     ap.add_argument("--profile-F", type=int, default=608)
     ap.add_argument("--profile-iters", type=int, default=5)
@@ -734,11 +809,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    w = WORKLOAD
-    config = {"workload": w.name, "M": w.M, "N": w.N, "F": w.F, "T": w.T, "iters": w.iters,
-              "K_nmf": w.K, "array": f"{w.array} {w.spacing * 100:.0f} cm",
-              "step": "IP+EM x iters + Wiener separation, from the seeded init",
-              "l2": "flushed between steps (512 MiB write, untimed)"}
+    w = HEADLINE
+    config = headline_config(w)
 
     if args.profile:
         run_profile_case(args.profile_F, args.profile_iters, args.profile_workload, args.profile_model,
@@ -748,16 +820,19 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        mix = synth.workload_mixture(w)
+        init = synth.random_init(mix.x, w.N, seed=w.seed)
         cores = os.cpu_count() or 1
-        freqs = list(range(0, w.F, max(1, w.F // (2 * cores))))[: 2 * cores]
-        iters = 25
-        pool = OraclePool(cores)
+        freqs = sample_freqs(w.F, 2 * cores)
+        iters = 2
+        pool = OraclePool(cores, sampled_data(mix.x, init, freqs))
+        rows = list(range(len(freqs)))
         try:
             for _ in range(args.warmup):
-                pool.run(freqs, iters)
+                pool.run(rows, iters)
             times = []
             for _ in range(args.steps):
-                wall, used = pool.run(freqs, iters)
+                wall, used, _ = pool.run(rows, iters)
                 times.append(wall)
         finally:
             pool.close()
@@ -781,34 +856,33 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
+    # inputs first (host work, before any CUDA context): this rank's headline mixture and start
+    mix = synth.workload_mixture(w, rank)
+    x_head = mix.x
+    init_head = synth.random_init(x_head, w.N, seed=w.seed + rank)
+    del mix
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()                   # spawned workers, before any CUDA work
+        cpu = cpu_baseline(w, x_head, init_head)      # spawned workers
     batch_data = None
     if rank == 0 and not args.no_batch:
-        batch_data = generate_batch()          # spawned workers, before any CUDA work
+        batch_data = generate_batch()
 
-    r = run_gpu(args, rank, world, local_rank)
-    batch = None
-    if batch_data is not None:
-        import torch
-        batch = run_batch(*batch_data, torch.device("cuda", local_rank), torch.cuda.current_stream())
-    learned = None
-    if rank == 0 and not args.no_learned:
-        learned = run_learned(args.learned_mixtures)
-    precision = None
-    if rank == 0 and world == 1 and not args.no_precision:
-        precision = precision_report()
-    large = None
-    if rank == 0 and world == 1 and not args.no_large:
-        large = run_large(load_peaks())
+    import torch
+    from paper_2101_08563_gb300 import build
+    torch.cuda.set_device(local_rank)
+    build.build()
+    r = run_headline(args, rank, world, local_rank, w, x_head, init_head)
     if rank != 0:
         return
+    dev = torch.device("cuda", local_rank)
+    second = None if args.no_second else run_second(args, rank, local_rank)
+    batch = run_batch(*batch_data, dev, torch.cuda.current_stream()) if batch_data is not None else None
+    learned = None if args.no_learned else run_learned(args.learned_mixtures)
+    precision = None
+    if world == 1 and not args.no_precision:
+        precision = precision_report(r["outputs"], x_head, init_head)
     peaks = load_peaks()
-    flops = algorithmic_flops_per_bin_iter(w.M, w.N) * w.F * w.T * w.iters
-    em_avg_s = statistics.mean(r["em_ms"]) * 1e-3
-    achieved = flops / em_avg_s / 1e12
-    traffic = em_traffic()
     out = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -816,49 +890,32 @@ def main():
         "dtype_detail": "complex64 bins in FP32; the IP (Eq. 34-35) and the log-likelihood sums in FP64",
         "data": "synthetic (model-generated mixtures, seeded)", "config": config,
         "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "fastfca_em_kernel", "flops_per_bin_iter": algorithmic_flops_per_bin_iter(w.M, w.N),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
-        "roofline_separation": separation_roofline(w, r["sep_ms"], peaks),
+        "roofline": em_roofline(w, r["em_ms"], peaks, "fastfca IP+EM launch (large-bin kernel, M=8)",
+                                em_traffic("fastfca_em_large")),
+        "roofline_separation": separation_roofline(w, r["sep_ms"], peaks,
+                                                   "bst_to_winv_kernel + fastfca_mwf_wide_kernel<8>"),
         "clocks": r["clocks"],
         "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
-                "d2h_bytes_per_step": r["d2h"],
-                "windows": r["e2e_windows"], "note": f"median of 3 windows of {r['e2e_steps']} steps"},
-        "ip_mm": {"algorithm": "IP+MM (Algorithm 2), same mixture and start, 20 iterations (Table I)",
-                  "iters": r["mm_iters"],
-                  "value": w.F * w.T * r["mm_iters"] / (statistics.mean(r["mm_ms"]) * 1e-3), "unit": UNIT,
-                  "launch_ms": statistics.mean(r["mm_ms"]), "loglik": r["mm_ll"],
-                  "ip_em_same_iters": {"value": w.F * w.T * r["mm_iters"] / (statistics.mean(r["em_ms_same"]) * 1e-3),
-                                       "launch_ms": statistics.mean(r["em_ms_same"]), "loglik": r["em_ll_same"]}},
-        "block_input": {"model": "piecewise-stationary FastFCA (Sec. VI-B), IP+EM, blocks of %d frames" % r["blk"],
-                        "B": r["blk"], "launch_ms": statistics.mean(r["blk_ms"]),
-                        "block_iters_per_s": w.F * (w.T // r["blk"]) * w.iters / (statistics.mean(r["blk_ms"]) * 1e-3),
-                        "frame_bin_iters_per_s": w.F * w.T * w.iters / (statistics.mean(r["blk_ms"]) * 1e-3)},
-        "fca_comparison": {
-            model: {"value": w.F * w.T * r["fca_iters"] / (r["fca_ms"][model] * 1e-3), "unit": UNIT,
-                    "iters": r["fca_iters"], "ms": r["fca_ms"][model],
-                    "loglik_per_bin": r["fca_ll"][model],
-                    "update": {"fca": "EM, Eq. 12-13", "fca_mm": "MM with the geometric mean, Eq. 15-17"}[model]}
-            for model in ("fca", "fca_mm")},
-        "fastmnmf": {"model": "FastMNMF (App. C), K = %d bases per source, same mixture" % MNMF_K,
-                     "iters": MNMF_ITERS, "ms": statistics.mean(r["mn_ms"]),
-                     "value": w.F * w.T * MNMF_ITERS / (statistics.mean(r["mn_ms"]) * 1e-3), "unit": UNIT,
-                     "launches_per_iter": 4, "loglik_per_bin": r["mn_ll"]},
+                "d2h_bytes_per_step": r["d2h"], "windows": r["e2e_windows"],
+                "note": f"median of 3 windows of {r['e2e_steps']} steps; two contexts on two streams; the last "
+                        f"step's log-likelihood history equals the device run's: {r['e2e_ll_equal']}"},
         "em_launch_ms": statistics.mean(r["em_ms"]),
+        "separation_ms": statistics.mean(r["sep_ms"]),
         "final_loglik": r["final_ll"],
+        "loglik_per_bin": r["final_ll"] / (w.F * w.T),
+        "images_sum_to_mixture_rel_err": r["images_sum_err"],
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    if precision is not None:
+        out["precision"] = precision
+    if second is not None:
+        out["m4n6"] = second
     if batch is not None:
         out["batch"] = batch
     if learned is not None:
         out["learned_init"] = learned
-    if precision is not None:
-        out["precision"] = precision
-    if large is not None:
-        out["large"] = large
-    if cpu is not None:
-        out["cpu_baseline"] = cpu
     print(json.dumps(out))
 
 

@@ -182,7 +182,7 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
  * [F][T][N][M], host or device, caller-allocated.  Stream-ordered and asynchronous for both:
  * a host c (pinned for a truly asynchronous copy) holds the images once the context's
  * stream has passed the call, e.g. after fastfca_sync, which also reports any kernel
- * status of the filter. */
+ * status of the filter.  c must start on an 8-byte boundary (EINVAL otherwise). */
 fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c);
 
 /* Replaces the mixture of a context with another of the same shape (complex64 [F][T][M],
@@ -288,7 +288,8 @@ void fastfca_batch_destroy(fastfca_batch* batch);
  *   x    complex64  [F][T][M]  device     P    complex128 [F][M][M]  device
  *   lam  float32    [F][M][N]  device     v    float32    [F][N][T]  device
  *   c    complex64  [F][T][N][M] device (output, caller-allocated)
- * x and P must start on a 16-byte boundary (EINVAL otherwise).
+ * x and P must start on a 16-byte boundary, c on an 8-byte and lam and v on a 4-byte boundary
+ * (EINVAL otherwise, checked before any device work).  Any T is accepted.
  *   stream  cudaStream_t (NULL = legacy default stream)
  *
  * Returns EINVAL when F*M*M > FASTFCA_NOALLOC_MAX_FMM, a size is not positive, a pointer is
@@ -297,7 +298,9 @@ void fastfca_batch_destroy(fastfca_batch* batch);
  * it reports no kernel-side numerical status.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress): make that call before any stream capture.
  * All calls share the array, which keeps the last call's contents: calls that overlap on
- * the GPU (other streams, other host threads) race on it and must be serialised. */
+ * the GPU (other streams, other host threads) race on it and must be serialised.  The
+ * looked-up address is kept for the process: do not call this on a device after
+ * cudaDeviceReset. */
 fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t N, const void* x,
                                         const void* P, const float* lam, const float* v, void* c,
                                         void* stream);

@@ -739,6 +739,8 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   fastfca_status st = check_params_usable(ctx);
   if (st) return st;
   if (!c_out) return fail(ctx, FASTFCA_EINVAL, "c is required");
+  if (reinterpret_cast<uintptr_t>(c_out) % 8 != 0)
+    return fail(ctx, FASTFCA_EINVAL, "c must start on an 8-byte boundary (complex64 stores)");
   const fastfca_config& c = ctx->cfg;
   const size_t bytes = sizeof(float2) * (size_t)c.F * ctx->Tf * c.N * c.M;
   const bool dev = is_device_ptr(c_out);

@@ -218,6 +218,14 @@ inline bool fast_ops(int M, int N, FastOps* o) {
   }
 }
 
+// The Wiener-filter kernels (winv, mwf) for (M, N): the frequency-resident filter where the
+// frequency-resident kernels exist, else the wide filter.  Neither filter limits T, so the
+// wide filter's ops are taken for a one-frame shape, which every cluster shape holds.
+inline bool filter_ops(int M, int N, FastOps* o) {
+  if (fast_ops(M, N, o)) return true;
+  return cluster_ops(M, N, 1, o);
+}
+
 // The kernels for one FastFCA problem: the frequency-resident kernel where it applies
 // (M <= 4, N <= 8, T <= 2048), else the cluster kernel (M <= 8, N <= 16, T up to what eight
 // CTAs hold).

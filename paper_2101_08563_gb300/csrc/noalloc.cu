@@ -10,8 +10,11 @@
 // The array lives in device memory of every GPU that loads the library, until the process
 // exits.  Its address is looked up once per device (cudaGetSymbolAddress, with that device
 // current) on the first call made on that device: make that first call before any stream
-// capture.  All calls share the array and it keeps the last call's contents, so calls that
-// overlap on the GPU (on different streams, or from different host threads) race on it.
+// capture.  The address is kept for the life of the process, so the entry point must not be
+// used on a device after cudaDeviceReset (the reset destroys the array with the context).
+// The filter is chosen by (M, N) alone: it has no frame limit, whatever the EM kernels'.
+// All calls share the array and it keeps the last call's contents, so calls that overlap on
+// the GPU (on different streams, or from different host threads) race on it.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -55,8 +58,7 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
   FFCA_TRACE("fastfca_separate_noalloc");
   if (F < 1 || T < 1 || M < 1 || N < 1) return noalloc_fail(FASTFCA_EINVAL, "F, T, M, N must be positive");
   ffca::FastOps ops{};
-  if (!ffca::fast_ops(M, N, &ops) && !ffca::cluster_ops(M, N, T, &ops))
-    return noalloc_fail(FASTFCA_EUNSUPPORTED, "no kernel for this (M, N)");
+  if (!ffca::filter_ops(M, N, &ops)) return noalloc_fail(FASTFCA_EUNSUPPORTED, "no kernel for this (M, N)");
   if ((long long)F * M * M > kNoAllocMaxWinv) {
     char msg[256];
     snprintf(msg, sizeof msg, "F*M*M = %lld exceeds the %d complex values of the static scratch",
@@ -64,10 +66,16 @@ extern "C" fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t
     return noalloc_fail(FASTFCA_EINVAL, msg);
   }
   if (!x || !P || !lam || !v || !c) return noalloc_fail(FASTFCA_EINVAL, "x, P, lam, v and c are required");
-  if (!device_pointer(x) || !device_pointer(P) || !device_pointer(lam) || !device_pointer(v) || !device_pointer(c))
-    return noalloc_fail(FASTFCA_EINVAL, "x, P, lam, v and c must be device pointers");
+  // the kernels load x and P as 16-byte vectors, store c as 8-byte complex values and read
+  // lam and v as floats: checked before anything touches the GPU
   if (reinterpret_cast<uintptr_t>(x) % 16 != 0 || reinterpret_cast<uintptr_t>(P) % 16 != 0)
     return noalloc_fail(FASTFCA_EINVAL, "x and P must start on a 16-byte boundary");
+  if (reinterpret_cast<uintptr_t>(c) % 8 != 0)
+    return noalloc_fail(FASTFCA_EINVAL, "c must start on an 8-byte boundary");
+  if (reinterpret_cast<uintptr_t>(lam) % 4 != 0 || reinterpret_cast<uintptr_t>(v) % 4 != 0)
+    return noalloc_fail(FASTFCA_EINVAL, "lam and v must start on a 4-byte boundary");
+  if (!device_pointer(x) || !device_pointer(P) || !device_pointer(lam) || !device_pointer(v) || !device_pointer(c))
+    return noalloc_fail(FASTFCA_EINVAL, "x, P, lam, v and c must be device pointers");
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

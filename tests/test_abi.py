@@ -64,3 +64,25 @@ def test_allocation_fault_injection_is_host_state(lib):
     fastfca.fail_allocation_after(3)
     fastfca.fail_allocation_after(-1)          # disarmed again: later tests allocate normally
     assert fastfca.live_allocations() == 0
+
+
+def test_noalloc_separation_refuses_misaligned_buffers_before_any_device_work(lib):
+    """fastfca_separate_noalloc checks the alignment its kernels' vector accesses need (x and
+    P 16 bytes, c 8 bytes, lam and v 4 bytes) before it looks at a pointer's memory type or
+    touches a device, so a misaligned buffer is an EINVAL here, on a machine with no GPU,
+    instead of a misaligned-address fault on one.  The addresses are never dereferenced."""
+    F, T, M, N = 4, 64, 6, 8                   # the wide filter's shape class
+    good = [ctypes.c_void_p(0x10000 * (k + 1)) for k in range(5)]    # x, P, lam, v, c
+
+    def call(x, P, lam, v, c):
+        return lib.fastfca_separate_noalloc(F, T, M, N, x, P, lam, v, c, None)
+
+    for k, bad, what in ((4, 0x50004, b"c must start on an 8-byte"), (0, 0x10008, b"x and P"),
+                         (1, 0x20008, b"x and P"), (2, 0x30002, b"lam and v"), (3, 0x40001, b"lam and v")):
+        args = list(good)
+        args[k] = ctypes.c_void_p(bad)
+        assert call(*args) == 1, what                    # FASTFCA_EINVAL
+        assert what in lib.fastfca_last_error(None)
+    # M = 9 has no filter kernel; a zero size is refused
+    assert lib.fastfca_separate_noalloc(F, T, 9, N, *good, None) == 5        # FASTFCA_EUNSUPPORTED
+    assert lib.fastfca_separate_noalloc(0, T, M, N, *good, None) == 1

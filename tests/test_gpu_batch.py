@@ -7,6 +7,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import fastfca as off  # noqa: E402
 from paper_2101_08563_gb300 import synth  # noqa: E402
+from parity import assert_images  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +75,7 @@ def test_batch_tuned_matches_oracle_and_resumes(ff):
         torch.cuda.synchronize()
         cr = np.stack([off.separate_fast(m.x[f], ref["W"][i], ref["L"][i], ref["H"][i])
                        for i, f in enumerate(ref["freqs"])])
-        assert np.linalg.norm(c.cpu().numpy() - cr) / np.linalg.norm(cr) <= 1e-4, b
+        assert_images(c.cpu().numpy(), cr, 1e-4, f"mixture {b}")
     assert np.all(ll2 >= ll1 - 1e-6 * np.abs(ll1))
     bt.close()
 
@@ -102,4 +103,39 @@ def test_batch_mixed_algorithms(ff):
         assert np.array_equal(Pb, Ps) and np.array_equal(lb, ls) and np.array_equal(vb, vs), (b, models[b])
         ref = off.run(m.x, init.P, init.lam, init.v, iters=4, algorithm="mm" if b % 2 else "em")
         assert ll[b] == pytest.approx(ref["ll"][:, -1].sum(), rel=1e-5), b
+    bt.close()
+
+
+def test_batch_bench_schedule_matches_oracle(ff):
+    """The schedule the benchmark's tuner picks for its 64-mixture batch (fine frame buckets,
+    grid share factor 4) on mixtures of the benchmark's frequency count range (F = 64) and
+    frame range (T up to 2000): every mixture's log-likelihood after each iteration, its final
+    parameters and its images against the oracle from the same start."""
+    shapes = [(4, 7, 2000), (3, 6, 1650), (2, 5, 1210), (4, 5, 731), (3, 4, 203), (2, 3, 1999)]
+    F, iters = 64, 3
+    mixes, inits = [], []
+    for b, (M, N, T) in enumerate(shapes):
+        mix = synth.generate_mixture(M, N, F, T, 8, seed=5100 + b, keep_images=False)
+        mixes.append(mix)
+        inits.append(synth.random_init(mix.x, N, seed=5100 + b))
+    xs = [torch.from_numpy(m.x).cuda() for m in mixes]
+    bt = ff.Batch(xs, [N for _, N, _ in shapes])
+    bt.schedule("fine", 4.0)
+    for b, init in enumerate(inits):
+        bt.set_params(b, init.P, init.lam, init.v)
+    lls = [bt.iterate(1)[0] for _ in range(iters)]      # the log-likelihood after each iteration
+    for b, ((M, N, T), m, init) in enumerate(zip(shapes, mixes, inits)):
+        ref = off.run(m.x, init.P, init.lam, init.v, iters=iters)
+        for it in range(iters):
+            tot = ref["ll"][:, it].sum()
+            assert abs(lls[it][b] - tot) <= 1e-5 * abs(tot), (b, it, lls[it][b], tot)
+        P, lam, v = bt.get_params(b)
+        s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
+        s2_ref = np.einsum("fmn,fnt->fmt", ref["L"], ref["H"])
+        assert np.allclose(s2, s2_ref, rtol=2e-3), b
+        c = torch.empty((F, T, N, M), dtype=torch.complex64, device="cuda")
+        bt.separate(b, c)
+        torch.cuda.synchronize()
+        cr = np.stack([off.separate_fast(m.x[f], ref["W"][f], ref["L"][f], ref["H"][f]) for f in range(F)])
+        assert_images(c.cpu().numpy(), cr, 1e-4, f"mixture {b} (M={M}, N={N}, T={T})")
     bt.close()

@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import fastfca as off  # noqa: E402
 from paper_2101_08563_gb300 import synth  # noqa: E402
+from parity import assert_images  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -71,7 +72,7 @@ def test_parity_small(ff, M, N, F, T, iters):
     ll_ref = ref["ll"].sum(axis=0)
     assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
     assert np.allclose(ll_f, ref["ll"][:, -1], rtol=LL_TOL, atol=1e-6)
-    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert_images(c, oracle_images(mix.x, ref), IMG_TOL)
     # sigma^2 = L H and the per-source powers, element-wise (scale-free diagnostics)
     s2 = np.einsum("fmn,fnt->fmt", lam.astype(np.float64), v.astype(np.float64))
     s2_ref = np.einsum("fmn,fnt->fmt", ref["L"], ref["H"])
@@ -87,7 +88,7 @@ def test_trajectory_small_config(ff):
     ref = off.run(mix.x, init.P, init.lam, init.v, iters=w.iters)
     ll_ref = ref["ll"].sum(axis=0)
     assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref))
-    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert_images(c, oracle_images(mix.x, ref), IMG_TOL)
 
 
 def test_full_size_m4n6_sampled_frequencies(ff):
@@ -109,7 +110,7 @@ def test_full_size_m4n6_sampled_frequencies(ff):
     for i, f in enumerate(freqs):
         assert abs(ll_f[f] - ref["ll"][i, -1]) <= LL_TOL * abs(ref["ll"][i, -1]), f
         cr = off.separate_fast(mix.x[f], ref["W"][i], ref["L"][i], ref["H"][i])
-        assert rel(c[f].cpu().numpy(), cr) <= IMG_TOL, f
+        assert_images(c[f:f + 1].cpu().numpy(), cr[None], IMG_TOL, f"f={f}")
     # images sum to the mixture everywhere (Eq. 2)
     xs = c.sum(dim=2)
     assert float((xs - xd).abs().pow(2).sum().sqrt() / xd.abs().pow(2).sum().sqrt()) < 1e-5
@@ -257,7 +258,7 @@ def test_ip_mm_parity(ff, M, N, F, T, iters):
     ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters, algorithm="mm")
     ll_ref = ref["ll"].sum(axis=0)
     assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
-    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert_images(c, oracle_images(mix.x, ref), IMG_TOL)
     assert rel(c.sum(axis=2), mix.x) < 1e-5
 
 
@@ -293,7 +294,7 @@ def test_ip_mm_cluster_parity(ff, M, N, F, T, iters):
     ref = off.run(mix.x, init.P, init.lam, init.v, iters=iters, algorithm="mm")
     ll_ref = ref["ll"].sum(axis=0)
     assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
-    assert rel(c, oracle_images(mix.x, ref)) <= IMG_TOL
+    assert_images(c, oracle_images(mix.x, ref), IMG_TOL)
     assert np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:]))
 
 
@@ -330,7 +331,7 @@ def test_block_input_parity(ff, M, N, F, T, B, algorithm):
     ll_ref = ref["ll"].sum(axis=0)
     assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)
     cr = np.stack([off.separate_blocks(mix.x[f], ref["W"][f], ref["L"][f], ref["H"][f], B) for f in range(F)])
-    assert rel(c, cr) <= IMG_TOL
+    assert_images(c, cr, IMG_TOL)
     assert rel(c.sum(axis=2), mix.x) < 1e-5
 
 

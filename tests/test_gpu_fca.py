@@ -6,6 +6,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import fca as ofca  # noqa: E402
 from paper_2101_08563_gb300 import synth  # noqa: E402
+from parity import assert_images  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +48,7 @@ def test_fca_parity_small(ff, M, N, F, T, iters, algorithm):
     assert np.all(np.abs(ll - ll_ref) <= 1e-5 * np.abs(ll_ref)), (ll, ll_ref)
     assert np.allclose(ll_f, ref["ll"][:, -1], rtol=1e-5)
     c_ref = np.stack([ofca.separate(mix.x[f], ref["R"][i], ref["h"][i]) for i, f in enumerate(ref["freqs"])])
-    assert rel(c, c_ref) <= 1e-4
+    assert_images(c, c_ref, 1e-4)
     assert rel(R, ref["R"]) <= 1e-4
     assert rel(h, ref["h"]) <= 1e-3
     assert rel(c.sum(axis=2), mix.x) < 1e-5

@@ -188,6 +188,71 @@ def test_ip_does_not_decrease_loglik(rng):
             ll = ll_new
 
 
+def sweep_problem(rng, M=4, N=3, J=40):
+    """A problem whose rows of sigma^2 = LH differ in shape, not only in scale (L spans three
+    decades per row), so each Q_m of Eq. 33 is a genuinely different matrix."""
+    x = rand_complex(rng, J, M) * 2.0
+    W = rand_complex(rng, M, M) + 2.0 * np.eye(M)
+    L = np.exp(rng.uniform(-3.5, 3.5, size=(M, N)))
+    H = rng.uniform(0.05, 3.0, size=(N, J))
+    return x, W, L, H
+
+
+def q_by_definition(x, L, H):
+    """Eq. 33 written out frame by frame, with sigma^2_{mj} = sum_n L_mn H_nj (Eq. 28, 38)."""
+    J, M = x.shape
+    Q = np.zeros((M, M, M), complex)
+    for m in range(M):
+        for j in range(J):
+            s2 = sum(L[m, n] * H[n, j] for n in range(L.shape[1]))
+            Q[m] += np.outer(x[j], x[j].conj()) / s2
+        Q[m] /= J
+    return Q
+
+
+def test_ip_sweep_last_column_is_stationary_for_its_own_q(rng):
+    """Eq. 32 after a whole sweep (Algorithm 1's m-loop): the last column was updated with every
+    other column already final, so W^H Q_M w_M = e_M holds exactly for its own Q_M, and for
+    no other Q_m (the rows of sigma^2 differ)."""
+    M = 4
+    x, W0, L, H = sweep_problem(rng, M)
+    Q = q_by_definition(x, L, H)
+    W = ff.ip_sweep(ff.Xhat_from_x(x), W0, L, H)
+    e = np.zeros(M)
+    e[M - 1] = 1.0
+    scale = np.linalg.norm(W) ** 2 * np.linalg.norm(Q[M - 1])
+    assert np.allclose(W.conj().T @ Q[M - 1] @ W[:, M - 1], e, atol=1e-12 * scale)
+    for m in range(M - 1):
+        assert np.linalg.norm(W.conj().T @ Q[m] @ W[:, M - 1] - e) > 1e-3
+
+
+def test_ip_sweep_is_the_sequence_of_column_updates(rng):
+    """The sweep equals M calls of Eq. 34-35 in order, column m with its own Q_m and the W that
+    the previous columns left (each call pinned on its own above); each column satisfies
+    Eq. 32 for its Q_m at the moment it is updated.  A sweep that solved every column with the
+    W it started from, or used one Q for all m, gives a different W."""
+    M = 4
+    x, W0, L, H = sweep_problem(rng, M)
+    Q = q_by_definition(x, L, H)
+    W = W0.copy()
+    for m in range(M):
+        W = ff.ip_update_column(W, Q[m], m)
+        e = np.zeros(M)
+        e[m] = 1.0
+        assert np.allclose(W.conj().T @ Q[m] @ W[:, m], e, atol=1e-10)
+    Wsweep = ff.ip_sweep(ff.Xhat_from_x(x), W0, L, H)
+    assert np.allclose(Wsweep, W, rtol=0, atol=1e-12 * np.abs(W).max())
+    # the slips this pins against give visibly different results on this problem
+    W_stale = W0.copy()
+    for m in range(M):
+        W_stale[:, m] = ff.ip_update_column(W0, Q[m], m)[:, m]
+    W_oneq = W0.copy()
+    for m in range(M):
+        W_oneq = ff.ip_update_column(W_oneq, Q[0], m)
+    for bad in (W_stale, W_oneq):
+        assert np.abs(bad - W).max() > 1e-3 * np.abs(W).max()
+
+
 # ----------------------------------------------------------------------------- NMF EM (Alg. 1)
 def test_phi_is_gaussian_posterior_second_moment(rng):
     """Phi_n of Algorithm 1 is E[|s_n|^2 | y] for y = sum_n s_n, s_n ~ CN(0, S_n) independent:
