@@ -216,6 +216,13 @@ void fastfca_debug_fail_alloc(int64_t n);
  * process (with fastfca_debug_fail_alloc: a failed call leaves this count where it was). */
 int64_t fastfca_debug_live_allocs(void);
 
+/* Kernel choice for IP+EM (Algorithm 1) on the large-bin shapes (M > 4, or N > 8, or T > 2048),
+ * for tests that run both kernels on one shape: 0 (the default) picks by shape, 1 takes the
+ * thread-block-cluster kernel, 2 the one-SM kernel wherever it fits (T <= 4096).  Read when a
+ * context is created; host state, process-wide; any other value is ignored.  Both kernels
+ * compute the same steps in the same order; their results differ by FP32 rounding. */
+void fastfca_debug_large_bin_kernel(int32_t which);
+
 /* ------------------------------------------------------------------------------------------
  * Batches: many independent mixtures (mixed M, N, T) iterated together in one CUDA-graph
  * launch.  Each (mixture, frequency) pair is one work item run by one CTA with the same code

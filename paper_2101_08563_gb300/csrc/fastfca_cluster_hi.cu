@@ -16,6 +16,8 @@ bool cluster_ops(int M, int N, int T, FastOps* o) {
     default: return cluster_ops_lo(M, N, T, o);
   }
   o->max_T = T;
+  o->cluster_c = C;
+  prefer_sm_kernel(M, N, T, o);
   return true;
 }
 

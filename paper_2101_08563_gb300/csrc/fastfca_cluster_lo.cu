@@ -15,6 +15,8 @@ bool cluster_ops_lo(int M, int N, int T, FastOps* o) {
     default: return false;
   }
   o->max_T = T;
+  o->cluster_c = C;
+  prefer_sm_kernel(M, N, T, o);
   return true;
 }
 

@@ -1,0 +1,558 @@
+// FastFCA IP+EM (Algorithm 1) for large bins, one SM per frequency, the per-frame state in
+// tensor memory.
+//
+// The cluster kernel (fastfca_em_cluster.cuh) spreads a frequency's frames over up to eight
+// CTAs because one SM's shared memory cannot hold H, U, sigma^2 and r for thousands of frames.
+// Every Q reduction, the IP hand-off and each of the N source means then cross SMs, and each
+// crossing waits for the slowest of the cluster's CTAs.  This kernel keeps a whole frequency
+// (T <= 4096 frames, M <= 8) on one SM instead, with the SM's 256 KB of tensor memory (TMEM,
+// reached with tcgen05.ld / tcgen05.st) as the per-frame store:
+//
+//   TMEM (all 512 columns, 128 lanes)   sigma^2 and U of every frame (16 32-bit columns per
+//                                       frame: sigma^2_m at 0..7, U_m at 8..15)
+//   shared memory                       r_mt (the n-loop's per-frame ratios) and 1/sigma^2,
+//                                       [frame][8] floats; Q partials; W, B, Q_m in FP64
+//   global memory (L2)                  H = v[f], updated in place row by row; x
+//
+// Thread `tid` of the 512 owns frames t = tid + k * 512, k < 8, and reaches its frames' TMEM
+// columns in its warp's lane quarter (lane 32 (warp % 4) + lane, columns 128 (warp / 4) +
+// 16 k ...).  Every reduction is CTA-local, so no step waits on another SM.
+//
+// The steps, their order and their arithmetic are those of the cluster kernel (see its file
+// comment and fastfca_em.cuh for the equations): pass A (pending H[N-1,:] update, sigma^2 =
+// L H, 1/sigma^2, log-likelihood terms), the Q pass (Eq. 33), the IP (Eq. 34-35, FP64), the
+// U pass (Eq. 37) and the n-loop (Gauss-Seidel over sources, sigma^2 updated by the change of
+// each source's term), with reductions over t in a fixed order.
+#pragma once
+#include "fastfca_em_cluster.cuh"
+
+namespace ffca {
+
+constexpr int kSThreads = 512;               // threads per CTA (one CTA per SM: 512 x 128 registers)
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kSSlots = 8;                   // frames per thread
+constexpr int kSMaxT = kSThreads * kSSlots;  // 4096 frames
+constexpr int kSMaxM = 8;
+constexpr unsigned kSCols = 512;             // TMEM columns allocated: all of them
+constexpr int kSColsPerSlot = 16;            // sigma^2 (8 columns), then U (8 columns)
+
+// ------------------------------------------------------------------ tensor-memory access
+// Allocation by one warp (the address lands in shared memory); the CTA gives up its right to
+// allocate more at once, so no other CTA ever waits on it.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Eight consecutive 32-bit columns of this thread's lane, waited for before returning.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+  v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+
+// Sixteen consecutive columns (sigma^2 then U of one frame), waited for before returning.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&a)[8], float (&b)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+  }
+}
+
+// Stores eight columns and waits until the store is complete, so a later load of the same
+// columns by this thread sees it.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+
+// ------------------------------------------------------------------ shared-memory layout
+template <int M>
+struct SmSmem {
+  static constexpr int NE = M * M;                        // packed Hermitian entries of Q_m
+  static constexpr int V = M * NE;                        // reals of all Q_m
+  static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
+  static constexpr int kWcPad = (M * M + 1) & ~1;
+  // byte offsets (all multiples of 16)
+  static constexpr size_t oR = 0;                                          // float [kSMaxT][8]
+  static constexpr size_t oQw = oR + 4 * (size_t)kSMaxT * 8;               // float [kSWarps/2][V]
+  static constexpr size_t oW = oQw + 4 * (size_t)(kSWarps / 2) * V;       // double2 M*M
+  static constexpr size_t oB = oW + 16 * M * M;                            // double2 M*M
+  static constexpr size_t oQ = oB + 16 * M * M;                            // double2 kQsz
+  static constexpr size_t oV = oQ + 16 * (size_t)kQsz;                     // double2 8 (w_raw)
+  static constexpr size_t oBeta = oV + 16 * 8;                             // double2 8
+  static constexpr size_t oDet = oBeta + 16 * 8;                           // double 4
+  static constexpr size_t oWc = oDet + 32;                                 // float2 kWcPad
+  static constexpr size_t oL = oWc + ((8 * (size_t)kWcPad + 15) & ~(size_t)15);   // float M*kCMaxN
+  static constexpr size_t oRed = oL + 4 * (size_t)M * kCMaxN;             // float 2 x kSWarps x 8
+  static constexpr size_t oLL = oRed + 4 * 2 * kSWarps * 8;                // float kSWarps
+  static constexpr size_t oTmem = oLL + 4 * kSWarps;                       // uint32 TMEM base (+ pad)
+  static constexpr size_t bytes = oTmem + 16;
+};
+
+// Lane jobs of the Q pass: each lane forms two packed entries of x x^H per frame from four
+// shuffled values.  Lanes 0 .. P-1 take the pairs a < b (row-major, P = M(M-1)/2) and give
+// Re and Im of x_a conj(x_b); the next ceil(M/2) lanes take two diagonal entries |x_a|^2,
+// |x_{a+1}|^2 (one when a + 1 = M); the rest are idle.  For M = 8 that is 28 + 4 = 32 lanes.
+template <int M>
+__device__ __forceinline__ void sm_lane_job(int lane, int& a, int& b, int& kind, int& e0, int& e1) {
+  constexpr int P = M * (M - 1) / 2;
+  if (lane < P) {
+    int idx = lane;
+    a = 0;
+    while (idx >= M - 1 - a) { idx -= M - 1 - a; ++a; }
+    b = a + 1 + idx;
+    kind = 0;
+    e0 = M + 2 * lane;
+    e1 = e0 + 1;
+  } else if (lane < P + (M + 1) / 2) {
+    a = 2 * (lane - P);
+    b = (a + 1 < M) ? a + 1 : a;
+    kind = 1;
+    e0 = a;
+    e1 = (a + 1 < M) ? a + 1 : -1;
+  } else {
+    a = 0; b = 0; kind = 2; e0 = -1; e1 = -1;
+  }
+}
+
+#ifdef FFCA_PHASE_CLOCKS
+#define FFCA_SMARK(it, slot)                                                                   \
+  do {                                                                                         \
+    if (p.clocks && f == 0 && tid == 0 && (it) < 8) p.clocks[(it) * 32 + (slot)] = clock64();  \
+  } while (0)
+#else
+#define FFCA_SMARK(it, slot) \
+  do {                       \
+  } while (0)
+#endif
+
+// ------------------------------------------------------------------ the kernel
+// Grid: F CTAs of kSThreads threads, one frequency each; dynamic shared memory
+// SmSmem<M>::bytes.  Requires T <= kSMaxT, N <= kCMaxN.
+template <int M>
+__global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
+  static_assert(M >= 2 && M <= kSMaxM, "M out of range");
+  using SM = SmSmem<M>;
+  constexpr int NE = SM::NE, V = SM::V;
+  constexpr int MP = pow2_ceil(M);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int f = blockIdx.x;
+  const int T = p.T, N = p.N;
+  if (N < 1 || N > kCMaxN || blockDim.x != kSThreads || f >= p.F || T < 1 || T > kSMaxT ||
+      dyn_smem_size() < SM::bytes) {
+    if (tid == 0) atomicOr(p.err, kErrConfig);
+    return;
+  }
+  float* sRr = reinterpret_cast<float*>(smem + SM::oR);          // [t][8]: 1/sigma^2 or r
+  float* sQw = reinterpret_cast<float*>(smem + SM::oQw);
+  double2* sW = reinterpret_cast<double2*>(smem + SM::oW);
+  double2* sB = reinterpret_cast<double2*>(smem + SM::oB);
+  double2* sQ = reinterpret_cast<double2*>(smem + SM::oQ);
+  double2* sV = reinterpret_cast<double2*>(smem + SM::oV);
+  double2* sBeta = reinterpret_cast<double2*>(smem + SM::oBeta);
+  double* sDet = reinterpret_cast<double*>(smem + SM::oDet);
+  float2* sWc = reinterpret_cast<float2*>(smem + SM::oWc);
+  float* sL = reinterpret_cast<float*>(smem + SM::oL);
+  float* sRed = reinterpret_cast<float*>(smem + SM::oRed);       // [parity][warp][8]
+  float* sLL = reinterpret_cast<float*>(smem + SM::oLL);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + SM::oTmem);
+
+  const float2* xf = p.x + (size_t)f * T * M;
+  double2* Pf = p.P + (size_t)f * M * M;
+  float* lamf = p.lam + (size_t)f * M * N;
+  float* vf = p.v + (size_t)f * N * T;
+  const double invT = 1.0 / (double)T;
+  const float invTf = 1.0f / (float)T;
+  const int KF = (T + kSThreads - 1) / kSThreads;          // frame slots in use, the same for every thread
+
+  // ---- tensor memory: warp 0 allocates all 512 columns; the address reaches every thread
+  if (warp == 0) tmem_alloc(sTmem, kSCols);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem = *sTmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+  auto tm_s2 = [&](int k) { return tmem + (uint32_t)(kSColsPerSlot * k); };
+
+  // ---- parameters: L and W in shared memory, B = W^{-H} and |det W|^2 (carried or formed)
+  for (int i = tid; i < M * N; i += kSThreads) sL[i] = lamf[i];
+  for (int i = tid; i < M * M; i += kSThreads) sW[i] = Pf[i];
+  __syncthreads();
+  if (warp == 0) {
+    if (p.b_valid) {
+      for (int e = lane; e < M * M; e += 32) sB[e] = p.Bst[(size_t)f * M * M + e];
+      if (lane == 0) { sDet[0] = p.detst[2 * f]; sDet[1] = p.detst[2 * f + 1]; }
+    } else {
+      for (int e = lane; e < M * M; e += 32) {
+        const int i = e / M, j = e - (e / M) * M;
+        const double2 w = sW[j * M + i];
+        sQ[e] = make_double2(w.x, -w.y);                        // W^H
+      }
+      __syncwarp();
+      double mant, expo;
+      warp_inverse_pivot<M>(sQ, sQ + M * M, sB, mant, expo, lane, p.err);
+      if (lane == 0) { sDet[0] = mant; sDet[1] = expo; }
+    }
+    for (int e = lane; e < M * M; e += 32) {
+      const int a = e / M, m = e - (e / M) * M;
+      const double2 w = sW[a * M + m];
+      sWc[m * M + a] = make_float2((float)w.x, (float)-w.y);
+    }
+  }
+  __syncthreads();
+
+  // U = |W^H x|^2 of this thread's frames into TMEM (columns 8..15 of each frame slot)
+  auto pass_U = [&]() {
+#pragma unroll
+    for (int k = 0; k < kSSlots; ++k) {
+      if (k >= KF) break;                                  // uniform over the CTA
+      const int t = tid + k * kSThreads;
+      float u[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) u[m] = 0.f;
+      if (t < T) {
+        float2 xv[M];
+        const float2* src = xf + (size_t)t * M;
+        if constexpr (M % 2 == 0) {
+#pragma unroll
+          for (int a = 0; a < M; a += 2) {
+            const float4 q4 = __ldg(reinterpret_cast<const float4*>(src + a));
+            xv[a] = make_float2(q4.x, q4.y);
+            xv[a + 1] = make_float2(q4.z, q4.w);
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xv[a], y);
+          u[m] = fmaf(y.x, y.x, y.y * y.y);
+        }
+      }
+      tmem_st8(tm_s2(k) + 8, u);
+    }
+  };
+
+  auto ll_from_sum = [&](double s) {
+    const double logdet = (double)__logf((float)sDet[0]) + sDet[1] * kLn2;
+    return (double)T * logdet - s - (double)M * (double)T * kLnPi;
+  };
+
+  // lane job of the Q pass
+  int ja, jb, jkind, je0, je1;
+  sm_lane_job<M>(lane, ja, jb, jkind, je0, je1);
+
+  float coef[M], Lold[M], Lnew[M], hprev[kSSlots];
+#pragma unroll
+  for (int m = 0; m < M; ++m) { coef[m] = 0.f; Lold[m] = 0.f; Lnew[m] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < kSSlots; ++k) hprev[k] = 0.f;
+  int rpar = 0;
+
+  if (p.n_iter == 0) {          // the log-likelihood of the incoming W needs its U
+    pass_U();
+    __syncthreads();
+  }
+
+#pragma unroll 1
+  for (int it = 0;; ++it) {
+    const bool have_ll = (it > 0) || (p.n_iter == 0);
+    const bool do_iter = it < p.n_iter;
+    FFCA_SMARK(it, 0);
+
+    // ---- pass A: pending H[N-1,:] update, sigma^2 = L H into TMEM, 1/sigma^2 into sRr,
+    // log-likelihood terms
+    {
+      float llp = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < kSSlots; ++k) {
+        if (k >= KF) break;                                // uniform over the CTA
+        const int t = tid + k * kSThreads;
+        float u[8], s2v[8];
+        if (have_ll) tmem_ld8(tm_s2(k) + 8, u);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) s2v[m] = 1.f;
+        if (t < T) {
+          float* rr = sRr + (size_t)t * 8;
+          if (it > 0) {
+            const float4 r0 = *reinterpret_cast<const float4*>(rr);
+            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
+            hprev[k] *= g;
+            vf[(size_t)(N - 1) * T + t] = hprev[k];
+          }
+          float h[kCMaxN];
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n) {
+            if (n < N) h[n] = (it > 0 && n == N - 1) ? hprev[k] : vf[(size_t)n * T + t];
+            else h[n] = 0.f;
+          }
+          float rs[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) rs[m] = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int n = 0; n < kCMaxN; ++n)
+              if (n < N) s2 = fmaf(sL[m * N + n], h[n], s2);
+            bad |= !(s2 > 0.f && s2 < INFINITY);
+            rs[m] = fast_rcp(s2);
+            s2v[m] = s2;
+            if (have_ll) llp += fmaf(u[m], rs[m], __logf(s2));
+          }
+          *reinterpret_cast<float4*>(rr) = make_float4(rs[0], rs[1], rs[2], rs[3]);
+          *reinterpret_cast<float4*>(rr + 4) = make_float4(rs[4], rs[5], rs[6], rs[7]);
+        }
+        tmem_st8(tm_s2(k), s2v);
+      }
+      if (bad) atomicOr(p.err, kErrSigma);
+      llp = warp_sum(llp);
+      if (lane == 0) sLL[warp] = llp;
+    }
+    __syncthreads();          // the Q pass reads 1/sigma^2 of frames other threads wrote
+    FFCA_SMARK(it, 1);
+    if (have_ll && tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kSWarps; ++w) s += (double)sLL[w];
+      const double ll = ll_from_sum(s);
+      if (it > 0 && p.ll_hist) p.ll_hist[(size_t)f * p.ll_stride + it - 1] = ll;
+      if (!do_iter && p.ll_last) p.ll_last[f] = ll;
+    }
+    if (!do_iter) break;
+
+    // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33).  Warp w takes a contiguous block of
+    // frames; one load instruction brings 4 frames x 8 channels (lane 8 f + a holds x_a of
+    // frame f); each lane forms its two entries from four shuffled values and accumulates
+    // them for every m with the weights 1/sigma^2 read as two broadcast float4.
+    {
+      float acc[M][2];
+#pragma unroll
+      for (int m = 0; m < M; ++m) { acc[m][0] = 0.f; acc[m][1] = 0.f; }
+      const int per = (T + kSWarps - 1) / kSWarps;
+      const int fb = warp * per, fe = min(fb + per, T);
+      const int lf = lane >> 3, la = lane & 7;
+#pragma unroll 1
+      for (int base = fb; base < fe; base += 32) {
+        float2 xr[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int fr = base + 4 * k + lf;
+          xr[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+          for (int fi = 0; fi < 4; ++fi) {
+            const int fr = base + 4 * k + fi;          // warp-uniform
+            if (fr >= fe) break;
+            const float ax = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + ja);
+            const float ay = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + ja);
+            const float bx = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + jb);
+            const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + jb);
+            const float v0 = (jkind == 0) ? fmaf(ax, bx, ay * by) : fmaf(ax, ax, ay * ay);
+            const float v1 = (jkind == 0) ? fmaf(ay, bx, -ax * by) : fmaf(bx, bx, by * by);
+            const float4 w0 = *reinterpret_cast<const float4*>(sRr + (size_t)fr * 8);
+            const float4 w1 = *reinterpret_cast<const float4*>(sRr + (size_t)fr * 8 + 4);
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              acc[m][0] = fmaf(wv[m], v0, acc[m][0]);
+              acc[m][1] = fmaf(wv[m], v1, acc[m][1]);
+            }
+          }
+        }
+      }
+      // per-warp partials, summed in a fixed order: warp w + 8 onto warp w, then warps 0..7
+      if (warp >= kSWarps / 2) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          if (je0 >= 0) sQw[(warp - kSWarps / 2) * V + m * NE + je0] = acc[m][0];
+          if (je1 >= 0) sQw[(warp - kSWarps / 2) * V + m * NE + je1] = acc[m][1];
+        }
+      }
+      __syncthreads();
+      if (warp < kSWarps / 2) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          if (je0 >= 0) sQw[warp * V + m * NE + je0] = acc[m][0] + sQw[warp * V + m * NE + je0];
+          if (je1 >= 0) sQw[warp * V + m * NE + je1] = acc[m][1] + sQw[warp * V + m * NE + je1];
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < V; i += kSThreads) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < kSWarps / 2; ++w) s += sQw[w * V + i];
+        const double qd = (double)s * invT;
+        const int m = i / NE, e = i - m * NE;
+        int a, b, kind;
+        decode_entry<M>(e, a, b, kind);
+        double2* Qm = sQ + m * M * M;
+        if (kind == 0) Qm[a * M + a] = make_double2(qd, 0.0);
+        else if (kind == 1) { Qm[a * M + b].x = qd; Qm[b * M + a].x = qd; }
+        else { Qm[a * M + b].y = qd; Qm[b * M + a].y = -qd; }
+      }
+      __syncthreads();
+    }
+    FFCA_SMARK(it, 2);
+
+    // ---- IP (FP64): the M inverses Q_m^{-1}, then the column loop of Eq. 34-35, on the four
+    // FP64 warps (one per sub-partition); the other warps wait at the barrier below
+    if (tid < kCIpThreads) {
+      cluster_hpd_inverses<M>(sQ, 0, 1, tid, p.err);
+      FFCA_SMARK(it, 3);
+      cluster_ip_columns<M>(sQ, sW, sB, sWc, sDet, sV, sBeta, tid, p.err);
+    }
+    __syncthreads();
+    FFCA_SMARK(it, 4);
+
+    // ---- U = |W^H x|^2 (Eq. 37) into TMEM; each thread later reads only its own frames
+    pass_U();
+    FFCA_SMARK(it, 5);
+
+    // ---- NMF EM sweep over sources (Gauss-Seidel); pass n first applies source n-1's H
+    // update and its change of sigma^2
+#pragma unroll 1
+    for (int n = 0; n < N; ++n) {
+      float Ln[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
+      float acc[MP];
+#pragma unroll
+      for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+#pragma unroll
+      for (int k = 0; k < kSSlots; ++k) {
+        if (k >= KF) break;                                // uniform over the CTA
+        const int t = tid + k * kSThreads;
+        float s2v[8], u[8];
+        tmem_ld16(tm_s2(k), s2v, u);
+        if (t < T) {
+          float* rr = sRr + (size_t)t * 8;
+          if (n > 0) {
+            const float4 r0 = *reinterpret_cast<const float4*>(rr);
+            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
+            const float hold = hprev[k];
+            const float hnew = hold * g;
+            vf[(size_t)(n - 1) * T + t] = hnew;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              // sigma^2 <- sigma^2 - L H + L' H' (one rounding: fma), never below the new term
+              const float s2 = fmaf(Lnew[m], hnew, fmaf(-Lold[m], hold, s2v[m]));
+              s2v[m] = fmaxf(s2, Lnew[m] * hnew);
+            }
+          }
+          const float hn = vf[(size_t)n * T + t];
+          hprev[k] = hn;
+          float rv[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) rv[m] = 0.f;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const float rs = fast_rcp(s2v[m]);
+            const float G = Ln[m] * hn * rs;
+            const float rr_ = fmaf(G, fmaf(u[m], rs, -1.f), 1.f);
+            rv[m] = rr_;
+            acc[m] += rr_;
+          }
+          *reinterpret_cast<float4*>(rr) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+          *reinterpret_cast<float4*>(rr + 4) = make_float4(rv[4], rv[5], rv[6], rv[7]);
+        }
+        if (n > 0) tmem_st8(tm_s2(k), s2v);
+      }
+      // per-warp sums of r, then every warp adds the 16 warps' sums in the same order: lane
+      // (m, q) adds warps q, q + 4, q + 8, q + 12, and two shuffles finish
+      warp_reduce_scatter<MP>(acc, lane);
+      float* rb = sRed + rpar * (kSWarps * 8);
+      if ((lane * MP) % 32 == 0 && (lane * MP) / 32 < M) rb[warp * 8 + (lane * MP) / 32] = acc[0];
+      __syncthreads();
+      float tot_l = 0.f;
+      {
+        const int m = lane >> 2, q = lane & 3;
+        if (m < M) {
+#pragma unroll
+          for (int w = q; w < kSWarps; w += 4) tot_l += rb[w * 8 + m];
+        }
+        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 1);
+        tot_l += __shfl_xor_sync(0xffffffffu, tot_l, 2);
+      }
+      rpar ^= 1;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float mean = __shfl_sync(0xffffffffu, tot_l, 4 * m) * invTf;
+        Lold[m] = Ln[m];
+        Lnew[m] = Ln[m] * mean;
+        coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+        if (tid == m) sL[m * N + n] = Lnew[m];
+      FFCA_SMARK(it, 6 + (n < 25 ? n : 25));
+    }
+    __syncthreads();          // sL of the last source before pass A reads it
+  }
+
+  // ---- write back the per-frequency parameters (H is already in global memory)
+  __syncthreads();
+  for (int i = tid; i < M * N; i += kSThreads) lamf[i] = sL[i];
+  for (int i = tid; i < M * M; i += kSThreads) {
+    Pf[i] = sW[i];
+    p.Bst[(size_t)f * M * M + i] = sB[i];
+  }
+  if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
+
+  // ---- release the tensor memory once every thread's accesses are complete
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(*sTmem, kSCols);
+}
+
+}  // namespace ffca

@@ -1,0 +1,30 @@
+// One-SM IP+EM kernels (fastfca_em_sm.cuh) for M = 5..8 microphones, and the host switch that
+// tests use to run either large-bin kernel on one shape.
+#include <atomic>
+
+#include "../../include/fastfca.h"
+#include "launch.cuh"
+
+namespace ffca {
+
+namespace {
+std::atomic<int> g_large_bin_kernel{0};
+}
+
+int large_bin_kernel_choice() { return g_large_bin_kernel.load(); }
+
+EmLaunch sm_em_launcher(int M) {
+  switch (M) {
+    case 5: return &launch_em_sm<5>;
+    case 6: return &launch_em_sm<6>;
+    case 7: return &launch_em_sm<7>;
+    case 8: return &launch_em_sm<8>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace ffca
+
+extern "C" void fastfca_debug_large_bin_kernel(int32_t which) {
+  if (which >= 0 && which <= 2) ffca::g_large_bin_kernel.store(which);
+}

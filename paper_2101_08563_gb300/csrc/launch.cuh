@@ -2,6 +2,7 @@
 #pragma once
 #include "fastfca_em.cuh"
 #include "fastfca_em_cluster.cuh"
+#include "fastfca_em_sm.cuh"
 #include "fastfca_mwf.cuh"
 
 namespace ffca {
@@ -26,6 +27,7 @@ struct FastOps {
   int (*em_blocks_per_sm[2])(int bd);
   int max_T;
   bool cluster;          // the cluster kernel (any T it fits, runtime N); no batch form
+  int cluster_c;         // the cluster kernel's CTAs per frequency for this shape (0: not cluster)
 };
 
 // Threads for a frequency of T frames: whole warps, kSlots frames each.
@@ -116,6 +118,7 @@ FastOps make_fast_ops() {
   o.em_blocks_per_sm[1] = &em_blocks_per_sm<M, N, true>;
   o.max_T = kMaxThreads * kSlots;
   o.cluster = false;
+  o.cluster_c = 0;
   return o;
 }
 
@@ -166,6 +169,38 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// The one-SM IP+EM kernel (fastfca_em_sm.cuh): one CTA of kSThreads per frequency.
+template <int M>
+cudaError_t launch_em_sm(const EmArgs& a, cudaStream_t s) {
+  if (a.T < 1 || a.T > kSMaxT || a.N < 1 || a.N > kCMaxN) return cudaErrorInvalidConfiguration;
+  const size_t smem = SmSmem<M>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(fastfca_em_sm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fastfca_em_sm_kernel<M><<<a.F, kSThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Which kernel takes IP+EM for the large-bin shapes: 0 picks by shape (below), 1 forces the
+// cluster kernel, 2 the one-SM kernel where it fits.  Host state, set by
+// fastfca_debug_large_bin_kernel (for tests that cover both kernels on one shape).
+int large_bin_kernel_choice();
+
+// The one-SM IP+EM launcher for M (null if not built for that M) (fastfca_sm.cu).
+using EmLaunch = cudaError_t (*)(const EmArgs&, cudaStream_t);
+EmLaunch sm_em_launcher(int M);
+
+// Gives IP+EM on a large-bin shape to the one-SM kernel where it fits (T <= kSMaxT) and the
+// cluster kernel would spread a frequency over two or more CTAs (at fewer frames two cluster
+// CTAs share an SM, i.e. two frequencies per SM, against one for the one-SM kernel).  The
+// other models and the block input stay on the cluster kernel.
+inline void prefer_sm_kernel(int M, int N, int T, FastOps* o) {
+  const int choice = large_bin_kernel_choice();
+  if (choice == 1 || T > kSMaxT || N < 1 || N > kCMaxN) return;
+  const EmLaunch fn = sm_em_launcher(M);
+  if (!fn) return;
+  if (choice == 2 || o->cluster_c >= 2) o->em = fn;
+}
+
 template <int M>
 cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
                             float2* c, int F, int T, int N, int B, cudaStream_t s) {
@@ -196,6 +231,7 @@ FastOps make_cluster_ops() {
   o.em_blocks_per_sm[1] = nullptr;
   o.max_T = 0;                     // set by cluster_ops for the N at hand
   o.cluster = true;
+  o.cluster_c = 0;                 // set by cluster_ops
   return o;
 }
 

@@ -51,6 +51,7 @@ _SIGNATURES = {
     "fastfca_version": (ctypes.c_char_p, []),
     "fastfca_debug_fail_alloc": (None, [ctypes.c_int64]),
     "fastfca_debug_live_allocs": (ctypes.c_int64, []),
+    "fastfca_debug_large_bin_kernel": (None, [ctypes.c_int32]),
     "fastfca_separate_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 _P, _P, _P, _P, _P, _P]),
     "fastfca_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]),
@@ -332,6 +333,12 @@ def fail_allocation_after(n: int):
     """Fault injection: after n more device allocations by the library succeed, the next one
     fails as an out of memory would (one-shot; n < 0 disarms)."""
     load().fastfca_debug_fail_alloc(int(n))
+
+
+def large_bin_kernel(which: str):
+    """Kernel for IP+EM on the large-bin shapes in contexts created from now on: "auto" (by
+    shape), "cluster" (thread-block clusters) or "sm" (one SM per frequency, T <= 4096)."""
+    load().fastfca_debug_large_bin_kernel({"auto": 0, "cluster": 1, "sm": 2}[which])
 
 
 def live_allocations() -> int:

@@ -1,7 +1,7 @@
 // Host-side check of the launch geometry the library computes, for every shape it accepts:
 // threads per CTA, frames per thread and the shared memory each kernel asks for, against the
 // GB300 limits (227 KB of dynamic shared memory per CTA, 48 KB of static, 1024 threads,
-// clusters of at most 8).  It includes the library's own launch headers and calls their
+// clusters of at most 8, 512 tensor-memory columns per SM).  It includes the library's own launch headers and calls their
 // host functions; it makes no CUDA call, so it runs without a GPU.  Prints "ok" or the first
 // violation (and exits 1).
 #include <cstdio>
@@ -79,6 +79,28 @@ void check_cluster() {
   if (kCThreads > 1024 || kCThreads % 32) fail("cluster threads", M, 0, 0, kCThreads);
 }
 
+// one-SM IP+EM kernel: T <= kSMaxT frames, kSThreads threads, every thread's frames inside
+// its kSSlots TMEM slots, every TMEM column it touches inside the kSCols allocated, 1/sigma^2
+// and r rows inside the shared array, one CTA per SM (the registers of kSThreads threads at
+// the 128-register cap fill the 64K register file, so no second CTA can contend for TMEM)
+template <int M>
+void check_sm() {
+  if (kSThreads % 128 || kSThreads > 1024) fail("sm threads", M, 0, 0, kSThreads);
+  if (kSThreads * 128 != 65536) fail("sm registers do not fill the SM", M, 0, 0, kSThreads * 128);
+  if (SmSmem<M>::bytes > kDynMax) fail("sm smem", M, 0, 0, SmSmem<M>::bytes);
+  if (SmSmem<M>::oQw < sizeof(float) * 8 * (size_t)kSMaxT) fail("sm r rows", M, 0, 0, SmSmem<M>::oQw);
+  for (int T = 1; T <= kSMaxT; ++T) {
+    const int KF = (T + kSThreads - 1) / kSThreads;
+    if (KF > kSSlots || KF * kSThreads < T) fail("sm frame slots", M, 0, T, KF);
+    const int warps = kSThreads / 32;
+    const int max_col = 128 * ((warps - 1) >> 2) + kSColsPerSlot * (KF - 1) + 15;
+    if (max_col >= (int)kSCols || 128 * (warps / 4) > (int)kSCols) fail("sm tmem column", M, 0, T, max_col);
+    // the Q pass: warp w takes frames [w per, min((w + 1) per, T)); together they cover [0, T)
+    const int per = (T + warps - 1) / warps;
+    if (warps * per < T) fail("sm q blocks", M, 0, T, per);
+  }
+}
+
 template <int M, int N>
 void check_frequency_resident() {
   check_em<M, N>();
@@ -111,6 +133,10 @@ int main() {
   check_cluster<6>();
   check_cluster<7>();
   check_cluster<8>();
+  check_sm<5>();
+  check_sm<6>();
+  check_sm<7>();
+  check_sm<8>();
   if (failures) {
     std::printf("%d violations\n", failures);
     return 1;

@@ -23,12 +23,16 @@ IMG_TOL = 1e-4
 
 @pytest.fixture(scope="module")
 def ff():
+    """The library with IP+EM on the large-bin shapes forced onto the cluster kernel (the
+    one-SM kernel takes some of these shapes by default; tests/test_gpu_sm.py covers it)."""
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     from paper_2101_08563_gb300 import build, fastfca
     build.build()
     fastfca.load()
-    return fastfca
+    fastfca.large_bin_kernel("cluster")
+    yield fastfca
+    fastfca.large_bin_kernel("auto")
 
 
 def rel(a, b):
@@ -122,28 +126,25 @@ def test_cluster_loglik_resume_and_monotone(ff):
     b.close()
 
 
-def test_large_workload_sampled_frequencies(ff):
+def test_large_workload_sampled_frequencies(ff, large_workload):
     """The large single instance at full size (M=8 circular 5 cm, N=12, F=1025, T=4000, K=16,
-    50 iterations) in the launch configuration the kernel picks for it (clusters of 8 CTAs);
-    the oracle follows three frequencies."""
-    w = synth.WORKLOADS["large"]
-    mix = synth.generate_mixture(w.M, w.N, w.F, w.T, w.K, seed=w.seed, array=w.array, spacing=w.spacing,
-                                 keep_images=False)
-    init = synth.random_init(mix.x, w.N, seed=w.seed)
-    xd = torch.from_numpy(mix.x).cuda()
+    50 iterations) on the cluster kernel (clusters of 8 CTAs); the oracle follows three
+    frequencies."""
+    w, x, init = large_workload
+    xd = torch.from_numpy(x).cuda()
     sep = ff.Separator(xd, w.N)
     sep.set_params(init.P, init.lam, init.v)
     hist = sep.iterate(w.iters)
     _, ll_f = sep.loglik(per_f=True)
     freqs = [1, 512, 1024]
-    ref = off.run(mix.x, init.P, init.lam, init.v, iters=w.iters, freqs=freqs)
+    ref = off.run(x, init.P, init.lam, init.v, iters=w.iters, freqs=freqs)
     c = torch.empty((w.F, w.T, w.N, w.M), dtype=torch.complex64, device="cuda")
     sep.separate(c)
     sep.close()
     assert np.all(np.diff(hist) >= -1e-6 * np.abs(hist[1:]))
     for i, f in enumerate(freqs):
         assert abs(ll_f[f] - ref["ll"][i, -1]) <= LL_TOL * abs(ref["ll"][i, -1]), f
-        cr = off.separate_fast(mix.x[f], ref["W"][i], ref["L"][i], ref["H"][i])
+        cr = off.separate_fast(x[f], ref["W"][i], ref["L"][i], ref["H"][i])
         assert_images(c[f:f + 1].cpu().numpy(), cr[None], IMG_TOL, f"f={f}")
     xs = c.sum(dim=2)
     assert float((xs - xd).abs().pow(2).sum().sqrt() / xd.abs().pow(2).sum().sqrt()) < 1e-5
