@@ -890,7 +890,7 @@ def main():
         "dtype_detail": "complex64 bins in FP32; the IP (Eq. 34-35) and the log-likelihood sums in FP64",
         "data": "synthetic (model-generated mixtures, seeded)", "config": config,
         "gpu_launches": 3 * args.steps,
-        "roofline": em_roofline(w, r["em_ms"], peaks, "fastfca IP+EM launch (large-bin kernel, M=8)",
+        "roofline": em_roofline(w, r["em_ms"], peaks, "fastfca_em_sm_kernel<8> (one CTA per frequency, sigma^2 and U in TMEM)",
                                 em_traffic("fastfca_em_large")),
         "roofline_separation": separation_roofline(w, r["sep_ms"], peaks,
                                                    "bst_to_winv_kernel + fastfca_mwf_wide_kernel<8>"),

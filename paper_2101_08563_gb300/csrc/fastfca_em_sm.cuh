@@ -59,20 +59,26 @@ __device__ __forceinline__ void tmem_fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Eight consecutive 32-bit columns of this thread's lane, waited for before returning.
+// Loads and stores of this thread's TMEM lane.  Tensor memory is outside the C++ memory
+// model: the data moves only through the asm operands, so the asm carries no memory clobber
+// and the compiler may move ordinary global and shared accesses across it (volatile keeps the
+// TMEM accesses in program order among themselves).  Each load waits for its data (wait::ld)
+// and each store for its completion (wait::st) inside the same asm, so an operand is never
+// read early and a later load of the same columns sees the store.
+//
+// Eight consecutive 32-bit columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-      : "r"(taddr)
-      : "memory");
+      : "r"(taddr));
   v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
   v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
 }
 
-// Sixteen consecutive columns (sigma^2 then U of one frame), waited for before returning.
+// Sixteen consecutive columns (sigma^2 then U of one frame).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&a)[8], float (&b)[8]) {
   uint32_t r[16];
   asm volatile(
@@ -81,8 +87,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&a)[8], float (
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
+      : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     a[i] = __uint_as_float(r[i]);
@@ -90,16 +95,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&a)[8], float (
   }
 }
 
-// Stores eight columns and waits until the store is complete, so a later load of the same
-// columns by this thread sees it.
+// Eight columns stored, without waiting: a pass stores each of its slots once and ends with
+// tmem_wait_st, before any later load of those columns.
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
-      "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
       "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-      : "memory");
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
 }
+
+// Waits until every TMEM store of this thread has completed.
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 
 // ------------------------------------------------------------------ shared-memory layout
 template <int M>
@@ -117,9 +123,11 @@ struct SmSmem {
   static constexpr size_t oV = oQ + 16 * (size_t)kQsz;                     // double2 8 (w_raw)
   static constexpr size_t oBeta = oV + 16 * 8;                             // double2 8
   static constexpr size_t oDet = oBeta + 16 * 8;                           // double 4
-  static constexpr size_t oWc = oDet + 32;                                 // float2 kWcPad
+  static constexpr size_t oPiv = oDet + 32;                                // double 8 (pivot reciprocals)
+  static constexpr size_t oWc = oPiv + 64;                                 // float2 kWcPad
   static constexpr size_t oL = oWc + ((8 * (size_t)kWcPad + 15) & ~(size_t)15);   // float M*kCMaxN
-  static constexpr size_t oRed = oL + 4 * (size_t)M * kCMaxN;             // float 2 x kSWarps x 8
+  static constexpr size_t oLt = oL + 4 * (size_t)M * kCMaxN;              // float [kCMaxN][8]: L transposed
+  static constexpr size_t oRed = oLt + 4 * (size_t)kCMaxN * 8;            // float 2 x kSWarps x 8
   static constexpr size_t oLL = oRed + 4 * 2 * kSWarps * 8;                // float kSWarps
   static constexpr size_t oTmem = oLL + 4 * kSWarps;                       // uint32 TMEM base (+ pad)
   static constexpr size_t bytes = oTmem + 16;
@@ -148,6 +156,59 @@ __device__ __forceinline__ void sm_lane_job(int lane, int& a, int& b, int& kind,
     e1 = (a + 1 < M) ? a + 1 : -1;
   } else {
     a = 0; b = 0; kind = 2; e0 = -1; e1 = -1;
+  }
+}
+
+// In-place inverses of the M matrices Q_m (HPD, row-major, consecutive) by the four FP64 warps
+// (threads 0..127), Gauss-Jordan without pivoting as in cluster_hpd_inverses, with every
+// entry spread over the warps the same way.  The reciprocal of each step's pivot is formed
+// once per matrix, by the thread that wrote that pivot in the step before (or by thread m
+// for step 0), and read from shared memory; on this part every FP64 warp instruction holds its
+// sub-partition's FP64 unit for ~68 cycles, so the per-entry reciprocals that this removes
+// were about a third of the inversion's FP64 instructions.  A non-positive pivot sets
+// kErrQPivot.
+template <int M>
+__device__ void sm_hpd_inverses(double2* Q, double* sPiv, int tid, int* err) {
+  constexpr int E = M * M;
+  constexpr int kSl = (M * E + kCIpThreads - 1) / kCIpThreads;
+  const int me = (tid & 31) * 4 + (tid >> 5);
+  auto pivot_rcp = [&](double d, int m) {
+    const float df = (float)d;
+    const bool ok = df > 0.f && df < INFINITY;
+    if (!ok) atomicOr(err, kErrQPivot);
+    sPiv[m] = rcp_pos_f64(ok ? d : 1.0);
+  };
+  if (tid < M) pivot_rcp(Q[tid * E].x, tid);
+  ip_bar();
+  for (int k = 0; k < M; ++k) {
+    double2 nv[kSl];
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      const int i = me + s * kCIpThreads;
+      if (i < M * E) {
+        const int mo = i / E, e = i - mo * E;
+        const double2* A = Q + mo * E;
+        const int r = e / M, cc = e - r * M;
+        const double rd = sPiv[mo];
+        const double2 aij = A[e], aik = A[r * M + k], akj = A[k * M + cc];
+        const double2 base = (r != k && cc != k) ? aij : make_double2(0.0, 0.0);
+        const double2 c1 = (r != k) ? aik : make_double2(-1.0, 0.0);
+        const double2 c2 = (cc != k) ? akj : make_double2(1.0, 0.0);
+        const double2 t = make_double2(c1.x * rd, c1.y * rd);
+        nv[s] = make_double2(fma(t.y, c2.y, fma(-t.x, c2.x, base.x)), fma(-t.y, c2.x, fma(-t.x, c2.y, base.y)));
+      }
+    }
+    ip_bar();
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      const int i = me + s * kCIpThreads;
+      if (i < M * E) {
+        const int mo = i / E, e = i - mo * E;
+        Q[mo * E + e] = nv[s];
+        if (k + 1 < M && e == (k + 1) * (M + 1)) pivot_rcp(nv[s].x, mo);
+      }
+    }
+    ip_bar();
   }
 }
 
@@ -188,8 +249,10 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
   double2* sV = reinterpret_cast<double2*>(smem + SM::oV);
   double2* sBeta = reinterpret_cast<double2*>(smem + SM::oBeta);
   double* sDet = reinterpret_cast<double*>(smem + SM::oDet);
+  double* sPiv = reinterpret_cast<double*>(smem + SM::oPiv);
   float2* sWc = reinterpret_cast<float2*>(smem + SM::oWc);
   float* sL = reinterpret_cast<float*>(smem + SM::oL);
+  float* sLt = reinterpret_cast<float*>(smem + SM::oLt);         // [n][8] = L[m][n], zero for m >= M
   float* sRed = reinterpret_cast<float*>(smem + SM::oRed);       // [parity][warp][8]
   float* sLL = reinterpret_cast<float*>(smem + SM::oLL);
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + SM::oTmem);
@@ -212,6 +275,10 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
 
   // ---- parameters: L and W in shared memory, B = W^{-H} and |det W|^2 (carried or formed)
   for (int i = tid; i < M * N; i += kSThreads) sL[i] = lamf[i];
+  for (int i = tid; i < kCMaxN * 8; i += kSThreads) {
+    const int n = i >> 3, m = i & 7;
+    sLt[i] = (n < N && m < M) ? lamf[m * N + n] : 0.f;
+  }
   for (int i = tid; i < M * M; i += kSThreads) sW[i] = Pf[i];
   __syncthreads();
   if (warp == 0) {
@@ -263,13 +330,24 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           float2 y = make_float2(0.f, 0.f);
+          if constexpr (M % 2 == 0) {           // row m starts on a 16-byte boundary
+            const float4* row = reinterpret_cast<const float4*>(sWc + m * M);
 #pragma unroll
-          for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xv[a], y);
+            for (int a = 0; a < M; a += 2) {
+              const float4 w2 = row[a / 2];
+              y = cfmaf(make_float2(w2.x, w2.y), xv[a], y);
+              y = cfmaf(make_float2(w2.z, w2.w), xv[a + 1], y);
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < M; ++a) y = cfmaf(sWc[m * M + a], xv[a], y);
+          }
           u[m] = fmaf(y.x, y.x, y.y * y.y);
         }
       }
       tmem_st8(tm_s2(k) + 8, u);
     }
+    tmem_wait_st();
   };
 
   auto ll_from_sum = [&](double s) {
@@ -304,6 +382,23 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
     {
       float llp = 0.f;
       bool bad = false;
+      if (it > 0) {                      // the last source's H update, for every slot first
+#pragma unroll
+        for (int k = 0; k < kSSlots; ++k) {
+          const int t = tid + k * kSThreads;
+          if (k < KF && t < T) {
+            const float* rr = sRr + (size_t)t * 8;
+            const float4 r0 = *reinterpret_cast<const float4*>(rr);
+            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
+            hprev[k] *= g;
+            vf[(size_t)(N - 1) * T + t] = hprev[k];
+          }
+        }
+      }
 #pragma unroll
       for (int k = 0; k < kSSlots; ++k) {
         if (k >= KF) break;                                // uniform over the CTA
@@ -314,31 +409,34 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
         for (int m = 0; m < 8; ++m) s2v[m] = 1.f;
         if (t < T) {
           float* rr = sRr + (size_t)t * 8;
-          if (it > 0) {
-            const float4 r0 = *reinterpret_cast<const float4*>(rr);
-            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
-            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            float g = 0.f;
-#pragma unroll
-            for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
-            hprev[k] *= g;
-            vf[(size_t)(N - 1) * T + t] = hprev[k];
-          }
+          // H[n][t] for every source (the pending row from the register), all loads in flight
+          // together; then sigma^2_m = sum_n L[m][n] H[n][t] source by source against rows of
+          // L^T (two float4 per source, eight independent accumulations)
           float h[kCMaxN];
 #pragma unroll
           for (int n = 0; n < kCMaxN; ++n) {
             if (n < N) h[n] = (it > 0 && n == N - 1) ? hprev[k] : vf[(size_t)n * T + t];
             else h[n] = 0.f;
           }
+          float acc2[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) acc2[m] = 0.f;
+#pragma unroll
+          for (int n = 0; n < kCMaxN; ++n) {
+            if (n < N) {
+              const float4 l0 = *reinterpret_cast<const float4*>(sLt + n * 8);
+              const float4 l1 = *reinterpret_cast<const float4*>(sLt + n * 8 + 4);
+              const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+              for (int m = 0; m < M; ++m) acc2[m] = fmaf(lv[m], h[n], acc2[m]);
+            }
+          }
           float rs[8];
 #pragma unroll
           for (int m = 0; m < 8; ++m) rs[m] = 0.f;
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            float s2 = 0.f;
-#pragma unroll
-            for (int n = 0; n < kCMaxN; ++n)
-              if (n < N) s2 = fmaf(sL[m * N + n], h[n], s2);
+            const float s2 = acc2[m];
             bad |= !(s2 > 0.f && s2 < INFINITY);
             rs[m] = fast_rcp(s2);
             s2v[m] = s2;
@@ -349,6 +447,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
         }
         tmem_st8(tm_s2(k), s2v);
       }
+      tmem_wait_st();
       if (bad) atomicOr(p.err, kErrSigma);
       llp = warp_sum(llp);
       if (lane == 0) sLL[warp] = llp;
@@ -443,7 +542,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
     // ---- IP (FP64): the M inverses Q_m^{-1}, then the column loop of Eq. 34-35, on the four
     // FP64 warps (one per sub-partition); the other warps wait at the barrier below
     if (tid < kCIpThreads) {
-      cluster_hpd_inverses<M>(sQ, 0, 1, tid, p.err);
+      sm_hpd_inverses<M>(sQ, sPiv, tid, p.err);
       FFCA_SMARK(it, 3);
       cluster_ip_columns<M>(sQ, sW, sB, sWc, sDet, sV, sBeta, tid, p.err);
     }
@@ -464,6 +563,13 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       float acc[MP];
 #pragma unroll
       for (int m = 0; m < MP; ++m) acc[m] = 0.f;
+      // this source's H row for all of the thread's frames, loads in flight together
+      float hrow[kSSlots];
+#pragma unroll
+      for (int k = 0; k < kSSlots; ++k) {
+        const int t = tid + k * kSThreads;
+        hrow[k] = (k < KF && t < T) ? vf[(size_t)n * T + t] : 0.f;
+      }
 #pragma unroll
       for (int k = 0; k < kSSlots; ++k) {
         if (k >= KF) break;                                // uniform over the CTA
@@ -484,12 +590,14 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
             vf[(size_t)(n - 1) * T + t] = hnew;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-              // sigma^2 <- sigma^2 - L H + L' H' (one rounding: fma), never below the new term
-              const float s2 = fmaf(Lnew[m], hnew, fmaf(-Lold[m], hold, s2v[m]));
-              s2v[m] = fmaxf(s2, Lnew[m] * hnew);
+              // sigma^2 <- sigma^2 - L H + L' H', never below the new term: the rest of the sum,
+              // clamped at zero, plus the new term in one fma (rounding is monotone, so this is
+              // max(fma(L', H', rest), L' H') bit for bit)
+              const float rest = fmaxf(fmaf(-Lold[m], hold, s2v[m]), 0.f);
+              s2v[m] = fmaf(Lnew[m], hnew, rest);
             }
           }
-          const float hn = vf[(size_t)n * T + t];
+          const float hn = hrow[k];
           hprev[k] = hn;
           float rv[8];
 #pragma unroll
@@ -507,6 +615,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
         }
         if (n > 0) tmem_st8(tm_s2(k), s2v);
       }
+      tmem_wait_st();
       // per-warp sums of r, then every warp adds the 16 warps' sums in the same order: lane
       // (m, q) adds warps q, q + 4, q + 8, q + 12, and two shuffles finish
       warp_reduce_scatter<MP>(acc, lane);
@@ -533,7 +642,10 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       }
 #pragma unroll
       for (int m = 0; m < M; ++m)
-        if (tid == m) sL[m * N + n] = Lnew[m];
+        if (tid == m) {
+          sL[m * N + n] = Lnew[m];
+          sLt[n * 8 + m] = Lnew[m];
+        }
       FFCA_SMARK(it, 6 + (n < 25 ? n : 25));
     }
     __syncthreads();          // sL of the last source before pass A reads it
@@ -549,6 +661,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
   if (tid == 0) { p.detst[2 * f] = sDet[0]; p.detst[2 * f + 1] = sDet[1]; }
 
   // ---- release the tensor memory once every thread's accesses are complete
+  tmem_wait_st();
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
