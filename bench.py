@@ -328,6 +328,20 @@ def load_peaks():
         return {}
 
 
+_FP32_MEASURED = {}
+
+
+def measured_fp32_tflops():
+    """The FP32 FMA rate of this GPU from the library's probe (measured once per process)."""
+    if "tf" not in _FP32_MEASURED:
+        try:
+            from paper_2101_08563_gb300 import fastfca
+            _FP32_MEASURED["tf"] = fastfca.measure_fp32_fma(2000)
+        except Exception:
+            _FP32_MEASURED["tf"] = None
+    return _FP32_MEASURED["tf"]
+
+
 def em_roofline(w, em_ms, peaks, kernel, traffic):
     """The IP+EM launch against both ceilings: FP32 arithmetic (algorithmic flops per
     bin-iteration, unit-count peak) and HBM (the streaming schedule's 16 M + 8 N bytes per
@@ -340,7 +354,10 @@ def em_roofline(w, em_ms, peaks, kernel, traffic):
     hbm = peaks.get("hbm_gbs")
     alu = {"achieved": flops * units / s / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
            "frac": flops * units / s / 1e12 / FP32_PEAK_TFLOPS, "flops_per_bin_iter": flops,
-           "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"}
+           "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)",
+           "peak_measured_tflops": measured_fp32_tflops(),
+           "peak_measured_source": "fastfca_measure_fp32_fma: 8 independent FMA chains per thread, 2048 threads "
+                                   "on every SM, CUDA events"}
     mem = {"achieved": by * units / s / 1e9, "peak": hbm, "unit": "GB/s",
            "frac": (by * units / s / 1e9 / hbm) if hbm else None, "bytes_per_bin_iter": by,
            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",

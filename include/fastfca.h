@@ -223,6 +223,29 @@ int64_t fastfca_debug_live_allocs(void);
  * compute the same steps in the same order; their results differ by FP32 rounding. */
 void fastfca_debug_large_bin_kernel(int32_t which);
 
+/* Failure injection for the cluster kernel's bounded waits (the wait of each source's exchange
+ * between the CTAs of a cluster, Algorithm 1's n-loop): spins > 0 sets the number of polls
+ * after which an exchange is reported as timed out, 0 restores the kernel's default (2^20).
+ * A timed-out exchange sets a status bit, so the next synchronising call returns ECUDA and the
+ * context stays failed; the kernel keeps waiting, bounded by the default, for the bytes
+ * already on their way, so no memory is written after the wait.  Read at each launch; host
+ * state, process-wide. */
+void fastfca_debug_cluster_wait_limit(int32_t spins);
+
+/* Measurement, not part of the method: the FP32 FMA rate of the current GPU in TFLOP/s (2 flops
+ * per FMA), from one timed launch of iters x 128 dependent-free FMAs per thread on every SM at
+ * full occupancy, after one untimed launch.  The denominator of the arithmetic roofline the
+ * benchmark reports beside the one from unit counts.  Synchronises; allocates a small buffer.
+ * EINVAL for iters < 1 or a null tflops; ECUDA on a failed launch. */
+fastfca_status fastfca_measure_fp32_fma(int32_t iters, double* tflops, void* stream);
+
+/* Check, not part of the method: the library's FP64 reciprocal and reciprocal square root of a
+ * positive normal number (an FP32 hardware approximation refined by one Newton-Raphson step,
+ * used by the IP of Eq. 34-35) applied to n device doubles x into device rcp and rsqrt, so a
+ * test can compare them with CUDA's correctly rounded 1/x and 1/sqrt(x).  Asynchronous on the
+ * stream; EINVAL for n < 1 or a null pointer. */
+fastfca_status fastfca_debug_f64_reciprocals(int32_t n, const double* x, double* rcp, double* rsqrt, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Batches: many independent mixtures (mixed M, N, T) iterated together in one CUDA-graph
  * launch.  Each (mixture, frequency) pair is one work item run by one CTA with the same code

@@ -27,7 +27,7 @@ REPORT_PATH = os.path.join(BUILD_DIR, "ptxas_report.json")
 
 SOURCES = ["fastfca_m4_hi.cu", "fastfca_m4.cu", "fastfca_m3.cu", "fastfca_m2.cu", "api.cu", "fca_ops.cu", "noalloc.cu", "batch.cu",
            "fastmnmf_m2.cu", "fastmnmf_m3.cu", "fastmnmf_m4.cu", "fastmnmf_common.cu",
-           "learn.cu", "fastfca_cluster_lo.cu", "fastfca_cluster_hi.cu", "fastfca_sm.cu"]
+           "learn.cu", "fastfca_cluster_lo.cu", "fastfca_cluster_hi.cu", "fastfca_sm.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", os.path.join(ROOT, "include")]

@@ -120,6 +120,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
   return ok != 0;
 }
 
+// The non-blocking form: true if the phase of this parity has completed, at once.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* m, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"((uint32_t)__cvta_generic_to_shared(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr),
                "r"(__float_as_uint(v)), "r"(remote_mbar)
@@ -127,7 +138,8 @@ __device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint
 }
 
 // Status bit: a cluster exchange waited longer than its limit (the kernel continues; the
-// host reports the launch as failed).
+// host reports the launch as failed).  kMbarSpinLimit is the default limit; a launch may pass
+// a smaller one (ClusterArgs::wait_limit) to make the time-out path run in a test.
 constexpr int kErrClusterWait = 64;
 constexpr int kMbarSpinLimit = 1 << 20;
 
@@ -322,6 +334,7 @@ struct ClusterArgs {
   EmArgs e;
   float* mn_u;
   float* mn_ab;
+  int wait_limit;       // spins of a cluster exchange before it is reported as timed out
 };
 
 template <int M, bool MM = false, bool BL = false, bool MN = false>
@@ -893,11 +906,26 @@ __global__ void __launch_bounds__(kCThreads, 2) fastfca_em_cluster_kernel(Cluste
           for (int c = 0; c < C; ++c)
             st_async_f32(dsmem_addr(slot, (unsigned)c), acc[0], dsmem_addr(&sMbar[npar], (unsigned)c));
         }
-        {
+        if (ca.wait_limit <= 0) {
           int spins = 0;
           while (!mbar_try_wait(&sMbar[npar], nphase[npar]) && ++spins < kMbarSpinLimit) {
           }
           if (spins >= kMbarSpinLimit && lane == 0) atomicOr(p.err, kErrClusterWait);
+        } else {
+          // an injected limit (failure tests): wait_limit non-blocking polls, then the exchange
+          // is reported as timed out and the wait continues, bounded by the default limit, so
+          // the peers' pushes still land in this phase (the barrier's phase count stays in
+          // step and nothing is written into this CTA's shared memory after it moves on)
+          int spins = 0;
+          bool done = false;
+          while (!(done = mbar_test_wait(&sMbar[npar], nphase[npar])) && ++spins < ca.wait_limit) {
+          }
+          if (!done) {
+            if (lane == 0) atomicOr(p.err, kErrClusterWait);
+            int drain = 0;
+            while (!mbar_try_wait(&sMbar[npar], nphase[npar]) && ++drain < kMbarSpinLimit) {
+            }
+          }
         }
         nphase[npar] ^= 1u;
         float tot_l = 0.f;

@@ -1,5 +1,5 @@
-// One-SM IP+EM kernels (fastfca_em_sm.cuh) for M = 5..8 microphones, and the host switch that
-// tests use to run either large-bin kernel on one shape.
+// One-SM IP+EM kernels (fastfca_em_sm.cuh) for M = 5..8 microphones, and the host switches that
+// tests use to run either large-bin kernel on one shape and to make a cluster exchange time out.
 #include <atomic>
 
 #include "../../include/fastfca.h"
@@ -9,9 +9,11 @@ namespace ffca {
 
 namespace {
 std::atomic<int> g_large_bin_kernel{0};
+std::atomic<int> g_cluster_wait_limit{0};
 }
 
 int large_bin_kernel_choice() { return g_large_bin_kernel.load(); }
+int cluster_wait_limit() { return g_cluster_wait_limit.load(); }
 
 EmLaunch sm_em_launcher(int M) {
   switch (M) {
@@ -27,4 +29,8 @@ EmLaunch sm_em_launcher(int M) {
 
 extern "C" void fastfca_debug_large_bin_kernel(int32_t which) {
   if (which >= 0 && which <= 2) ffca::g_large_bin_kernel.store(which);
+}
+
+extern "C" void fastfca_debug_cluster_wait_limit(int32_t spins) {
+  ffca::g_cluster_wait_limit.store(spins > 0 ? spins : 0);
 }

@@ -27,7 +27,7 @@ cudaError_t launch_mnmf_cluster(const MnmfArgs& m, cudaStream_t s) {
   a.ll_stride = m.ll_stride;
   a.N = m.N;
   a.clocks = nullptr;
-  ClusterArgs ca{a, m.u, m.ab};
+  ClusterArgs ca{a, m.u, m.ab, cluster_wait_limit()};
   int C = 0;
   size_t smem = 0;
   if (!cluster_shape<M>(a.T, a.N, &C, &smem)) return cudaErrorInvalidConfiguration;

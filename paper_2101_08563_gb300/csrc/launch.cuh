@@ -123,6 +123,10 @@ FastOps make_fast_ops() {
 }
 
 // ---------------------------------------------------------------- cluster kernel (large bins)
+// Spins a cluster exchange of the cluster kernel waits before it reports a time-out (0: the
+// kernel's default).  Host state, set by fastfca_debug_cluster_wait_limit (fastfca_sm.cu).
+int cluster_wait_limit();
+
 // Shared memory available to one CTA, alone on an SM or as one of two.
 constexpr size_t kSmemOnePerSm = 227 * 1024;
 constexpr size_t kSmemTwoPerSm = 113 * 1024;
@@ -164,7 +168,7 @@ cudaError_t launch_em_cluster(const EmArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  ClusterArgs ca{a, nullptr, nullptr};
+  ClusterArgs ca{a, nullptr, nullptr, cluster_wait_limit()};
   e = cudaLaunchKernelEx(&cfg, fastfca_em_cluster_kernel<M, MM, BL>, ca);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -52,6 +52,10 @@ _SIGNATURES = {
     "fastfca_debug_fail_alloc": (None, [ctypes.c_int64]),
     "fastfca_debug_live_allocs": (ctypes.c_int64, []),
     "fastfca_debug_large_bin_kernel": (None, [ctypes.c_int32]),
+    "fastfca_debug_cluster_wait_limit": (None, [ctypes.c_int32]),
+    "fastfca_measure_fp32_fma": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "fastfca_debug_f64_reciprocals": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_void_p]),
     "fastfca_separate_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 _P, _P, _P, _P, _P, _P]),
     "fastfca_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]),
@@ -339,6 +343,22 @@ def large_bin_kernel(which: str):
     """Kernel for IP+EM on the large-bin shapes in contexts created from now on: "auto" (by
     shape), "cluster" (thread-block clusters) or "sm" (one SM per frequency, T <= 4096)."""
     load().fastfca_debug_large_bin_kernel({"auto": 0, "cluster": 1, "sm": 2}[which])
+
+
+def cluster_wait_limit(spins: int):
+    """Failure injection: a cluster exchange of the cluster kernel is reported as timed out
+    after `spins` polls (0 restores the default)."""
+    load().fastfca_debug_cluster_wait_limit(int(spins))
+
+
+def measure_fp32_fma(iters: int = 2000, stream=None) -> float:
+    """The FP32 FMA rate of the current GPU in TFLOP/s (one timed launch over every SM)."""
+    lib = load()
+    out = ctypes.c_double()
+    st = lib.fastfca_measure_fp32_fma(int(iters), ctypes.byref(out), ctypes.c_void_p(stream or _default_stream()))
+    if st != 0:
+        raise FastFCAError(st, lib.fastfca_last_error(None).decode())
+    return float(out.value)
 
 
 def live_allocations() -> int:

@@ -325,3 +325,37 @@ def test_net_create_survives_every_failed_allocation(ff):
     from paper_2101_08563_gb300 import learned as L
     n = sweep_allocations(ff, lambda: L.InitNet(3, 4, max_rows=64, max_T=256, seed=1))
     assert n >= 15
+
+
+def test_cluster_exchange_timeout_is_reported_and_a_fresh_context_works(ff):
+    """The cluster kernel's one wait on other CTAs (each source's exchange in the n-loop) made
+    to run out: with the limit set to one non-blocking poll, an exchange that is not complete
+    at the first poll is reported (status bit -> ECUDA, and the context stays failed).  The
+    kernel then waits, bounded, for the bytes already sent, so nothing is left in flight; a
+    context created after the limit is restored computes what the oracle computes."""
+    M, N, F, T = 8, 12, 2, 2003                   # clusters of four CTAs
+    mix = synth.generate_mixture(M, N, F, T, 8, seed=71, array="circular", spacing=0.05)
+    init = synth.random_init(mix.x, N, seed=71)
+    xd = torch.from_numpy(mix.x).cuda()
+    ff.large_bin_kernel("cluster")
+    try:
+        ff.cluster_wait_limit(1)
+        sep = ff.Separator(xd, N)
+        sep.set_params(init.P, init.lam, init.v)
+        with pytest.raises(ff.FastFCAError, match="ECUDA") as e:
+            sep.iterate(2)
+        assert "timed out" in str(e.value)
+        with pytest.raises(ff.FastFCAError, match="ECUDA"):
+            sep.iterate(1)                          # failed for good
+        sep.close()
+        ff.cluster_wait_limit(0)
+        fresh = ff.Separator(xd, N)
+        fresh.set_params(init.P, init.lam, init.v)
+        ll = fresh.iterate(2)
+        fresh.close()
+    finally:
+        ff.cluster_wait_limit(0)
+        ff.large_bin_kernel("auto")
+    ref = off.run(mix.x, init.P, init.lam, init.v, iters=2)
+    ll_ref = ref["ll"].sum(axis=0)
+    assert np.all(np.abs(ll - ll_ref) <= LL_TOL * np.abs(ll_ref)), (ll, ll_ref)

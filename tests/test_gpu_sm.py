@@ -181,3 +181,29 @@ def test_large_workload_full_size_on_the_sm_kernel(ff, large_workload):
         assert_images(c[f:f + 1].cpu().numpy(), cr[None], IMG_TOL, f"f={f}")
     xs = c.sum(dim=2)
     assert float((xs - xd).abs().pow(2).sum().sqrt() / xd.abs().pow(2).sum().sqrt()) < 1e-5
+
+
+def test_frequency_ranges_run_alone_equal_the_whole_run(ff):
+    """The premise of sharding one mixture over ranks by frequency (shard.py): each frequency
+    is computed on its own, so contexts on contiguous frequency ranges give, bit for bit, the
+    rows of one context on the whole mixture, and their per-iteration log-likelihoods sum to
+    the whole run's."""
+    from paper_2101_08563_gb300 import shard
+    M, N, F, T = 8, 12, 5, 2500
+    mix = mixture(M, N, F, T, 31)
+    init = synth.random_init(mix.x, N, seed=31)
+    xd = torch.from_numpy(mix.x).cuda()
+    whole = ff.Separator(xd, N)
+    whole.set_params(init.P, init.lam, init.v)
+    ll_whole = whole.iterate(3)
+    Pw, lw, vw = whole.get_params()
+    whole.close()
+    ll_sum = np.zeros(3)
+    for f0, f1 in shard.frequency_ranges(F, 2):
+        part = ff.Separator(xd[f0:f1].clone(), N)
+        part.set_params(init.P[f0:f1], init.lam[f0:f1], init.v[f0:f1])
+        ll_sum += part.iterate(3)
+        P, lam, v = part.get_params()
+        part.close()
+        assert np.array_equal(P, Pw[f0:f1]) and np.array_equal(lam, lw[f0:f1]) and np.array_equal(v, vw[f0:f1])
+    assert np.allclose(ll_sum, ll_whole, rtol=1e-12, atol=0)

@@ -44,6 +44,11 @@ def test_every_open_ended_loop_is_bounded():
     assert re.search(r"if \(i >= n_items\) return;", loop[:400])
     spins = [m.group(0) for _, t in sources() for m in re.finditer(r"while \(!mbar_try_wait[^\n]*", strip_comments(t))]
     assert spins and all("kMbarSpinLimit" in s for s in spins)
+    # the injected-limit form polls without blocking, against the launch's limit
+    polls = [m.group(0) for _, t in sources()
+             for m in re.finditer(r"while \(!\(done = mbar_test_wait[^\n]*", strip_comments(t))]
+    assert polls and all("wait_limit" in s for s in polls)
+
 
 
 def test_device_allocations_go_through_the_counted_allocator():
