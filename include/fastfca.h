@@ -182,7 +182,9 @@ fastfca_status fastfca_loglik(fastfca_ctx* ctx, double* ll_total, double* ll_per
  * [F][T][N][M], host or device, caller-allocated.  Stream-ordered and asynchronous for both:
  * a host c (pinned for a truly asynchronous copy) holds the images once the context's
  * stream has passed the call, e.g. after fastfca_sync, which also reports any kernel
- * status of the filter.  c must start on an 8-byte boundary (EINVAL otherwise). */
+ * status of the filter.  c must start on an 8-byte boundary (EINVAL otherwise).  For a host c
+ * the images pass through a device staging buffer of the same size, which the context makes
+ * on the first such call (ENOMEM if that fails) and keeps until fastfca_destroy. */
 fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c);
 
 /* Replaces the mixture of a context with another of the same shape (complex64 [F][T][M],

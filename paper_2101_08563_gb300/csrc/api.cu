@@ -86,6 +86,7 @@ struct fastfca_ctx {
   float* lam = nullptr;
   float* v = nullptr;
   float2* winv = nullptr;        // W^{-H} complex64 scratch for the filter
+  float2* c_stage = nullptr;     // device staging of a separation into a host c (made on first use)
   double2* Bst = nullptr;        // W^{-H} (FP64) carried between FastFCA launches
   double* detst = nullptr;       // |det W|^2 as (mantissa, exponent) per frequency
   int b_valid = 0;               // Bst/detst match the current P
@@ -267,6 +268,7 @@ void free_all(fastfca_ctx* c) {
   ffca::dev_free(c->lam);
   ffca::dev_free(c->v);
   ffca::dev_free(c->winv);
+  ffca::dev_free(c->c_stage);
   ffca::dev_free(c->Bst);
   ffca::dev_free(c->detst);
   ffca::dev_free(c->tb);
@@ -745,10 +747,11 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   const size_t bytes = sizeof(float2) * (size_t)c.F * ctx->Tf * c.N * c.M;
   const bool dev = is_device_ptr(c_out);
   float2* dst = static_cast<float2*>(c_out);
-  float2* tmp = nullptr;
   if (!dev) {
-    CK(ctx, ffca::dev_malloc_async(&tmp, bytes, ctx->stream), "c staging alloc");
-    dst = tmp;
+    // the staging buffer is made on the first separation into host memory and kept: a
+    // stream of host separations then allocates nothing per call
+    if (!ctx->c_stage) CK(ctx, ffca::dev_malloc(&ctx->c_stage, bytes), "c staging alloc");
+    dst = ctx->c_stage;
   }
   cudaError_t e = cudaSuccess;
   if (fastfca_family(c.model) || c.model == FASTFCA_MODEL_FASTMNMF) {
@@ -769,15 +772,11 @@ fastfca_status fastfca_separate(fastfca_ctx* ctx, void* c_out) {
   } else {
     e = ctx->fops.mwf(ctx->x, ctx->R, ctx->h, dst, c.F, c.T, ctx->err, ctx->stream);
   }
-  if (e != cudaSuccess) {
-    if (tmp) ffca::dev_free_async(tmp, ctx->stream);
-    return cuda_fail(ctx, e, "separate launch");
-  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "separate launch");
   if (!dev) {
-    // stream-ordered download and release of the staging buffer: no synchronisation here,
-    // kernel status is collected by the next synchronising call
-    e = cudaMemcpyAsync(c_out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-    ffca::dev_free_async(tmp, ctx->stream);
+    // stream-ordered download: no synchronisation here, kernel status is collected by the
+    // next synchronising call
+    e = cudaMemcpyAsync(c_out, ctx->c_stage, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "c download");
   }
   return FASTFCA_OK;

@@ -11,7 +11,10 @@
 //   TMEM (all 512 columns, 128 lanes)   sigma^2 and U of every frame (16 32-bit columns per
 //                                       frame: sigma^2_m at 0..7, U_m at 8..15)
 //   shared memory                       r_mt (the n-loop's per-frame ratios) and 1/sigma^2,
-//                                       [frame][8] floats; Q partials; W, B, Q_m in FP64
+//                                       in two planes [frame][4] (m < 4, m >= 4), so a warp's
+//                                       float4 accesses of consecutive frames are conflict-free;
+//                                       the last source row of H per frame slot; Q partials;
+//                                       W, B, Q_m in FP64
 //   global memory (L2)                  H = v[f], updated in place row by row; x
 //
 // Thread `tid` of the 512 owns frames t = tid + k * 512, k < 8, and reaches its frames' TMEM
@@ -115,8 +118,9 @@ struct SmSmem {
   static constexpr int kQsz = (M * M * M > 3 * M * M) ? M * M * M : 3 * M * M;
   static constexpr int kWcPad = (M * M + 1) & ~1;
   // byte offsets (all multiples of 16)
-  static constexpr size_t oR = 0;                                          // float [kSMaxT][8]
-  static constexpr size_t oQw = oR + 4 * (size_t)kSMaxT * 8;               // float [kSWarps/2][V]
+  static constexpr size_t oR = 0;                                          // float [2][kSMaxT][4]
+  static constexpr size_t oHp = oR + 4 * (size_t)kSMaxT * 8;               // float [kSSlots][kSThreads]
+  static constexpr size_t oQw = oHp + 4 * (size_t)kSSlots * kSThreads;     // float [kSWarps/2][V]
   static constexpr size_t oW = oQw + 4 * (size_t)(kSWarps / 2) * V;       // double2 M*M
   static constexpr size_t oB = oW + 16 * M * M;                            // double2 M*M
   static constexpr size_t oQ = oB + 16 * M * M;                            // double2 kQsz
@@ -241,7 +245,8 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
     if (tid == 0) atomicOr(p.err, kErrConfig);
     return;
   }
-  float* sRr = reinterpret_cast<float*>(smem + SM::oR);          // [t][8]: 1/sigma^2 or r
+  float* sRr = reinterpret_cast<float*>(smem + SM::oR);          // [2][t][4]: 1/sigma^2 or r
+  float* sHp = reinterpret_cast<float*>(smem + SM::oHp);         // [k][tid]: H of the last source done
   float* sQw = reinterpret_cast<float*>(smem + SM::oQw);
   double2* sW = reinterpret_cast<double2*>(smem + SM::oW);
   double2* sB = reinterpret_cast<double2*>(smem + SM::oB);
@@ -305,6 +310,20 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
   __syncthreads();
 
   // U = |W^H x|^2 of this thread's frames into TMEM (columns 8..15 of each frame slot)
+  auto load_x = [&](int t, float2 (&xv)[M]) {
+    const float2* src = xf + (size_t)t * M;
+    if constexpr (M % 2 == 0) {
+#pragma unroll
+      for (int a = 0; a < M; a += 2) {
+        const float4 q4 = __ldg(reinterpret_cast<const float4*>(src + a));
+        xv[a] = make_float2(q4.x, q4.y);
+        xv[a + 1] = make_float2(q4.z, q4.w);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
+    }
+  };
   auto pass_U = [&]() {
 #pragma unroll
     for (int k = 0; k < kSSlots; ++k) {
@@ -315,18 +334,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       for (int m = 0; m < 8; ++m) u[m] = 0.f;
       if (t < T) {
         float2 xv[M];
-        const float2* src = xf + (size_t)t * M;
-        if constexpr (M % 2 == 0) {
-#pragma unroll
-          for (int a = 0; a < M; a += 2) {
-            const float4 q4 = __ldg(reinterpret_cast<const float4*>(src + a));
-            xv[a] = make_float2(q4.x, q4.y);
-            xv[a + 1] = make_float2(q4.z, q4.w);
-          }
-        } else {
-#pragma unroll
-          for (int a = 0; a < M; ++a) xv[a] = __ldg(src + a);
-        }
+        load_x(t, xv);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
           float2 y = make_float2(0.f, 0.f);
@@ -359,11 +367,20 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
   int ja, jb, jkind, je0, je1;
   sm_lane_job<M>(lane, ja, jb, jkind, je0, je1);
 
-  float coef[M], Lold[M], Lnew[M], hprev[kSSlots];
+  float coef[M], Lold[M], Lnew[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) { coef[m] = 0.f; Lold[m] = 0.f; Lnew[m] = 0.f; }
-#pragma unroll
-  for (int k = 0; k < kSSlots; ++k) hprev[k] = 0.f;
+  // the eight ratios of frame t (two conflict-free float4) and the H of a thread's slot k
+  auto r_load = [&](int t, float (&v)[8]) {
+    const float4 a = *reinterpret_cast<const float4*>(sRr + 4 * t);
+    const float4 b = *reinterpret_cast<const float4*>(sRr + 4 * kSMaxT + 4 * t);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  };
+  auto r_store = [&](int t, const float (&v)[8]) {
+    *reinterpret_cast<float4*>(sRr + 4 * t) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(sRr + 4 * kSMaxT + 4 * t) = make_float4(v[4], v[5], v[6], v[7]);
+  };
+  float* hprev = sHp + tid;                                      // hprev[k * kSThreads]
   int rpar = 0;
 
   if (p.n_iter == 0) {          // the log-likelihood of the incoming W needs its U
@@ -387,15 +404,14 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
         for (int k = 0; k < kSSlots; ++k) {
           const int t = tid + k * kSThreads;
           if (k < KF && t < T) {
-            const float* rr = sRr + (size_t)t * 8;
-            const float4 r0 = *reinterpret_cast<const float4*>(rr);
-            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
-            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float rv[8];
+            r_load(t, rv);
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
-            hprev[k] *= g;
-            vf[(size_t)(N - 1) * T + t] = hprev[k];
+            const float hn = hprev[k * kSThreads] * g;
+            hprev[k * kSThreads] = hn;
+            vf[(size_t)(N - 1) * T + t] = hn;
           }
         }
       }
@@ -408,14 +424,13 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) s2v[m] = 1.f;
         if (t < T) {
-          float* rr = sRr + (size_t)t * 8;
           // H[n][t] for every source (the pending row from the register), all loads in flight
           // together; then sigma^2_m = sum_n L[m][n] H[n][t] source by source against rows of
           // L^T (two float4 per source, eight independent accumulations)
           float h[kCMaxN];
 #pragma unroll
           for (int n = 0; n < kCMaxN; ++n) {
-            if (n < N) h[n] = (it > 0 && n == N - 1) ? hprev[k] : vf[(size_t)n * T + t];
+            if (n < N) h[n] = (it > 0 && n == N - 1) ? hprev[k * kSThreads] : vf[(size_t)n * T + t];
             else h[n] = 0.f;
           }
           float acc2[8];
@@ -442,8 +457,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
             s2v[m] = s2;
             if (have_ll) llp += fmaf(u[m], rs[m], __logf(s2));
           }
-          *reinterpret_cast<float4*>(rr) = make_float4(rs[0], rs[1], rs[2], rs[3]);
-          *reinterpret_cast<float4*>(rr + 4) = make_float4(rs[4], rs[5], rs[6], rs[7]);
+          r_store(t, rs);
         }
         tmem_st8(tm_s2(k), s2v);
       }
@@ -494,8 +508,8 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
             const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + jb);
             const float v0 = (jkind == 0) ? fmaf(ax, bx, ay * by) : fmaf(ax, ax, ay * ay);
             const float v1 = (jkind == 0) ? fmaf(ay, bx, -ax * by) : fmaf(bx, bx, by * by);
-            const float4 w0 = *reinterpret_cast<const float4*>(sRr + (size_t)fr * 8);
-            const float4 w1 = *reinterpret_cast<const float4*>(sRr + (size_t)fr * 8 + 4);
+            const float4 w0 = *reinterpret_cast<const float4*>(sRr + 4 * fr);
+            const float4 w1 = *reinterpret_cast<const float4*>(sRr + 4 * kSMaxT + 4 * fr);
             const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
             for (int m = 0; m < M; ++m) {
@@ -574,18 +588,17 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       for (int k = 0; k < kSSlots; ++k) {
         if (k >= KF) break;                                // uniform over the CTA
         const int t = tid + k * kSThreads;
+        const float hn = hrow[k];
         float s2v[8], u[8];
         tmem_ld16(tm_s2(k), s2v, u);
         if (t < T) {
-          float* rr = sRr + (size_t)t * 8;
           if (n > 0) {
-            const float4 r0 = *reinterpret_cast<const float4*>(rr);
-            const float4 r1 = *reinterpret_cast<const float4*>(rr + 4);
-            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float rv[8];
+            r_load(t, rv);
             float g = 0.f;
 #pragma unroll
             for (int m = 0; m < M; ++m) g = fmaf(rv[m], coef[m], g);
-            const float hold = hprev[k];
+            const float hold = hprev[k * kSThreads];
             const float hnew = hold * g;
             vf[(size_t)(n - 1) * T + t] = hnew;
 #pragma unroll
@@ -597,8 +610,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
               s2v[m] = fmaf(Lnew[m], hnew, rest);
             }
           }
-          const float hn = hrow[k];
-          hprev[k] = hn;
+          hprev[k * kSThreads] = hn;
           float rv[8];
 #pragma unroll
           for (int m = 0; m < 8; ++m) rv[m] = 0.f;
@@ -610,8 +622,7 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
             rv[m] = rr_;
             acc[m] += rr_;
           }
-          *reinterpret_cast<float4*>(rr) = make_float4(rv[0], rv[1], rv[2], rv[3]);
-          *reinterpret_cast<float4*>(rr + 4) = make_float4(rv[4], rv[5], rv[6], rv[7]);
+          r_store(t, rv);
         }
         if (n > 0) tmem_st8(tm_s2(k), s2v);
       }

@@ -88,7 +88,8 @@ void check_sm() {
   if (kSThreads % 128 || kSThreads > 1024) fail("sm threads", M, 0, 0, kSThreads);
   if (kSThreads * 128 != 65536) fail("sm registers do not fill the SM", M, 0, 0, kSThreads * 128);
   if (SmSmem<M>::bytes > kDynMax) fail("sm smem", M, 0, 0, SmSmem<M>::bytes);
-  if (SmSmem<M>::oQw < sizeof(float) * 8 * (size_t)kSMaxT) fail("sm r rows", M, 0, 0, SmSmem<M>::oQw);
+  if (SmSmem<M>::oHp < sizeof(float) * 8 * (size_t)kSMaxT) fail("sm r planes", M, 0, 0, SmSmem<M>::oHp);
+  if (SmSmem<M>::oQw - SmSmem<M>::oHp < sizeof(float) * (size_t)kSSlots * kSThreads) fail("sm h slots", M, 0, 0, SmSmem<M>::oQw);
   for (int T = 1; T <= kSMaxT; ++T) {
     const int KF = (T + kSThreads - 1) / kSThreads;
     if (KF > kSSlots || KF * kSThreads < T) fail("sm frame slots", M, 0, T, KF);
