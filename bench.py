@@ -311,7 +311,7 @@ def run_learned(n_train):
     loss1 = L.mean_loss(net, data)
     del data
     torch.cuda.empty_cache()
-    res = L.evaluate(net, n_eval, w.F, w.T, w.M, w.N, w.K, w.spacing, seed=(0xFFFF << 32) + w.seed, iters=w.iters)
+    res = L.evaluate(net, n_eval, w.F, w.T, w.M, w.N, w.K, w.spacing, seed=(0xFFFF << 32) + w.seed, max_iters=1000)
     net.close()
     res.update({"workload": w.name, "train_mixtures": n_train, "target_iters": w.iters,
                 "train_data_seconds": t_data, "train_seconds": t_train, "epochs": 6, "batch_rows": 2048,

@@ -253,79 +253,109 @@ def mean_loss(net, data, batch=4096):
 
 
 # ---------------------------------------------------------------------------- evaluation
-def _ll_trace(sep, n_mix, F, iters):
-    """Log-likelihood per mixture after each of `iters` iterations: (iters, n_mix)."""
-    out = np.empty((iters, n_mix))
-    for it in range(iters):
+def _ll_trace(sep, n_mix, F, T, max_iters, conv):
+    """Log-likelihood per mixture after each iteration, (iters run, n_mix), until no mixture's
+    log-likelihood moves by more than conv per bin in one iteration, or max_iters."""
+    out = []
+    prev = None
+    for _ in range(max_iters):
         sep.iterate(1, return_ll=False)
         _, pf = sep.loglik(per_f=True)
-        out[it] = pf.reshape(n_mix, F).sum(axis=1)
-    return out
+        cur = pf.reshape(n_mix, F).sum(axis=1)
+        out.append(cur)
+        if prev is not None and np.max(np.abs(cur - prev)) < conv * F * T:
+            break
+        prev = cur
+    return np.array(out)
 
 
-def _time_iters(sep, k=10):
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+def _timed_replay(sep, iters, before=None):
+    """(seconds the start `before()` took, seconds from the beginning to the end of each of
+    `iters` single iterations), from CUDA events on the current stream, which the contexts
+    here run on."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters)]
     torch.cuda.synchronize()
-    start.record()
-    sep.iterate(k, return_ll=False)
-    end.record()
+    e0.record(st)
+    if before is not None:
+        before()
+    e1.record(st)
+    for k in range(iters):
+        sep.iterate(1, return_ll=False)
+        ev[k].record(st)
     torch.cuda.synchronize()
-    return start.elapsed_time(end) / 1e3 / k
+    return e0.elapsed_time(e1) / 1e3, np.array([e0.elapsed_time(e) / 1e3 for e in ev])
 
 
-def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, iters=200, tol=1e-3, stream=None):
+def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3, conv=1e-6, stream=None):
     """Learned start vs the default start on n_mix held-out mixtures, batched as one context.
 
-    The reference is the log-likelihood the default start reaches after `iters` iterations; a
-    mixture has converged once its log-likelihood is within tol per bin (tol F T) of that.
-    Reports, per start, the iterations at which 50 % and 90 % of the mixtures have converged,
-    the batched wall time to get there (start cost + iterations x measured time per
-    iteration), the fraction that converges at all within `iters`, and the final
-    log-likelihood per bin relative to the reference.
+    Both starts are run to convergence (until no mixture's log-likelihood changes by more than
+    `conv` per bin in an iteration, at most max_iters iterations).  The reference of a mixture
+    is the better of the two converged log-likelihoods; a start has reached it once it is
+    within tol per bin (tol F T) of it.  Each start is then replayed, bit for bit the same
+    run, with a CUDA event after every iteration: its time to the reference is measured from
+    the start (for the learned start: features, network, prediction, upload) to the iteration
+    that crosses.  Reports, per start, the iterations and seconds at which 50 % and 90 % of the
+    mixtures have reached the reference, the fraction that reaches it at all, the converged
+    log-likelihood per bin relative to the reference, and the fraction of mixtures on which the
+    learned start ends below the default one (by more than tol per bin).
     """
     x = generate_mixtures(n_mix, F, T, M, N, K, spacing, seed, stream).view(n_mix * F, T, M)
     bins = F * T
-    # default start
-    plain = ff.Separator(x, N, stream=stream, seed=(int(seed) * 31 + 7) & 0x7fffffff)
-    t_iter = _time_iters(plain)
-    plain.close()
-    plain = ff.Separator(x, N, stream=stream, seed=(int(seed) * 31 + 7) & 0x7fffffff)
-    ll_plain = _ll_trace(plain, n_mix, F, iters)
-    plain.close()
-    # learned start (timed: features, network, prediction, parameter upload)
+    plain_seed = (int(seed) * 31 + 7) & 0x7fffffff
+    # default start: its parameters, then a trace to convergence
+    plain = ff.Separator(x, N, stream=stream, seed=plain_seed)
+    P0, lam0, v0 = (torch.from_numpy(a).cuda() for a in plain.get_params())
+    tr_plain = _ll_trace(plain, n_mix, F, T, max_iters, conv)
+    # learned start: features, network, prediction, then a trace to convergence
     sep = ff.Separator(x, N, stream=stream, seed=0)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record()
-    feats, q = features(x, F, stream)
-    P, lam, v = net.predict(feats, q)
-    sep.set_params(P, lam, v)
-    ev1.record()
-    torch.cuda.synchronize()
-    t_start = ev0.elapsed_time(ev1) / 1e3
-    ll_learned = _ll_trace(sep, n_mix, F, iters)
-    sep.close()
-    ref = ll_plain[-1]
+
+    def learned_start():
+        feats, q = features(x, F, stream)
+        P, lam, v = net.predict(feats, q)
+        sep.set_params(P, lam, v)
+
+    learned_start()
+    tr_learned = _ll_trace(sep, n_mix, F, T, max_iters, conv)
+    ref = np.maximum(tr_plain[-1], tr_learned[-1])
     thresh = ref - tol * bins
 
     def first_hit(tr):
         hit = tr >= thresh[None, :]
-        its = np.where(hit.any(axis=0), hit.argmax(axis=0) + 1, np.inf)
-        return its
+        return np.where(hit.any(axis=0), hit.argmax(axis=0) + 1, np.inf)
 
-    res = {"n_mix": n_mix, "iters": iters, "tol_per_bin": tol, "seconds_per_iteration": t_iter,
-           "learned_start_seconds": t_start}
-    for name, tr, t0 in (("plain", ll_plain, 0.0), ("learned", ll_learned, t_start)):
-        its = first_hit(tr)
+    hits = {"plain": first_hit(tr_plain), "learned": first_hit(tr_learned)}
+    # timed replays of the same runs, up to the last crossing
+    times, t_start = {}, {}
+    for name, ctx, start in (("plain", plain, lambda: plain.set_params(P0, lam0, v0)),
+                             ("learned", sep, learned_start)):
+        fin = hits[name][np.isfinite(hits[name])]
+        kmax = int(fin.max()) if fin.size else 1
+        t_start[name], times[name] = _timed_replay(ctx, kmax, before=start)
+    plain.close()
+    sep.close()
+    res = {"n_mix": n_mix, "max_iters": max_iters, "tol_per_bin": tol, "conv_per_bin": conv,
+           "iters_run": {"plain": int(tr_plain.shape[0]), "learned": int(tr_learned.shape[0])},
+           "reference": "per mixture, the better of the two starts' converged log-likelihoods",
+           "timing": "CUDA events after every iteration of a replay of the same run, from the start "
+                     "(the learned start's features, network, prediction and upload included)",
+           "learned_ends_below_default_fraction": float(np.mean(tr_learned[-1] < tr_plain[-1] - tol * bins)),
+           "learned_start_seconds": float(t_start["learned"]),
+           "seconds_per_iteration": float(np.median(np.diff(times["plain"]))) if len(times["plain"]) > 1 else None}
+    for name, tr in (("plain", tr_plain), ("learned", tr_learned)):
+        its = hits[name]
+        sec = np.array([times[name][int(k) - 1] if np.isfinite(k) else np.inf for k in its])
         out = {"converged_fraction": float(np.isfinite(its).mean()),
                "final_ll_per_bin_minus_ref": float(np.median((tr[-1] - ref) / bins)),
                "ll_per_bin_after_1": float(np.median((tr[0] - ref) / bins)),
-               "ll_per_bin_after_10": float(np.median((tr[min(9, iters - 1)] - ref) / bins))}
-        srt = np.sort(its)
+               "ll_per_bin_after_10": float(np.median((tr[min(9, tr.shape[0] - 1)] - ref) / bins))}
         for pct in (50, 90):
-            k = srt[max(int(np.ceil(pct / 100.0 * len(srt))) - 1, 0)]   # order statistic; inf = never
-            k = float(k) if np.isfinite(k) else None
-            out[f"iters_p{pct}"] = k
-            out[f"seconds_p{pct}"] = None if k is None else t0 + k * t_iter
+            q = int(max(np.ceil(pct / 100.0 * len(its)) - 1, 0))
+            k = np.sort(its)[q]
+            t = np.sort(sec)[q]
+            out[f"iters_p{pct}"] = float(k) if np.isfinite(k) else None
+            out[f"seconds_p{pct}"] = float(t) if np.isfinite(t) else None
         res[name] = out
     return res

@@ -312,14 +312,18 @@ def trained(L):
 def test_trained_network_beats_the_default_start(L, trained):
     net, before, after, (M, N, F, T, K, d) = trained
     assert after < 0.5 * before
-    res = L.evaluate(net, 32, F, T, M, N, K, d, seed=(0xFFFF << 32) + 31, iters=200)
+    res = L.evaluate(net, 32, F, T, M, N, K, d, seed=(0xFFFF << 32) + 31, max_iters=1000)
     p, q = res["plain"], res["learned"]
-    # reaches the default start's 200-iteration log-likelihood (within 1e-3 per bin) on most
-    # held-out mixtures, in fewer iterations and less time, and ends no worse
+    # both starts run to convergence; the reference of a mixture is the better converged
+    # log-likelihood.  The learned start reaches it (within 1e-3 per bin) on most held-out
+    # mixtures, in less measured time than the default start (which may never reach it where
+    # the learned start found the better optimum), and rarely ends below the default start
     assert q["converged_fraction"] >= 0.9
-    assert q["iters_p50"] is not None and q["iters_p50"] < 0.8 * p["iters_p50"]
-    assert q["seconds_p50"] < p["seconds_p50"]
+    assert q["seconds_p50"] is not None
+    if p["seconds_p50"] is not None:
+        assert q["seconds_p50"] < p["seconds_p50"] and q["iters_p50"] < p["iters_p50"]
     assert q["final_ll_per_bin_minus_ref"] >= -1e-3
+    assert res["learned_ends_below_default_fraction"] <= 0.1
     assert q["ll_per_bin_after_10"] > p["ll_per_bin_after_10"]
 
 
