@@ -255,18 +255,29 @@ def mean_loss(net, data, batch=4096):
 # ---------------------------------------------------------------------------- evaluation
 def _ll_trace(sep, n_mix, F, T, max_iters, conv):
     """Log-likelihood per mixture after each iteration, (iters run, n_mix), until no mixture's
-    log-likelihood moves by more than conv per bin in one iteration, or max_iters."""
+    log-likelihood moves by more than conv per bin in one iteration, or max_iters, or the first
+    numerical failure (ENUMERIC: after many iterations a nearly degenerate bin can leave the
+    FP32 range of its Q_m or sigma^2); the trace then holds the iterations before it.
+    Returns (trace, why it stopped)."""
     out = []
     prev = None
-    for _ in range(max_iters):
-        sep.iterate(1, return_ll=False)
-        _, pf = sep.loglik(per_f=True)
+    why = "max_iters"
+    for k in range(max_iters):
+        try:
+            sep.iterate(1, return_ll=False)
+            _, pf = sep.loglik(per_f=True)
+        except ff.FastFCAError as e:
+            if "ENUMERIC" not in str(e) or not out:
+                raise
+            why = f"numerical failure reported after iteration {k + 1} ({e}); the trace ends at iteration {k}"
+            break
         cur = pf.reshape(n_mix, F).sum(axis=1)
         out.append(cur)
         if prev is not None and np.max(np.abs(cur - prev)) < conv * F * T:
+            why = "converged"
             break
         prev = cur
-    return np.array(out)
+    return np.array(out), why
 
 
 def _timed_replay(sep, iters, before=None):
@@ -308,7 +319,7 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
     # default start: its parameters, then a trace to convergence
     plain = ff.Separator(x, N, stream=stream, seed=plain_seed)
     P0, lam0, v0 = (torch.from_numpy(a).cuda() for a in plain.get_params())
-    tr_plain = _ll_trace(plain, n_mix, F, T, max_iters, conv)
+    tr_plain, why_plain = _ll_trace(plain, n_mix, F, T, max_iters, conv)
     # learned start: features, network, prediction, then a trace to convergence
     sep = ff.Separator(x, N, stream=stream, seed=0)
 
@@ -318,7 +329,7 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
         sep.set_params(P, lam, v)
 
     learned_start()
-    tr_learned = _ll_trace(sep, n_mix, F, T, max_iters, conv)
+    tr_learned, why_learned = _ll_trace(sep, n_mix, F, T, max_iters, conv)
     ref = np.maximum(tr_plain[-1], tr_learned[-1])
     thresh = ref - tol * bins
 
@@ -338,6 +349,7 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
     sep.close()
     res = {"n_mix": n_mix, "max_iters": max_iters, "tol_per_bin": tol, "conv_per_bin": conv,
            "iters_run": {"plain": int(tr_plain.shape[0]), "learned": int(tr_learned.shape[0])},
+           "trace_stopped": {"plain": why_plain, "learned": why_learned},
            "reference": "per mixture, the better of the two starts' converged log-likelihoods",
            "timing": "CUDA events after every iteration of a replay of the same run, from the start "
                      "(the learned start's features, network, prediction and upload included)",
