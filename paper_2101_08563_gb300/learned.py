@@ -299,7 +299,8 @@ def _timed_replay(sep, iters, before=None):
     return e0.elapsed_time(e1) / 1e3, np.array([e0.elapsed_time(e) / 1e3 for e in ev])
 
 
-def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3, conv=1e-6, stream=None):
+def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3, conv=1e-6, early_iters=200,
+             stream=None):
     """Learned start vs the default start on n_mix held-out mixtures, batched as one context.
 
     Both starts are run to convergence (until no mixture's log-likelihood changes by more than
@@ -312,6 +313,10 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
     mixtures have reached the reference, the fraction that reaches it at all, the converged
     log-likelihood per bin relative to the reference, and the fraction of mixtures on which the
     learned start ends below the default one (by more than tol per bin).
+
+    The same is reported (under "to_default_<early_iters>") for a second reference: the
+    default start's log-likelihood after early_iters iterations, the iteration count of the
+    network's training targets.
     """
     x = generate_mixtures(n_mix, F, T, M, N, K, spacing, seed, stream).view(n_mix * F, T, M)
     bins = F * T
@@ -331,18 +336,19 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
     learned_start()
     tr_learned, why_learned = _ll_trace(sep, n_mix, F, T, max_iters, conv)
     ref = np.maximum(tr_plain[-1], tr_learned[-1])
-    thresh = ref - tol * bins
+    ref_early = tr_plain[min(early_iters, tr_plain.shape[0]) - 1]
 
-    def first_hit(tr):
-        hit = tr >= thresh[None, :]
+    def first_hit(tr, r):
+        hit = tr >= (r - tol * bins)[None, :]
         return np.where(hit.any(axis=0), hit.argmax(axis=0) + 1, np.inf)
 
-    hits = {"plain": first_hit(tr_plain), "learned": first_hit(tr_learned)}
-    # timed replays of the same runs, up to the last crossing
+    hits = {name: first_hit(tr, ref) for name, tr in (("plain", tr_plain), ("learned", tr_learned))}
+    hits_early = {name: first_hit(tr, ref_early) for name, tr in (("plain", tr_plain), ("learned", tr_learned))}
+    # timed replays of the same runs, up to the last crossing of either reference
     times, t_start = {}, {}
     for name, ctx, start in (("plain", plain, lambda: plain.set_params(P0, lam0, v0)),
                              ("learned", sep, learned_start)):
-        fin = hits[name][np.isfinite(hits[name])]
+        fin = np.concatenate([hits[name][np.isfinite(hits[name])], hits_early[name][np.isfinite(hits_early[name])]])
         kmax = int(fin.max()) if fin.size else 1
         t_start[name], times[name] = _timed_replay(ctx, kmax, before=start)
     plain.close()
@@ -356,18 +362,25 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
            "learned_ends_below_default_fraction": float(np.mean(tr_learned[-1] < tr_plain[-1] - tol * bins)),
            "learned_start_seconds": float(t_start["learned"]),
            "seconds_per_iteration": float(np.median(np.diff(times["plain"]))) if len(times["plain"]) > 1 else None}
-    for name, tr in (("plain", tr_plain), ("learned", tr_learned)):
-        its = hits[name]
+    def crossing(name, its):
         sec = np.array([times[name][int(k) - 1] if np.isfinite(k) else np.inf for k in its])
-        out = {"converged_fraction": float(np.isfinite(its).mean()),
-               "final_ll_per_bin_minus_ref": float(np.median((tr[-1] - ref) / bins)),
-               "ll_per_bin_after_1": float(np.median((tr[0] - ref) / bins)),
-               "ll_per_bin_after_10": float(np.median((tr[min(9, tr.shape[0] - 1)] - ref) / bins))}
+        out = {"reached_fraction": float(np.isfinite(its).mean())}
         for pct in (50, 90):
             q = int(max(np.ceil(pct / 100.0 * len(its)) - 1, 0))
-            k = np.sort(its)[q]
-            t = np.sort(sec)[q]
+            k, t = np.sort(its)[q], np.sort(sec)[q]
             out[f"iters_p{pct}"] = float(k) if np.isfinite(k) else None
             out[f"seconds_p{pct}"] = float(t) if np.isfinite(t) else None
+        return out
+
+    res[f"to_default_{early_iters}"] = {
+        "reference": f"per mixture, the default start's log-likelihood after {early_iters} iterations "
+                     f"(the training targets' iteration count), within tol per bin"}
+    for name, tr in (("plain", tr_plain), ("learned", tr_learned)):
+        out = crossing(name, hits[name])
+        out["converged_fraction"] = out.pop("reached_fraction")
+        out.update({"final_ll_per_bin_minus_ref": float(np.median((tr[-1] - ref) / bins)),
+                    "ll_per_bin_after_1": float(np.median((tr[0] - ref) / bins)),
+                    "ll_per_bin_after_10": float(np.median((tr[min(9, tr.shape[0] - 1)] - ref) / bins))})
         res[name] = out
+        res[f"to_default_{early_iters}"][name] = crossing(name, hits_early[name])
     return res
