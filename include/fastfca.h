@@ -357,7 +357,9 @@ fastfca_status fastfca_separate_noalloc(int32_t F, int32_t T, int32_t M, int32_t
  *     lexicographic order on ties);  loss = sum_m (1 - |u_sigma(m)^H u*_m|^2)
  *     + sum_{m,n} (l[sigma(m)][pi(n)] - l*[m][n])^2 + (1/T) sum_{n,t} (h[pi(n)][t] - h*[n][t])^2,
  *     averaged over the rows of a batch.
- * Products run on BF16 tensor cores (operands rounded to BF16, FP32 accumulation); the rest in
+ * Products run on the tensor cores (tcgen05.mma: operands rounded to BF16, FP32 accumulators in
+ * tensor memory; a product whose completion wait runs out makes the net's next synchronising
+ * call return ECUDA); the rest in
  * FP32.  Parameters are one flat FP32 vector: W1 [256][16], b1 [256], W2 [256][256], b2 [256],
  * W3 [40][256], b3 [40], k [N][9], c [N].  The network supports M in {2, 3}, N <= 5 and
  * 2 M^2 + M N + N <= 40.  A "row" is one frequency of one mixture.  Unless stated otherwise

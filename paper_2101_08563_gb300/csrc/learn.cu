@@ -1,8 +1,8 @@
 // Learned initialiser of FastFCA (not in the paper; its own initialisation is mask-based,
 // Sec. VII).  Kernels and C ABI for: model-generated training mixtures (Philox4x32-10 on the
 // GPU), per-frequency features, scale-free targets from converged FastFCA parameters, a
-// 3-layer MLP (hidden 256, GELU) whose products run on BF16 tensor cores (mma.sync) with FP32
-// accumulation, the 1-D conv over t that gives per-frame powers, the permutation-free loss
+// 3-layer MLP (hidden 256, GELU) whose products run on the fifth-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulators in tensor memory), the 1-D conv over t that gives per-frame powers, the permutation-free loss
 // with its gradient, Adam, and the prediction of (W, L, H) for Algorithm 1.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -15,6 +15,7 @@
 
 #include "../../include/fastfca.h"
 #include "alloc.h"
+#include "fastfca_em_sm.cuh"
 #include "launch.cuh"
 #include "learn.cuh"
 #include "trace.h"
@@ -204,91 +205,154 @@ __global__ void targets_kernel(int rows, int T, int M, int N, const double2* __r
 
 // ------------------------------------------------------------------------------ BF16 GEMM
 // C[m][n] = sum_k A(m,k) B(n,k) (+ bias[n]), A(m,k) = A[m*sam + k*sak], B(n,k) = B[n*sbn + k*sbk],
-// FP32 in memory; tiles are rounded to BF16 in shared memory and multiplied on the tensor
-// cores (mma.sync m16n8k16, FP32 accumulation).  64x64 output tile per CTA, 4 warps of 32x32.
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+// FP32 in memory (the master weights and FP32 activations, transposed in the backward
+// products).  A CTA computes a 128 x 64 tile of C on the tensor cores with tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulation in 64 columns of tensor memory):
+//  * per K block of 64, the 128 threads round their share of the A (128 x 64) and B (64 x 64)
+//    tiles to BF16 into shared memory in the tensor cores' no-swizzle K-major layout: 8 x 8
+//    core matrices of 128 contiguous bytes, K-neighbouring core matrices 128 bytes apart (the
+//    leading-dimension offset), groups of 8 rows 1024 bytes apart (the stride offset);
+//  * one thread issues the block's four K = 16 products and commits them to an mbarrier;
+//    every thread waits on it (bounded) before the tiles are rewritten;
+//  * the epilogue reads the accumulator (warp w: rows 32w..32w+31, one per lane) with
+//    tcgen05.ld, adds the bias and stores C.
+// The operands are rounded to BF16 while staged because they live in FP32; a TMA copy cannot
+// convert, and BF16 copies of every operand would cost an extra pass for products of at most
+// 2048 x 256 x 256.  A wait past its limit (the products never arrive) sets bit 1 of *status,
+// waits once more (bounded) for the products in flight and skips the epilogue; the net's
+// synchronising calls report it as ECUDA.
+constexpr int GUM = 128, GUN = 64, GUK = 64;
+constexpr int kGemmThreads = 128;
+constexpr unsigned kGemmCols = 64;                   // TMEM columns of the FP32 accumulator
+constexpr int kGemmSpin = 1 << 20;
+constexpr size_t kGemmSmemA = GUM * GUK * 2, kGemmSmemB = GUN * GUK * 2;
+// 29 KB of shared memory per CTA caps an SM at 7 CTAs: 7 x 64 <= 512 TMEM columns, so no CTA
+// ever waits for tensor memory
+constexpr size_t kGemmDynSmem = 29 * 1024;
+static_assert(kGemmSmemA + kGemmSmemB + 16 <= kGemmDynSmem, "GEMM tiles exceed the CTA's shared memory");
+static_assert((228 * 1024 / kGemmDynSmem) * kGemmCols <= 512, "GEMM CTAs per SM could exceed TMEM");
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int k) {
+  return (uint32_t)((k >> 3) * 128 + (row >> 3) * (GUK / 8) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int Md, int Nd, int Kd, const float* __restrict__ A,
-                                                       long long sam, long long sak, const float* __restrict__ B,
-                                                       long long sbn, long long sbk, const float* __restrict__ bias,
-                                                       float* __restrict__ C, long long ldc) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, c = lane & 3;
-  float acc[2][4][4];
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 4; ++j)
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  for (int k0 = 0; k0 < Kd; k0 += GBK) {
-    // stage A and B tiles (element-wise, coalesced along whichever stride is 1)
-    for (int e = 0; e < (GBM * GBK) / 128; ++e) {
-      const int i = tid + e * 128;
+// Shared-memory matrix descriptor: start address, leading-dimension offset 128 B and stride
+// offset 1024 B (each in 16-byte units), descriptor version 1 (bits 46-47), no swizzle.
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9
+// and 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28.
+constexpr uint32_t kUmmaIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GUN >> 3) << 17) | ((uint32_t)(GUM >> 4) << 24);
+
+__global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd, int Kd, const float* __restrict__ A,
+                                                                long long sam, long long sak, const float* __restrict__ B,
+                                                                long long sbn, long long sbk,
+                                                                const float* __restrict__ bias, float* __restrict__ C,
+                                                                long long ldc, int* status) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  unsigned char* sA = gsm;
+  unsigned char* sB = gsm + kGemmSmemA;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(gsm + kGemmSmemA + kGemmSmemB);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(gsm + kGemmSmemA + kGemmSmemB + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * GUM, n0 = blockIdx.x * GUN;
+  if (warp == 0) tmem_alloc(tbase, kGemmCols);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t d_tmem = *tbase;
+  const uint32_t aBase = (uint32_t)__cvta_generic_to_shared(sA), bBase = (uint32_t)__cvta_generic_to_shared(sB);
+  unsigned phase = 0;
+  bool failed = false;
+  const int nkb = (Kd + GUK - 1) / GUK;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int k0 = kb * GUK;
+    // stage the block's tiles as BF16 (coalesced along whichever stride is 1)
+    for (int e = 0; e < GUM * GUK / kGemmThreads; ++e) {
+      const int i = tid + e * kGemmThreads;
       int row, col;
-      if (sak == 1) { row = i / GBK; col = i % GBK; } else { row = i % GBM; col = i / GBM; }
+      if (sak == 1) { row = i / GUK; col = i % GUK; } else { row = i % GUM; col = i / GUM; }
       const int m = m0 + row, k = k0 + col;
       const float val = (m < Md && k < Kd) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
-      As[row][col] = __float2bfloat16(val);
+      *reinterpret_cast<__nv_bfloat16*>(sA + kmajor_offset(row, col)) = __float2bfloat16(val);
     }
-    for (int e = 0; e < (GBN * GBK) / 128; ++e) {
-      const int i = tid + e * 128;
+    for (int e = 0; e < GUN * GUK / kGemmThreads; ++e) {
+      const int i = tid + e * kGemmThreads;
       int row, col;
-      if (sbk == 1) { row = i / GBK; col = i % GBK; } else { row = i % GBN; col = i / GBN; }
+      if (sbk == 1) { row = i / GUK; col = i % GUK; } else { row = i % GUN; col = i / GUN; }
       const int n = n0 + row, k = k0 + col;
       const float val = (n < Nd && k < Kd) ? B[(long long)n * sbn + (long long)k * sbk] : 0.f;
-      Bs[row][col] = __float2bfloat16(val);
+      *reinterpret_cast<__nv_bfloat16*>(sB + kmajor_offset(row, col)) = __float2bfloat16(val);
     }
+    // the tensor cores read shared memory through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0) {
+      tmem_fence_after_sync();
 #pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t af[2][4], bf[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int r0 = wm + mi * 16 + g;
-        af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r0][kk + 2 * c]);
-        af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kk + 2 * c]);
-        af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r0][kk + 2 * c + 8]);
-        af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][kk + 2 * c + 8]);
+      for (int s = 0; s < GUK / 16; ++s) {
+        const uint64_t ad = umma_smem_desc(aBase + s * 256), bd = umma_smem_desc(bBase + s * 256);
+        const uint32_t accum = (kb > 0 || s > 0) ? 1u : 0u;      // the first product overwrites
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                d_tmem),
+            "l"(ad), "l"(bd), "r"(kUmmaIdesc), "r"(accum)
+            : "memory");
       }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int nr = wn + ni * 8 + g;
-        bf[ni][0] = *reinterpret_cast<const uint32_t*>(&Bs[nr][kk + 2 * c]);
-        bf[ni][1] = *reinterpret_cast<const uint32_t*>(&Bs[nr][kk + 2 * c + 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], af[mi], bf[ni]);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(mbar))
+                   : "memory");
     }
-    __syncthreads();
+    int spins = 0;
+    while (!mbar_try_wait(mbar, phase) && ++spins < kGemmSpin) {
+    }
+    if (__syncthreads_or(spins >= kGemmSpin)) {      // the same decision in every thread
+      int drain = 0;
+      while (!mbar_try_wait(mbar, phase) && ++drain < kGemmSpin) {
+      }
+      failed = true;
+      break;
+    }
+    phase ^= 1;
+    tmem_fence_after_sync();
   }
+  if (failed) {
+    if (tid == 0) atomicOr(status, 1);
+  } else {
+    const int m = m0 + warp * 32 + lane;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+    for (int c4 = 0; c4 < GUN / 16; ++c4) {
+      float a8[8], b8[8];
+      tmem_ld16(d_tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c4 * 16), a8, b8);
+      if (m < Md) {
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = m0 + wm + mi * 16 + g + ((e >= 2) ? 8 : 0);
-        const int n = n0 + wn + ni * 8 + 2 * c + (e & 1);
-        if (m < Md && n < Nd) C[(long long)m * ldc + n] = acc[mi][ni][e] + (bias ? bias[n] : 0.f);
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c4 * 16 + j;
+          const float v = j < 8 ? a8[j] : b8[j - 8];
+          if (n < Nd) C[(long long)m * ldc + n] = v + (bias ? bias[n] : 0.f);
+        }
       }
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(d_tmem, kGemmCols);
 }
 
 cudaError_t gemm(int Md, int Nd, int Kd, const float* A, long long sam, long long sak, const float* B, long long sbn,
-                 long long sbk, const float* bias, float* C, long long ldc, cudaStream_t s) {
-  dim3 grid((Nd + GBN - 1) / GBN, (Md + GBM - 1) / GBM);
-  gemm_bf16_kernel<<<grid, 128, 0, s>>>(Md, Nd, Kd, A, sam, sak, B, sbn, sbk, bias, C, ldc);
+                 long long sbk, const float* bias, float* C, long long ldc, int* status, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmDynSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((Nd + GUN - 1) / GUN, (Md + GUM - 1) / GUM);
+  gemm_bf16_kernel<<<grid, kGemmThreads, kGemmDynSmem, s>>>(Md, Nd, Kd, A, sam, sak, B, sbn, sbk, bias, C, ldc, status);
   return cudaGetLastError();
 }
 
@@ -655,6 +719,7 @@ struct fastfca_net {
   long long off_W1, off_b1, off_W2, off_b2, off_W3, off_b3, off_k, off_c;
   float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *o = nullptr;
   float *dout = nullptr, *d2 = nullptr, *d1 = nullptr, *dconv = nullptr, *loss = nullptr, *scal = nullptr;
+  int* gstat = nullptr;         // device status of the tensor-core products (bit 1: a wait ran out)
   int step = 0;
   char msg[256] = "";
 };
@@ -683,16 +748,27 @@ fastfca_status nfail(fastfca_net* n, fastfca_status st, const char* fmt, ...) {
 
 unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// After a synchronisation: the tensor-core products' status (a wait that ran out is ECUDA;
+// the word is cleared).
+fastfca_status net_status(fastfca_net* n) {
+  int bits = 0;
+  NCK(n, cudaMemcpyAsync(&bits, n->gstat, sizeof(int), cudaMemcpyDeviceToHost, n->stream), "status read");
+  NCK(n, cudaStreamSynchronize(n->stream), "status sync");
+  if (bits == 0) return FASTFCA_OK;
+  NCK(n, cudaMemsetAsync(n->gstat, 0, sizeof(int), n->stream), "status clear");
+  return nfail(n, FASTFCA_ECUDA, "a tensor-core product's completion wait ran out (bits 0x%x)", bits);
+}
+
 // forward for `rows` feature rows into net->o (and the activations)
 fastfca_status net_forward(fastfca_net* n, int rows, const float* feats) {
   cudaStream_t s = n->stream;
   const float* P = n->params;
-  NCK(n, gemm(rows, kHidden, kDin, feats, kDin, 1, P + n->off_W1, kDin, 1, P + n->off_b1, n->z1, kHidden, s), "gemm 1");
+  NCK(n, gemm(rows, kHidden, kDin, feats, kDin, 1, P + n->off_W1, kDin, 1, P + n->off_b1, n->z1, kHidden, n->gstat, s), "gemm 1");
   gelu_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z1, n->h1);
-  NCK(n, gemm(rows, kHidden, kHidden, n->h1, kHidden, 1, P + n->off_W2, kHidden, 1, P + n->off_b2, n->z2, kHidden, s),
+  NCK(n, gemm(rows, kHidden, kHidden, n->h1, kHidden, 1, P + n->off_W2, kHidden, 1, P + n->off_b2, n->z2, kHidden, n->gstat, s),
       "gemm 2");
   gelu_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z2, n->h2);
-  NCK(n, gemm(rows, kOutPad, kHidden, n->h2, kHidden, 1, P + n->off_W3, kHidden, 1, P + n->off_b3, n->o, kOutPad, s),
+  NCK(n, gemm(rows, kOutPad, kHidden, n->h2, kHidden, 1, P + n->off_W3, kHidden, 1, P + n->off_b3, n->o, kOutPad, n->gstat, s),
       "gemm 3");
   return FASTFCA_OK;
 }
@@ -729,17 +805,17 @@ fastfca_status net_loss_grad(fastfca_net* n, int rows, int T, const float* feats
   const int NKc = n->N * kConvK + n->N;
   colsum_kernel<<<blocks(NKc, 32), 256, 0, s>>>(rows, NKc, n->dconv, NKc, G + n->off_k);
   // backward through the MLP
-  NCK(n, gemm(kOutPad, kHidden, rows, n->dout, 1, kOutPad, n->h2, 1, kHidden, nullptr, G + n->off_W3, kHidden, s), "dW3");
+  NCK(n, gemm(kOutPad, kHidden, rows, n->dout, 1, kOutPad, n->h2, 1, kHidden, nullptr, G + n->off_W3, kHidden, n->gstat, s), "dW3");
   colsum_kernel<<<blocks(kOutPad, 32), 256, 0, s>>>(rows, kOutPad, n->dout, kOutPad, G + n->off_b3);
-  NCK(n, gemm(rows, kHidden, kOutPad, n->dout, kOutPad, 1, n->params + n->off_W3, 1, kHidden, nullptr, n->d2, kHidden, s),
+  NCK(n, gemm(rows, kHidden, kOutPad, n->dout, kOutPad, 1, n->params + n->off_W3, 1, kHidden, nullptr, n->d2, kHidden, n->gstat, s),
       "dh2");
   gelu_back_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z2, n->d2);
-  NCK(n, gemm(kHidden, kHidden, rows, n->d2, 1, kHidden, n->h1, 1, kHidden, nullptr, G + n->off_W2, kHidden, s), "dW2");
+  NCK(n, gemm(kHidden, kHidden, rows, n->d2, 1, kHidden, n->h1, 1, kHidden, nullptr, G + n->off_W2, kHidden, n->gstat, s), "dW2");
   colsum_kernel<<<blocks(kHidden, 32), 256, 0, s>>>(rows, kHidden, n->d2, kHidden, G + n->off_b2);
-  NCK(n, gemm(rows, kHidden, kHidden, n->d2, kHidden, 1, n->params + n->off_W2, 1, kHidden, nullptr, n->d1, kHidden, s),
+  NCK(n, gemm(rows, kHidden, kHidden, n->d2, kHidden, 1, n->params + n->off_W2, 1, kHidden, nullptr, n->d1, kHidden, n->gstat, s),
       "dh1");
   gelu_back_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z1, n->d1);
-  NCK(n, gemm(kHidden, kDin, rows, n->d1, 1, kHidden, feats, 1, kDin, nullptr, G + n->off_W1, kDin, s), "dW1");
+  NCK(n, gemm(kHidden, kDin, rows, n->d1, 1, kHidden, feats, 1, kDin, nullptr, G + n->off_W1, kDin, n->gstat, s), "dW1");
   colsum_kernel<<<blocks(kHidden, 32), 256, 0, s>>>(rows, kHidden, n->d1, kHidden, G + n->off_b1);
   NCK(n, cudaGetLastError(), "backward launches");
   if (loss) {
@@ -748,6 +824,7 @@ fastfca_status net_loss_grad(fastfca_net* n, int rows, int T, const float* feats
     NCK(n, cudaMemcpyAsync(&lsum, n->scal, sizeof(float), cudaMemcpyDeviceToHost, s), "loss download");
     NCK(n, cudaStreamSynchronize(s), "loss sync");
     *loss = (double)lsum / rows;
+    return net_status(n);
   }
   return FASTFCA_OK;
 }
@@ -836,6 +913,8 @@ fastfca_status fastfca_net_create(int32_t M, int32_t N, int32_t max_rows, int32_
   if ((e = ffca::dev_malloc(&n->dconv, sizeof(float) * (size_t)max_rows * (N * kConvK + N))) != cudaSuccess) return bail("dconv", e);
   if ((e = ffca::dev_malloc(&n->loss, sizeof(float) * (size_t)max_rows)) != cudaSuccess) return bail("loss", e);
   if ((e = ffca::dev_malloc(&n->scal, sizeof(float) * 4)) != cudaSuccess) return bail("scalar", e);
+  if ((e = ffca::dev_malloc(&n->gstat, sizeof(int))) != cudaSuccess) return bail("status", e);
+  cudaMemsetAsync(n->gstat, 0, sizeof(int), n->stream);
   cudaMemsetAsync(n->adam_m, 0, sizeof(float) * c, n->stream);
   cudaMemsetAsync(n->adam_v, 0, sizeof(float) * c, n->stream);
   cudaMemsetAsync(n->grads, 0, sizeof(float) * c, n->stream);
@@ -866,6 +945,7 @@ void fastfca_net_destroy(fastfca_net* n) {
   for (float* p : {n->params, n->grads, n->adam_m, n->adam_v, n->z1, n->h1, n->z2, n->h2, n->o, n->dout, n->d2, n->d1,
                    n->dconv, n->loss, n->scal})
     ffca::dev_free(p);
+  ffca::dev_free(n->gstat);
   delete n;
 }
 
@@ -877,7 +957,7 @@ fastfca_status fastfca_net_get_params(fastfca_net* n, float* out) {
   if (!n || !out) return FASTFCA_EINVAL;
   NCK(n, cudaMemcpyAsync(out, n->params, sizeof(float) * n->count, cudaMemcpyDefault, n->stream), "get params");
   NCK(n, cudaStreamSynchronize(n->stream), "get params sync");
-  return FASTFCA_OK;
+  return net_status(n);
 }
 
 fastfca_status fastfca_net_set_params(fastfca_net* n, const float* in) {
@@ -894,7 +974,7 @@ fastfca_status fastfca_net_forward(fastfca_net* n, int32_t rows, const float* fe
   if (st) return st;
   NCK(n, cudaMemcpyAsync(out, n->o, sizeof(float) * (size_t)rows * kOutPad, cudaMemcpyDefault, n->stream), "out copy");
   NCK(n, cudaStreamSynchronize(n->stream), "forward sync");
-  return FASTFCA_OK;
+  return net_status(n);
 }
 
 fastfca_status fastfca_net_loss_grad(fastfca_net* n, int32_t rows, int32_t T, const float* feats, const float* q,
@@ -906,6 +986,7 @@ fastfca_status fastfca_net_loss_grad(fastfca_net* n, int32_t rows, int32_t T, co
   if (grads) {
     NCK(n, cudaMemcpyAsync(grads, n->grads, sizeof(float) * n->count, cudaMemcpyDefault, n->stream), "grad copy");
     NCK(n, cudaStreamSynchronize(n->stream), "grad sync");
+    return net_status(n);
   }
   return FASTFCA_OK;
 }

@@ -32,8 +32,9 @@ def test_no_trap_and_no_device_assert():
 
 def test_every_open_ended_loop_is_bounded():
     """Loops with no bound of their own: the persistent batch kernel's item loop (it ends when
-    the atomic counter passes the item count) is the only `for (;;)`; the one wait on other
-    CTAs (the cluster exchange's mbarrier) counts its spins against a limit."""
+    the atomic counter passes the item count) is the only `for (;;)`; every mbarrier wait (the
+    cluster exchange's, and the tensor-core product's completion in the learned network's
+    GEMM) counts its spins against a limit."""
     forever = []
     for name, text in sources():
         code = strip_comments(text)
@@ -43,7 +44,7 @@ def test_every_open_ended_loop_is_bounded():
     loop = em[em.index("for (;;)"):]
     assert re.search(r"if \(i >= n_items\) return;", loop[:400])
     spins = [m.group(0) for _, t in sources() for m in re.finditer(r"while \(!mbar_try_wait[^\n]*", strip_comments(t))]
-    assert spins and all("kMbarSpinLimit" in s for s in spins)
+    assert spins and all(("kMbarSpinLimit" in s) or ("kGemmSpin" in s) for s in spins)
     # the injected-limit form polls without blocking, against the launch's limit
     polls = [m.group(0) for _, t in sources()
              for m in re.finditer(r"while \(!\(done = mbar_test_wait[^\n]*", strip_comments(t))]
