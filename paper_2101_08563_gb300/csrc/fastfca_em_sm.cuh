@@ -163,57 +163,133 @@ __device__ __forceinline__ void sm_lane_job(int lane, int& a, int& b, int& kind,
   }
 }
 
+// -x with an integer operation on the sign bit (no FP64 instruction).
+__device__ __forceinline__ double neg_f64(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
 // In-place inverses of the M matrices Q_m (HPD, row-major, consecutive) by the four FP64 warps
-// (threads 0..127), Gauss-Jordan without pivoting as in cluster_hpd_inverses, with every
-// entry spread over the warps the same way.  The reciprocal of each step's pivot is formed
-// once per matrix, by the thread that wrote that pivot in the step before (or by thread m
-// for step 0), and read from shared memory; on this part every FP64 warp instruction holds its
-// sub-partition's FP64 unit for ~68 cycles, so the per-entry reciprocals that this removes
-// were about a third of the inversion's FP64 instructions.  A non-positive pivot sets
-// kErrQPivot.
+// (threads 0..127), by the Hermitian sweep: step k, with d = a_kk > 0,
+//   a_ij <- a_ij - a_ik a_kj / d  (i, j != k),   a_kj <- a_kj / d,   a_ik <- a_ik / d,
+//   a_kk <- -1 / d,
+// keeps the matrix Hermitian and leaves -Q^{-1} after the M steps.  Only the upper triangle
+// is updated (entries below the diagonal are read as conj(a_ji)), which is 36 of the 64
+// entries at M = 8; the off-diagonal entries take two slots of the 128 threads and the real
+// diagonal entries one, three FP64 instructions each instead of six.  On this part every FP64
+// warp instruction holds its sub-partition's FP64 unit for ~68 cycles, so the instruction count
+// per warp sets the time.  The reciprocal of each step's pivot is formed once per matrix, by
+// the thread that wrote that pivot in the step before (or by thread m for step 0), and read
+// from shared memory.  A final pass writes -a (upper) and -conj(a) (lower) so that Q holds the
+// full Q^{-1}.  A non-positive pivot sets kErrQPivot.
 template <int M>
 __device__ void sm_hpd_inverses(double2* Q, double* sPiv, int tid, int* err) {
   constexpr int E = M * M;
-  constexpr int kSl = (M * E + kCIpThreads - 1) / kCIpThreads;
-  const int me = (tid & 31) * 4 + (tid >> 5);
+  constexpr int P = M * (M - 1) / 2;                                  // upper pairs per matrix
+  constexpr int kOff = (M * P + kCIpThreads - 1) / kCIpThreads;       // slots of pairs
+  constexpr int kDia = (M * M + kCIpThreads - 1) / kCIpThreads;       // slots of diagonal entries
   auto pivot_rcp = [&](double d, int m) {
     const float df = (float)d;
     const bool ok = df > 0.f && df < INFINITY;
     if (!ok) atomicOr(err, kErrQPivot);
     sPiv[m] = rcp_pos_f64(ok ? d : 1.0);
   };
+  // this thread's pairs (matrix, r < c) and diagonal entries (matrix, r), -1 when idle
+  int om[kOff], orr[kOff], oc[kOff], dm[kDia], dr[kDia];
+#pragma unroll
+  for (int s = 0; s < kOff; ++s) {
+    const int i = tid + s * kCIpThreads;
+    om[s] = -1; orr[s] = 0; oc[s] = 1;
+    if (i < M * P) {
+      om[s] = i / P;
+      int idx = i - om[s] * P, a = 0;
+      while (idx >= M - 1 - a) { idx -= M - 1 - a; ++a; }
+      orr[s] = a;
+      oc[s] = a + 1 + idx;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kDia; ++s) {
+    const int i = tid + s * kCIpThreads;
+    dm[s] = i < M * M ? i / M : -1;
+    dr[s] = i < M * M ? i - (i / M) * M : 0;
+  }
+  // a_ij of matrix A read from the upper triangle
+  auto get = [&](const double2* A, int i, int j) {
+    if (i <= j) return A[i * M + j];
+    const double2 v = A[j * M + i];
+    return make_double2(v.x, neg_f64(v.y));
+  };
   if (tid < M) pivot_rcp(Q[tid * E].x, tid);
   ip_bar();
   for (int k = 0; k < M; ++k) {
-    double2 nv[kSl];
+    double2 nv[kOff];
+    double nd[kDia];
 #pragma unroll
-    for (int s = 0; s < kSl; ++s) {
-      const int i = me + s * kCIpThreads;
-      if (i < M * E) {
-        const int mo = i / E, e = i - mo * E;
-        const double2* A = Q + mo * E;
-        const int r = e / M, cc = e - r * M;
-        const double rd = sPiv[mo];
-        const double2 aij = A[e], aik = A[r * M + k], akj = A[k * M + cc];
-        const double2 base = (r != k && cc != k) ? aij : make_double2(0.0, 0.0);
-        const double2 c1 = (r != k) ? aik : make_double2(-1.0, 0.0);
-        const double2 c2 = (cc != k) ? akj : make_double2(1.0, 0.0);
-        const double2 t = make_double2(c1.x * rd, c1.y * rd);
-        nv[s] = make_double2(fma(t.y, c2.y, fma(-t.x, c2.x, base.x)), fma(-t.y, c2.x, fma(-t.x, c2.y, base.y)));
+    for (int s = 0; s < kOff; ++s) {
+      nv[s] = make_double2(0.0, 0.0);
+      if (om[s] >= 0) {
+        const double2* A = Q + om[s] * E;
+        const int r = orr[s], c = oc[s];
+        const double rd = sPiv[om[s]];
+        double2 base = make_double2(0.0, 0.0), c1, c2;
+        if (r != k && c != k) {
+          base = A[r * M + c];
+          c1 = get(A, r, k);
+          c2 = get(A, k, c);
+        } else if (r == k) {                        // row k: a_kc / d
+          c1 = make_double2(-1.0, 0.0);
+          c2 = A[k * M + c];
+        } else {                                    // column k: a_rk / d
+          c1 = A[r * M + k];
+          c2 = make_double2(-1.0, 0.0);
+        }
+        const double2 u = make_double2(c2.x * rd, c2.y * rd);
+        nv[s] = make_double2(fma(c1.y, u.y, fma(-c1.x, u.x, base.x)), fma(-c1.y, u.x, fma(-c1.x, u.y, base.y)));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kDia; ++s) {
+      nd[s] = 0.0;
+      if (dm[s] >= 0) {
+        const double2* A = Q + dm[s] * E;
+        const int r = dr[s];
+        const double rd = sPiv[dm[s]];
+        const double2 g = (r != k) ? get(A, r, k) : make_double2(1.0, 0.0);
+        const double base = (r != k) ? A[r * M + r].x : 0.0;
+        nd[s] = fma(-fma(g.x, g.x, g.y * g.y), rd, base);
       }
     }
     ip_bar();
 #pragma unroll
-    for (int s = 0; s < kSl; ++s) {
-      const int i = me + s * kCIpThreads;
-      if (i < M * E) {
-        const int mo = i / E, e = i - mo * E;
-        Q[mo * E + e] = nv[s];
-        if (k + 1 < M && e == (k + 1) * (M + 1)) pivot_rcp(nv[s].x, mo);
+    for (int s = 0; s < kOff; ++s)
+      if (om[s] >= 0) Q[om[s] * E + orr[s] * M + oc[s]] = nv[s];
+#pragma unroll
+    for (int s = 0; s < kDia; ++s)
+      if (dm[s] >= 0) {
+        Q[dm[s] * E + dr[s] * (M + 1)] = make_double2(nd[s], 0.0);
+        if (k + 1 < M && dr[s] == k + 1) pivot_rcp(nd[s], dm[s]);
       }
-    }
     ip_bar();
   }
+  // Q <- -(the swept matrix), upper triangle in place and lower triangle by conjugation
+  constexpr int kAll = (M * E + kCIpThreads - 1) / kCIpThreads;
+  double2 fin[kAll];
+#pragma unroll
+  for (int s = 0; s < kAll; ++s) {
+    const int i = tid + s * kCIpThreads;
+    if (i < M * E) {
+      const int mo = i / E, e = i - mo * E, r = e / M, c = e - (e / M) * M;
+      const double2 v = get(Q + mo * E, r, c);
+      fin[s] = make_double2(neg_f64(v.x), neg_f64(v.y));
+    }
+  }
+  ip_bar();
+#pragma unroll
+  for (int s = 0; s < kAll; ++s) {
+    const int i = tid + s * kCIpThreads;
+    if (i < M * E) Q[i] = fin[s];
+  }
+  ip_bar();
 }
 
 #ifdef FFCA_PHASE_CLOCKS

@@ -205,16 +205,26 @@ inline void prefer_sm_kernel(int M, int N, int T, FastOps* o) {
   if (choice == 2 || o->cluster_c >= 2) o->em = fn;
 }
 
+// One persistent wave: as many CTAs as fit on every SM at once, so that each warp's range of
+// tiles is the same length.
 template <int M>
 cudaError_t launch_mwf_wide(const float2* x, const double2* P, const float2* WmH, const float* lam, const float* v,
                             float2* c, int F, int T, int N, int B, cudaStream_t s) {
   if (N < 1 || N > kMwfWMaxN || B < 1 || T % B != 0) return cudaErrorInvalidValue;
-  dim3 grid(F, (T + kMwfWFrames * kMwfWBatches - 1) / (kMwfWFrames * kMwfWBatches));
-  const size_t smem = mwf_wide_smem(M, N);
-  cudaError_t e = cudaFuncSetAttribute(fastfca_mwf_wide_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (F < 1 || T < 1) return cudaSuccess;
+  const size_t smem = mwf_tile_smem(M, N);
+  cudaError_t e = cudaFuncSetAttribute(fastfca_mwf_tile_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  fastfca_mwf_wide_kernel<M><<<grid, M * 32, smem, s>>>(x, P, WmH, lam, v, c, F, T, N, B);
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fastfca_mwf_tile_kernel<M>, kMwfTThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long tiles = (long long)F * ((T + mwf_tile_frames(M) - 1) / mwf_tile_frames(M));
+  const long long ctas = std::min<long long>((long long)sms * per_sm, (tiles + kMwfTWarps - 1) / kMwfTWarps);
+  fastfca_mwf_tile_kernel<M><<<(unsigned)ctas, kMwfTThreads, smem, s>>>(x, P, WmH, lam, v, c, F, T, N, B);
   return cudaGetLastError();
 }
 

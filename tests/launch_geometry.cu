@@ -70,11 +70,29 @@ void check_cluster() {
       if (smem > kDynMax || smem != ClusterSmem<M>::bytes(N, Tc)) fail("cluster smem", M, N, T, smem);
     }
     if (accepted < 4000) fail("cluster accepts fewer than 4000 frames", M, N, accepted, accepted);
-    const size_t wide_dyn = mwf_wide_smem(M, N);
-    const size_t wide_static = sizeof(float2) * M * (M + 1) + sizeof(float) * M * kMwfWMaxN +
-                               sizeof(float2) * 2 * kMwfWFrames * M + sizeof(float) * 2 * kMwfWMaxN * kMwfWFrames;
-    if (wide_dyn + wide_static > kDynMax || wide_static > kStaticMax) fail("wide filter smem", M, N, 0, wide_dyn);
-    if (kMwfWRow(M) % 2 || kMwfWRow(M) < M) fail("wide filter z row", M, N, 0, kMwfWRow(M));
+    // tiled filter: P threads per frame hold R rows each, covering the M rows, a whole number
+    // of frames per warp; shared memory of one CTA, 16-byte alignment of every region and staged
+    // frame (bulk copies), staged frames in odd 16-byte strides (conflict-free 16-byte stores)
+    const MwfTileLayout L = mwf_tile_layout(M, N);
+    if (mwf_tile_smem(M, N) > kDynMax) fail("tile filter smem", M, N, 0, mwf_tile_smem(M, N));
+    if (L.k % 16 || L.wc % 16 || L.lt % 16 || L.h % 16 || L.out % 16 || L.total % 16)
+      fail("tile filter region alignment", M, N, 0, L.total);
+    if (mwf_tile_p(M) * mwf_tile_r(M) < M || (mwf_tile_p(M) - 1) * mwf_tile_r(M) >= M || 32 % mwf_tile_p(M) ||
+        mwf_tile_frames(M) * mwf_tile_p(M) != 32)
+      fail("tile filter threads per frame", M, N, mwf_tile_p(M), mwf_tile_r(M));
+    // 16-byte vector accesses: every row segment a thread reads or writes starts on 16 bytes
+    if (mwf_tile_vec(M))
+      for (int qq = 0; qq < mwf_tile_p(M); ++qq)
+        for (int a = 0; a < M; ++a)
+          for (int n = 0; n < N; ++n)
+            if ((a * M + qq * mwf_tile_r(M)) % 2 || ((n * M + a) * M + qq * mwf_tile_r(M)) % 2 ||
+                (n * M + qq * mwf_tile_r(M)) % 2 || mwf_tile_r(M) % 2)
+              fail("tile filter vector alignment", M, N, a, qq);
+    const int FB = mwf_tile_frame_bytes(N, M);
+    if (FB % 16 || (FB / 16) % 2 == 0 || FB < N * M * 8) fail("tile filter frame stride", M, N, 0, FB);
+    if (L.wc - L.k < N * M * M * 8 || L.lt - L.wc < M * M * 8 || L.h - L.lt < kMwfWMaxN * M * 4 ||
+        L.out - L.h < kMwfWMaxN * mwf_tile_frames(M) * 4)
+      fail("tile filter region size", M, N, 0, L.total);
   }
   if (kCThreads > 1024 || kCThreads % 32) fail("cluster threads", M, 0, 0, kCThreads);
 }
@@ -123,7 +141,28 @@ void check_all_n() {
 
 }  // namespace
 
+// tiled filter: the warps' contiguous ranges [gw G / nw, (gw + 1) G / nw) of the G tiles
+// cover every tile once, and no two warps' ranges differ by more than one tile
+void check_tile_ranges() {
+  const int grids[] = {1, 7, 152, 304, 456};
+  const long long Gs[] = {1, 3, 255, 1216, 4100, 128125, 256250};
+  for (int grid : grids)
+    for (long long G : Gs) {
+      const long long nw = (long long)grid * kMwfTWarps;
+      long long next = 0, lo = G, hi = 0;
+      for (long long gw = 0; gw < nw; ++gw) {
+        const long long g0 = gw * G / nw, g1 = (gw + 1) * G / nw;
+        if (g0 != next || g1 < g0) fail("tile filter tile ranges", grid, 0, (int)G, (int)gw);
+        next = g1;
+        lo = std::min(lo, g1 - g0);
+        hi = std::max(hi, g1 - g0);
+      }
+      if (next != G || hi - lo > 1) fail("tile filter tile cover", grid, 0, (int)G, (int)(hi - lo));
+    }
+}
+
 int main() {
+  check_tile_ranges();
   check_all_n<2>();
   check_all_n<3>();
   check_all_n<4>();
