@@ -288,9 +288,28 @@ def run_batch(shapes, data, dev, stream):
     bt.close()
     sec = np.median(np.array(secs), axis=0)
     ms = float(np.median(times))
+    # the same mixtures one at a time: one single-mixture context each, launched in a row on
+    # one stream (device-resident, the same iterations), for the comparison with the batch
+    seps = [fastfca.Separator(xs[b], shapes[b][1], stream=stream.cuda_stream) for b in range(len(shapes))]
+    seq = []
+    for _ in range(3):
+        for b, s_ in enumerate(seps):
+            s_.set_params(*inits[b])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s_ in seps:
+            s_.iterate_async(BATCH_ITERS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    for s_ in seps:
+        s_.close()
+    ms_seq = float(np.median(seq))
     return {"value": units / (ms * 1e-3), "unit": UNIT, "mixtures": BATCH_B, "iters": BATCH_ITERS,
             "ms_per_launch": ms, "per_mixture_ms_p50": float(np.percentile(sec, 50) * 1e3),
             "per_mixture_ms_p99": float(np.percentile(sec, 99) * 1e3),
+            "one_at_a_time_value": units / (ms_seq * 1e-3), "one_at_a_time_ms": ms_seq,
             "schedule": {"bucketing": scheme, "grid_factor": factor},
             "config": "M in {2,3,4}, N in M+1..M+3, F=513, T uniform [200,2000], one CUDA-graph launch"}
 

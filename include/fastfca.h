@@ -251,9 +251,11 @@ fastfca_status fastfca_debug_f64_reciprocals(int32_t n, const double* x, double*
 /* ------------------------------------------------------------------------------------------
  * Batches: many independent mixtures (mixed M, N, T) iterated together in one CUDA-graph
  * launch.  Each (mixture, frequency) pair is one work item run by one CTA with the same code
- * as the single-mixture path; items are grouped into classes by (M, N) and a frame bucket,
- * each class is one persistent launch whose CTAs take items longest-first from an atomic
- * counter, and all classes run concurrently on forked streams inside one captured graph.
+ * as the single-mixture path.  Two kinds of schedule: (a) items grouped into classes by
+ * (M, N) and a frame bucket, each class one persistent launch whose CTAs take items
+ * longest-first from an atomic counter, all classes concurrent on forked streams; (b) one
+ * single-mixture launch per mixture (one CTA per frequency), the mixtures spread
+ * longest-first over concurrent branches.  Either is captured once per n_iter in one graph.
  * (Not in the paper: FastFCA processes frequencies independently, Sec. IV-G, so independent
  * mixtures batch naturally.)
  */
@@ -279,7 +281,9 @@ fastfca_status fastfca_batch_get_params(fastfca_batch* batch, int32_t b, void* P
  * config.model says) on every frequency of every mixture with one graph launch (the graph is
  * captured on first use of each n_iter and reused).  Optional host outputs: ll_per_mixture[b]
  * = sum_f l_f after the last iteration; seconds_per_mixture[b] = the span between the first
- * start and the last end of mixture b's items inside the launch (%globaltimer).  With either
+ * start and the last end of mixture b's items inside the launch (%globaltimer; under schedule
+ * 3 the time between CUDA events around mixture b's launch, which then goes out directly
+ * rather than through the graph).  With either
  * output the call synchronises; otherwise it is asynchronous.  Mixtures are independent: on
  * FASTFCA_ENUMERIC the outputs are still filled, ll_per_mixture[b] is non-finite for each
  * mixture that failed, and the others' results are valid.  A failed mixture keeps reporting
@@ -287,12 +291,14 @@ fastfca_status fastfca_batch_get_params(fastfca_batch* batch, int32_t b, void* P
 fastfca_status fastfca_batch_iterate(fastfca_batch* batch, int32_t n_iter, double* ll_per_mixture,
                                      double* seconds_per_mixture);
 
-/* Autotuner: times every candidate schedule (frame bucketing: fine / coarse / one per (M, N);
- * grid share factor 1, 2 or 4) on this batch with n_iter iterations, restores the parameters,
- * and keeps the fastest.  *scheme and *factor (may be NULL) receive the choice. */
+/* Autotuner: times every candidate schedule (frame bucketing: fine / coarse / one per (M, N),
+ * with grid share factor 1, 2 or 4; or one launch per mixture on 2, 4, 8 or 16 branches) on this
+ * batch with n_iter iterations, restores the parameters, and keeps the fastest.  *scheme and
+ * *factor (may be NULL) receive the choice. */
 fastfca_status fastfca_batch_tune(fastfca_batch* batch, int32_t n_iter, int32_t* scheme, double* factor);
 
-/* Sets a schedule directly (scheme 0 fine, 1 coarse, 2 one per (M, N); factor > 0). */
+/* Sets a schedule directly (scheme 0 fine, 1 coarse, 2 one per (M, N): factor > 0 scales each
+ * class's persistent grid; scheme 3 one launch per mixture: round(2 factor) branches). */
 fastfca_status fastfca_batch_schedule(fastfca_batch* batch, int32_t scheme, double factor);
 
 /* Wiener-filter separation of mixture b into c (complex64 [F][T][N][M], device). */

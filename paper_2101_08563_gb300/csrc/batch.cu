@@ -8,6 +8,14 @@
 // whole batch.  The schedule (bucketing of T into CTA sizes, CTAs per class) is chosen by a
 // small autotuner that times each candidate on the batch itself (fastfca_batch_tune).
 // %globaltimer stamps per item give each mixture's wall time inside the launch.
+//
+// One more schedule runs each mixture as one launch of the single-mixture kernel (one CTA per
+// frequency, all of them in one wave), the mixtures spread longest-first over a few concurrent
+// branches of the graph so that one launch's tail overlaps the next launch's start.  Measured
+// on the 64-mixture batch (M in {2,3,4}, T in [200, 2000], 20 iterations), the per-class
+// persistent launches took 44.5 ms and the same 64 single-mixture launches in a row 35.9 ms:
+// co-resident CTAs of many classes, each running items of its own size, used the SMs worse
+// than one mixture's uniform wave.  The tuner measures this schedule beside the others.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,7 +61,8 @@ struct Class {
 };
 
 // Frame-bucket schemes the tuner chooses between.
-enum Scheme { kFine = 0, kCoarse = 1, kSingle = 2, kNumSchemes = 3 };
+// kMixture: one single-mixture launch per mixture, on 2 x factor concurrent graph branches.
+enum Scheme { kFine = 0, kCoarse = 1, kSingle = 2, kMixture = 3, kNumSchemes = 4 };
 
 int bucket_threads(int scheme, int T, int group_max_T) {
   auto warps_for = [](int t) { return std::max(1, (t + 32 * ffca::kSlots - 1) / (32 * ffca::kSlots)); };
@@ -80,6 +89,9 @@ struct fastfca_batch {
   std::map<int, cudaGraphExec_t> graphs;
   int scheme = kFine;
   double grid_factor = 1.0;
+  bool have_schedule = false;
+  std::vector<std::vector<int>> branch_mix;   // kMixture: the mixtures of each branch, in order
+  std::vector<cudaEvent_t> tev;              // kMixture: start / end events per mixture (timing)
   int sms = 0;
   fastfca_status sticky = FASTFCA_OK;
   char msg[512] = "";
@@ -172,17 +184,59 @@ void free_batch(fastfca_batch* b) {
   ffca::dev_free(b->d_err);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
+  for (auto e : b->tev) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->capture) cudaStreamDestroy(b->capture);
 }
 
 double item_cost(const ffca::EmItem& it, int M, int N) { return (double)it.T * (double)(M * M + M * N + 8); }
 
+fastfca_status ensure_side_streams(fastfca_batch* b, size_t n) {
+  while (b->side.size() < n) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    BCK(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "side stream");
+    BCK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side event");
+    b->side.push_back(s);
+    b->ev.push_back(e);
+  }
+  if (!b->fork) BCK(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+  return FASTFCA_OK;
+}
+
+// The kMixture schedule: 2 x factor branches; mixtures longest-first, each to the branch with
+// the least work so far.
+fastfca_status build_mixture_schedule(fastfca_batch* b, double grid_factor) {
+  const int nb = std::max(1, std::min<int>((int)std::lround(2.0 * grid_factor), (int)b->mix.size()));
+  std::vector<std::pair<double, int>> order;
+  for (size_t i = 0; i < b->mix.size(); ++i) {
+    const fastfca_config& c = b->mix[i].cfg;
+    order.push_back({(double)c.F * c.T * (double)(c.M * c.M + c.M * c.N + 8), (int)i});
+  }
+  std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& z) { return a.first > z.first; });
+  b->branch_mix.assign(nb, {});
+  std::vector<double> load(nb, 0.0);
+  for (const auto& w : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->branch_mix[j].push_back(w.second);
+    load[j] += w.first;
+  }
+  const fastfca_status st = ensure_side_streams(b, (size_t)nb);
+  if (st) return st;
+  b->scheme = kMixture;
+  b->grid_factor = grid_factor;
+  b->have_schedule = true;
+  return FASTFCA_OK;
+}
+
 // Builds the classes of a schedule: bucket the items, order each class longest first, size
 // each class's persistent grid by its share of the work and the occupancy of its kernel.
 fastfca_status build_classes_once(fastfca_batch* b, int scheme, double grid_factor) {
   free_graphs(b);
   free_classes(b);
+  b->have_schedule = false;
+  b->branch_mix.clear();
+  if (scheme == kMixture) return build_mixture_schedule(b, grid_factor);
   std::map<std::pair<int, int>, int> group_max_T;
   for (const auto& m : b->mix) {
     auto key = std::make_pair(m.cfg.M, m.cfg.N);
@@ -233,18 +287,12 @@ fastfca_status build_classes_once(fastfca_batch* b, int scheme, double grid_fact
         "batch item upload");
     BCK(b, ffca::dev_malloc(&c.d_counter, sizeof(int)), "batch counter alloc");
   }
-  while (b->side.size() < b->classes.size()) {
-    cudaStream_t s;
-    cudaEvent_t e;
-    BCK(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "side stream");
-    BCK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side event");
-    b->side.push_back(s);
-    b->ev.push_back(e);
-  }
-  if (!b->fork) BCK(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+  const fastfca_status st = ensure_side_streams(b, b->classes.size());
+  if (st) return st;
   b->scheme = scheme;
   b->grid_factor = grid_factor;
   BCK(b, cudaStreamSynchronize(b->stream), "batch schedule upload");
+  b->have_schedule = true;
   return FASTFCA_OK;
 }
 
@@ -268,8 +316,47 @@ fastfca_status build_classes(fastfca_batch* b, int scheme, double grid_factor, i
   return st;
 }
 
+// kMixture: each branch's mixtures, one single-mixture launch each (B = W^{-H} formed at the
+// start of every launch), between start / end events of each mixture when `timed`.
+fastfca_status enqueue_mixtures(fastfca_batch* b, int n_iter, cudaStream_t origin, bool timed) {
+  BCK(b, cudaEventRecord(b->fork, origin), "fork record");
+  for (size_t j = 0; j < b->branch_mix.size(); ++j) {
+    cudaStream_t s = b->side[j];
+    BCK(b, cudaStreamWaitEvent(s, b->fork, 0), "fork wait");
+    for (int i : b->branch_mix[j]) {
+      Mix& m = b->mix[i];
+      ffca::EmArgs a{};
+      a.x = m.x;
+      a.xh = nullptr;
+      a.P = m.P;
+      a.lam = m.lam;
+      a.v = m.v;
+      a.ll_hist = nullptr;
+      a.ll_last = m.ll_last;
+      a.Bst = m.Bst;
+      a.detst = m.detst;
+      a.b_valid = 0;
+      a.err = b->d_err;
+      a.F = m.cfg.F;
+      a.T = m.cfg.T;
+      a.n_iter = n_iter;
+      a.ll_stride = 0;
+      a.N = m.cfg.N;
+      a.clocks = nullptr;
+      if (timed) BCK(b, cudaEventRecord(b->tev[2 * i], s), "mixture start record");
+      const bool mm = m.cfg.model == FASTFCA_MODEL_FASTFCA_MM;
+      BCK(b, mm ? m.ops.em_mm(a, s) : m.ops.em(a, s), "mixture launch");
+      if (timed) BCK(b, cudaEventRecord(b->tev[2 * i + 1], s), "mixture end record");
+    }
+    BCK(b, cudaEventRecord(b->ev[j], s), "join record");
+    BCK(b, cudaStreamWaitEvent(origin, b->ev[j], 0), "join wait");
+  }
+  return FASTFCA_OK;
+}
+
 // Enqueues every class launch: fork from `origin` onto side streams, join back onto it.
 fastfca_status enqueue_all(fastfca_batch* b, int n_iter, cudaStream_t origin) {
+  if (b->scheme == kMixture) return enqueue_mixtures(b, n_iter, origin, false);
   cudaEvent_t fork = b->fork;
   BCK(b, cudaEventRecord(fork, origin), "fork record");
   for (size_t ci = 0; ci < b->classes.size(); ++ci) {
@@ -469,12 +556,25 @@ fastfca_status fastfca_batch_iterate(fastfca_batch* b, int32_t n_iter, double* l
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
-  if (b->classes.empty())
+  if (!b->have_schedule)
     return bfail(b, FASTFCA_EINVAL, "the batch has no schedule (building one failed); call fastfca_batch_schedule");
-  cudaGraphExec_t exec = nullptr;
-  fastfca_status st = graph_for(b, n_iter, &exec);
-  if (st) return st;
-  BCK(b, cudaGraphLaunch(exec, b->stream), "graph launch");
+  const bool timed_mix = seconds_per_mixture && b->scheme == kMixture;
+  if (timed_mix) {
+    // per-mixture spans from events around each launch: the launches go out directly
+    // (the same launches as the graph's), not through the graph
+    while (b->tev.size() < 2 * b->mix.size()) {
+      cudaEvent_t e;
+      BCK(b, cudaEventCreate(&e), "timing event");
+      b->tev.push_back(e);
+    }
+    const fastfca_status st = enqueue_mixtures(b, n_iter, b->stream, true);
+    if (st) return st;
+  } else {
+    cudaGraphExec_t exec = nullptr;
+    fastfca_status st = graph_for(b, n_iter, &exec);
+    if (st) return st;
+    BCK(b, cudaGraphLaunch(exec, b->stream), "graph launch");
+  }
   if (!ll_per_mixture && !seconds_per_mixture) return FASTFCA_OK;
   // ENUMERIC still fills the outputs: mixtures are independent, the failed ones read
   // non-finite there and the others are valid.
@@ -490,7 +590,13 @@ fastfca_status fastfca_batch_iterate(fastfca_batch* b, int32_t n_iter, double* l
       ll_per_mixture[i] = s;
     }
   }
-  if (seconds_per_mixture) {
+  if (timed_mix) {
+    for (size_t i = 0; i < b->mix.size(); ++i) {
+      float ms = 0.f;
+      BCK(b, cudaEventElapsedTime(&ms, b->tev[2 * i], b->tev[2 * i + 1]), "mixture span");
+      seconds_per_mixture[i] = (double)ms * 1e-3;
+    }
+  } else if (seconds_per_mixture) {
     std::vector<unsigned long long> st2(2 * b->items.size());
     BCK(b, cudaMemcpy(st2.data(), b->d_stamps, sizeof(unsigned long long) * st2.size(), cudaMemcpyDeviceToHost),
         "stamp download");
@@ -512,7 +618,7 @@ fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* cho
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (n_iter < 1) return bfail(b, FASTFCA_EINVAL, "n_iter must be >= 1");
-  const int orig_scheme = b->classes.empty() ? -1 : b->scheme;
+  const int orig_scheme = b->have_schedule ? b->scheme : -1;
   const double orig_factor = b->grid_factor;
   // snapshot the parameters: the probes iterate on them.  Every exit below frees the
   // snapshot and the events, and puts the parameters back once the snapshot is complete.
@@ -549,12 +655,13 @@ fastfca_status fastfca_batch_tune(fastfca_batch* b, int32_t n_iter, int32_t* cho
   };
   if (!st) st = bcheck(b, cudaEventCreate(&e0), "tune event");
   if (!st) st = bcheck(b, cudaEventCreate(&e1), "tune event");
-  const double factors[] = {1.0, 2.0, 4.0};
+  const double factors[] = {1.0, 2.0, 4.0, 8.0};     // 8: the per-mixture schedule only (16 branches)
   float best_ms = 1e30f;
   int best_scheme = kFine;
   double best_factor = 1.0;
   for (int scheme = 0; scheme < kNumSchemes && !st; ++scheme) {
     for (double fac : factors) {
+      if (fac > 4.0 && scheme != kMixture) continue;
       st = build_classes(b, scheme, fac, -1, 0.0);
       if (st) break;
       st = restore();
@@ -602,7 +709,7 @@ fastfca_status fastfca_batch_schedule(fastfca_batch* b, int32_t scheme, double g
   if (!b) return FASTFCA_EINVAL;
   if (b->sticky == FASTFCA_ECUDA) return b->sticky;
   if (scheme < 0 || scheme >= kNumSchemes || !(grid_factor > 0.0)) return bfail(b, FASTFCA_EINVAL, "bad schedule");
-  return build_classes(b, scheme, grid_factor, b->classes.empty() ? -1 : b->scheme, b->grid_factor);
+  return build_classes(b, scheme, grid_factor, b->have_schedule ? b->scheme : -1, b->grid_factor);
 }
 
 fastfca_status fastfca_batch_separate(fastfca_batch* b, int32_t i, void* c) {

@@ -384,7 +384,7 @@ class Batch:
     Algorithm 2).
     """
 
-    SCHEMES = {0: "fine", 1: "coarse", 2: "single"}
+    SCHEMES = {0: "fine", 1: "coarse", 2: "single", 3: "mixture"}
 
     def __init__(self, xs, Ns, stream=None, seeds=None, models=None):
         self.lib = load()
@@ -444,15 +444,16 @@ class Batch:
                                                       _ptr(v, np.float32, v.shape, "v", True)[0]))
         return P, lam, v
 
-    def iterate(self, n_iter, stats=True):
-        """Returns (log-likelihood per mixture, seconds per mixture) when stats, else None."""
+    def iterate(self, n_iter, stats=True, seconds=True):
+        """Returns (log-likelihood per mixture, seconds per mixture or None) when stats, else
+        None; seconds=False leaves the per-mixture spans out."""
         if not stats:
             self._check(self.lib.fastfca_batch_iterate(self._h, int(n_iter), None, None))
             return None
         ll = np.empty(self.B, np.float64)
-        sec = np.empty(self.B, np.float64)
+        sec = np.empty(self.B, np.float64) if seconds else None
         st = self.lib.fastfca_batch_iterate(self._h, int(n_iter), ll.ctypes.data_as(ctypes.c_void_p),
-                                            sec.ctypes.data_as(ctypes.c_void_p))
+                                            sec.ctypes.data_as(ctypes.c_void_p) if seconds else None)
         if st == STATUS_ENUMERIC:
             # the log-likelihoods are filled anyway: non-finite for the mixtures that failed
             err = FastFCAError(st, self.lib.fastfca_batch_last_error(self._h).decode())

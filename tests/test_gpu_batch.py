@@ -57,6 +57,40 @@ def test_batch_fine_schedule_equals_single_path_bitwise(ff):
     bt.close()
 
 
+def test_batch_mixture_schedule(ff):
+    """One single-mixture launch per mixture on concurrent graph branches (schedule 3), with
+    Algorithm 1 and Algorithm 2 mixtures mixed.  The first call after set_params equals the
+    single-mixture path bit for bit (both form B = W^{-H} from W at the start); a second call
+    (B formed again, where the single path carries it) continues the oracle's trajectory; the
+    timed form (seconds requested: direct launches between events) gives the same results as
+    the graph."""
+    items = mixed_batch(seed=21, B=7, F=5)
+    models = ["fastfca_mm" if b % 3 == 1 else "fastfca" for b in range(len(items))]
+    xs = [torch.from_numpy(m.x).cuda() for m, _, _ in items]
+    bt = ff.Batch(xs, [N for _, _, N in items], models=models)
+    bt.schedule("mixture", 2.0)
+    for b, (m, init, N) in enumerate(items):
+        bt.set_params(b, init.P, init.lam, init.v)
+    ll1, sec = bt.iterate(3)
+    assert np.all(sec > 0)
+    for b, (m, init, N) in enumerate(items):
+        sep = ff.Separator(xs[b], N, model=models[b])
+        sep.set_params(init.P, init.lam, init.v)
+        sep.iterate(3, return_ll=False)
+        tot = sep.loglik()
+        Ps, ls, vs = sep.get_params()
+        sep.close()
+        Pb, lb, vb = bt.get_params(b)
+        assert np.array_equal(Pb, Ps) and np.array_equal(lb, ls) and np.array_equal(vb, vs), (b, models[b])
+        assert ll1[b] == pytest.approx(tot, rel=1e-12)
+    bt.iterate(2, stats=False)                   # through the graph
+    ll2, _ = bt.iterate(1, seconds=False)        # through the graph, log-likelihoods read back
+    for b, (m, init, N) in enumerate(items):
+        ref = off.run(m.x, init.P, init.lam, init.v, iters=6, algorithm="mm" if models[b] == "fastfca_mm" else "em")
+        assert ll2[b] == pytest.approx(ref["ll"][:, -1].sum(), rel=1e-5), b
+    bt.close()
+
+
 def test_batch_tuned_matches_oracle_and_resumes(ff):
     items = mixed_batch(seed=3, B=6, F=4)
     xs = [torch.from_numpy(m.x).cuda() for m, _, _ in items]
@@ -64,7 +98,7 @@ def test_batch_tuned_matches_oracle_and_resumes(ff):
     for b, (m, init, N) in enumerate(items):
         bt.set_params(b, init.P, init.lam, init.v)
     scheme, factor = bt.tune(2)                  # probes restore the parameters
-    assert scheme in ("fine", "coarse", "single") and factor > 0
+    assert scheme in ("fine", "coarse", "single", "mixture") and factor > 0
     ll1, _ = bt.iterate(3)
     ll2, _ = bt.iterate(2)                       # graph reuse for a new n_iter, resume
     for b, (m, init, N) in enumerate(items):
