@@ -44,6 +44,7 @@
 // b_m <- b_m / (w_m^H b_m), where w_m^H b_m = sqrt(s); and |det W|^2 is multiplied by s.
 #pragma once
 #include "common.cuh"
+#include "tmem.cuh"
 
 namespace ffca {
 
@@ -362,8 +363,13 @@ struct EmItem {
 
 // The whole IP+EM run of one frequency by one CTA (see the file comment).  `smem_raw` is the
 // CTA's dynamic shared memory (EmSmem<M, N>::bytes(blockDim.x)); T <= blockDim.x * kSlots.
-template <int M, int N, bool MM = false, bool BL = false>
-__device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned char* smem_raw) {
+// TM (IP+EM only): sigma^2 of every frame kept in tensor memory, 4 columns per frame slot
+// (32 columns per four warps), and updated by each source's change in the n-loop instead of
+// recomputed as L H from all sources; pass A still forms it from L H once per iteration.
+// tmem_slot: one 32-bit word of shared memory for the allocation's address.
+template <int M, int N, bool MM = false, bool BL = false, bool TM = false>
+__device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned char* smem_raw,
+                                             uint32_t* tmem_slot = nullptr) {
   using SM = EmSmem<M, N>;
   constexpr int QCH = SM::kQCH, MC = SM::kMC, V = SM::kV, VP = SM::kVP;
   constexpr int MP = pow2_ceil(M);
@@ -397,6 +403,19 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
   const float* xhf = q.xh;
   const double invT = 1.0 / (double)T;
   const float invTf = 1.0f / (float)T;
+
+  // ---- tensor memory for sigma^2 (TM): warp 0 allocates; warps w and w + 4 share a lane
+  // quarter and take column groups 0 and 1; slot k of a thread at columns 4k of its group
+  static_assert(!TM || (!MM && M <= 4), "sigma^2 in tensor memory: IP+EM, M <= 4");
+  const unsigned tm_cols = nw > 4 ? 64u : 32u;
+  uint32_t tm_base = 0;
+  if constexpr (TM) {
+    if (warp == 0) tmem_alloc(tmem_slot, tm_cols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    tm_base = *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+  }
 
   // ---- load the parameters of frequency f
   for (int i = tid; i < M * N; i += bd) sL[i] = q.lam[i];
@@ -575,6 +594,7 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
         const int t = tid + k * bd;
+        float s2v[4] = {1.f, 1.f, 1.f, 1.f};
         if (t < T) {
           if (!MM && it > 0) {
             float g = 0.f;
@@ -593,10 +613,15 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
             bad |= !(s2 > 0.f && s2 < INFINITY);
             const float rs = fast_rcp(s2);
             r[k][m] = rs;
+            if constexpr (TM) s2v[m] = s2;
             if (have_ll) llp += fmaf(pU[k * M + m], rs, __logf(s2));
           }
         }
+        if constexpr (TM) {
+          if (k * bd < T) tmem_st4(tm_base + 4 * k, s2v);         // uniform over the CTA
+        }
       }
+      if constexpr (TM) tmem_wait_st();
       if (bad) atomicOr(err, kErrSigma);
       if (have_ll) {
         llp = warp_sum(llp);
@@ -788,11 +813,15 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
     } else {
       // ---- NMF EM sweep over sources (Algorithm 1 n-loop, Gauss-Seidel).  Pass n applies
       // the H[n-1,:] update of the previous source, then forms r for source n.
+      // L[:, n-1] before and after its update (TM: the change of sigma^2 it makes)
+      float Lold[M], Lnew[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) Lold[m] = Lnew[m] = 0.f;
 #pragma unroll 1
       for (int n = 0; n < N; ++n) {
         float* pHn = pH + n;                   // this thread's H[n, .] (slot k at k*N)
         float Lr[M][N];
-        load_L(Lr);
+        if constexpr (!TM) load_L(Lr);
         float Ln[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) Ln[m] = sL[m * N + n];
@@ -802,22 +831,43 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
 #pragma unroll
         for (int k = 0; k < kSlots; ++k) {
           const int t = tid + k * bd;
+          float s2v[4] = {1.f, 1.f, 1.f, 1.f};
+          if constexpr (TM) {
+            if (k * bd < T) tmem_ld4(tm_base + 4 * k, s2v);       // uniform over the CTA
+          }
           if (t < T) {
             if (n > 0) {
               float g = 0.f;
 #pragma unroll
               for (int m = 0; m < M; ++m) g = fmaf(r[k][m], coef[m], g);
-              pHn[k * N - 1] *= g;
-            }
-            float h[N];
+              const float hold = pHn[k * N - 1];
+              const float hnew = hold * g;
+              pHn[k * N - 1] = hnew;
+              if constexpr (TM) {
 #pragma unroll
-            for (int n2 = 0; n2 < N; ++n2) h[n2] = pH[k * N + n2];
+                for (int m = 0; m < M; ++m) {
+                  // sigma^2 <- sigma^2 - L H + L' H', never below the new term: the rest of
+                  // the sum, clamped at zero, plus the new term in one fma
+                  const float rest = fmaxf(fmaf(-Lold[m], hold, s2v[m]), 0.f);
+                  s2v[m] = fmaf(Lnew[m], hnew, rest);
+                }
+              }
+            }
             const float hn = pHn[k * N];
+            float h[N];
+            if constexpr (!TM) {
+#pragma unroll
+              for (int n2 = 0; n2 < N; ++n2) h[n2] = pH[k * N + n2];
+            }
 #pragma unroll
             for (int m = 0; m < M; ++m) {
               float s2 = 0.f;
+              if constexpr (TM) {
+                s2 = s2v[m];
+              } else {
 #pragma unroll
-              for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
+                for (int n2 = 0; n2 < N; ++n2) s2 = fmaf(Lr[m][n2], h[n2], s2);
+              }
               const float rs = fast_rcp(s2);
               const float G = Ln[m] * hn * rs;
               const float rr = fmaf(G, fmaf(pU[k * M + m], rs, -1.f), 1.f);
@@ -825,7 +875,11 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
               acc[m] += rr;
             }
           }
+          if constexpr (TM) {
+            if (n > 0 && k * bd < T) tmem_st4(tm_base + 4 * k, s2v);
+          }
         }
+        if constexpr (TM) tmem_wait_st();
         warp_reduce_scatter<MP>(acc, lane);
         {
           float* red = sRed + par * kMaxWarps * SM::kRedW + warp * SM::kRedW;
@@ -840,6 +894,8 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
           const float mean = tot[m] * invTf;
           sL[m * N + n] = Ln[m] * mean;       // same value from every thread
           coef[m] = fast_rcp(mean) * (1.0f / (float)M);
+          Lold[m] = Ln[m];
+          Lnew[m] = Ln[m] * mean;
         }
         FFCA_MARK(it, 5 + (n < 9 ? n : 9));
       }
@@ -863,10 +919,18 @@ __device__ __forceinline__ void em_frequency(const EmItem& q, int* err, unsigned
     float* vf = q.v + (size_t)n * T;
     for (int t = tid; t < T; t += bd) vf[t] = sH[(t % bd) * SH + (t / bd) * N + n];
   }
+  // ---- release the tensor memory once every thread's accesses are complete
+  if constexpr (TM) {
+    tmem_wait_st();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_dealloc(*tmem_slot, tm_cols);
+  }
 }
 
 
-template <int M, int N, bool MM = false, bool BL = false>
+template <int M, int N, bool MM = false, bool BL = false, bool TM = false>
 __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   const int f = blockIdx.x;
   if (f >= p.F) return;
@@ -891,7 +955,8 @@ __global__ void __maxnreg__(kEmMaxRegs) fastfca_em_kernel(EmArgs p) {
   q.T = p.T;
   q.n_iter = p.n_iter;
   q.b_valid = p.b_valid;
-  em_frequency<M, N, MM, BL>(q, p.err, smem_raw);
+  __shared__ uint32_t tmem_slot;
+  em_frequency<M, N, MM, BL, TM>(q, p.err, smem_raw, &tmem_slot);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {

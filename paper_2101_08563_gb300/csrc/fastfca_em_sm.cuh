@@ -39,76 +39,6 @@ constexpr int kSMaxM = 8;
 constexpr unsigned kSCols = 512;             // TMEM columns allocated: all of them
 constexpr int kSColsPerSlot = 16;            // sigma^2 (8 columns), then U (8 columns)
 
-// ------------------------------------------------------------------ tensor-memory access
-// Allocation by one warp (the address lands in shared memory); the CTA gives up its right to
-// allocate more at once, so no other CTA ever waits on it.
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, unsigned ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tmem_fence_before_sync() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_fence_after_sync() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Loads and stores of this thread's TMEM lane.  Tensor memory is outside the C++ memory
-// model: the data moves only through the asm operands, so the asm carries no memory clobber
-// and the compiler may move ordinary global and shared accesses across it (volatile keeps the
-// TMEM accesses in program order among themselves).  Each load waits for its data (wait::ld)
-// and each store for its completion (wait::st) inside the same asm, so an operand is never
-// read early and a later load of the same columns sees the store.
-//
-// Eight consecutive 32-bit columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-      : "r"(taddr));
-  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
-  v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
-}
-
-// Sixteen consecutive columns (sigma^2 then U of one frame).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&a)[8], float (&b)[8]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    a[i] = __uint_as_float(r[i]);
-    b[i] = __uint_as_float(r[8 + i]);
-  }
-}
-
-// Eight columns stored, without waiting: a pass stores each of its slots once and ends with
-// tmem_wait_st, before any later load of those columns.
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
-}
-
-// Waits until every TMEM store of this thread has completed.
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
 
 // ------------------------------------------------------------------ shared-memory layout
 template <int M>

@@ -36,17 +36,45 @@ inline int em_threads(int T) {
   return (warps < 1 ? 1 : warps) * 32;
 }
 
+// Dynamic shared memory for the IP+EM kernel with sigma^2 in tensor memory: at least its
+// layout's, and enough more that the CTAs one SM holds at once never ask for more than the
+// SM's 512 TMEM columns together (32 columns per CTA up to four warps, 64 above), so no
+// allocation ever waits.  0 when that cannot be arranged.
+template <typename Kernel>
+size_t em_tm_smem(Kernel kernel, int threads, size_t smem) {
+  const int cap = 512 / (threads > 128 ? 64 : 32);
+  int dev = 0, per_sm_smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return 0;
+  for (size_t dyn = smem; dyn <= (size_t)per_sm_smem; dyn += 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, dyn) != cudaSuccess) return 0;
+    if (nb >= 1 && nb <= cap) return dyn;
+  }
+  return 0;
+}
+
 template <int M, int N, bool MM = false, bool BL = false>
 cudaError_t launch_em(const EmArgs& a, cudaStream_t s) {
   const int threads = em_threads(a.T);
   if (threads > kMaxThreads) return cudaErrorInvalidConfiguration;
   if (BL && !a.xh) return cudaErrorInvalidValue;
   const size_t smem = EmSmem<M, N>::bytes(threads);
-  cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N, MM, BL>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  fastfca_em_kernel<M, N, MM, BL><<<a.F, threads, smem, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (!MM) {
+    // IP+EM keeps sigma^2 in tensor memory (the n-loop then updates it by each source's change)
+    const size_t dyn = em_tm_smem(fastfca_em_kernel<M, N, false, BL, true>, threads, smem);
+    if (dyn == 0) return cudaErrorInvalidConfiguration;
+    fastfca_em_kernel<M, N, false, BL, true><<<a.F, threads, dyn, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(fastfca_em_kernel<M, N, MM, BL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fastfca_em_kernel<M, N, MM, BL><<<a.F, threads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 template <int M>
