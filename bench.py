@@ -930,7 +930,7 @@ def main():
         "roofline": em_roofline(w, r["em_ms"], peaks, "fastfca_em_sm_kernel<8> (one CTA per frequency, sigma^2 and U in TMEM)",
                                 em_traffic("fastfca_em_large")),
         "roofline_separation": separation_roofline(w, r["sep_ms"], peaks,
-                                                   "bst_to_winv_kernel + fastfca_mwf_wide_kernel<8>"),
+                                                   "bst_to_winv_kernel + fastfca_mwf_tile_kernel<8>"),
         "clocks": r["clocks"],
         "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"], "windows": r["e2e_windows"],
