@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -225,6 +226,7 @@ constexpr int GUM = 128, GUN = 64, GUK = 64;
 constexpr int kGemmThreads = 128;
 constexpr unsigned kGemmCols = 64;                   // TMEM columns of the FP32 accumulator
 constexpr int kGemmSpin = 1 << 20;
+constexpr int kGemmMaxSplit = 16;                    // K slices of a split product
 constexpr size_t kGemmSmemA = GUM * GUK * 2, kGemmSmemB = GUN * GUK * 2;
 // 29 KB of shared memory per CTA caps an SM at 7 CTAs: 7 x 64 <= 512 TMEM columns, so no CTA
 // ever waits for tensor memory
@@ -252,7 +254,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd,
                                                                 long long sam, long long sak, const float* __restrict__ B,
                                                                 long long sbn, long long sbk,
                                                                 const float* __restrict__ bias, float* __restrict__ C,
-                                                                long long ldc, int* status) {
+                                                                long long ldc, int kchunk, float* __restrict__ part,
+                                                                int* status) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   unsigned char* sA = gsm;
   unsigned char* sB = gsm + kGemmSmemA;
@@ -272,16 +275,19 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd,
   const uint32_t aBase = (uint32_t)__cvta_generic_to_shared(sA), bBase = (uint32_t)__cvta_generic_to_shared(sB);
   unsigned phase = 0;
   bool failed = false;
-  const int nkb = (Kd + GUK - 1) / GUK;
+  // split K (part != null): slice blockIdx.z takes K range [z kchunk, min(Kd, (z + 1) kchunk))
+  const int kbeg = part ? (int)blockIdx.z * kchunk : 0;
+  const int kend = part ? min(Kd, kbeg + kchunk) : Kd;
+  const int nkb = (kend - kbeg + GUK - 1) / GUK;
   for (int kb = 0; kb < nkb; ++kb) {
-    const int k0 = kb * GUK;
+    const int k0 = kbeg + kb * GUK;
     // stage the block's tiles as BF16 (coalesced along whichever stride is 1)
     for (int e = 0; e < GUM * GUK / kGemmThreads; ++e) {
       const int i = tid + e * kGemmThreads;
       int row, col;
       if (sak == 1) { row = i / GUK; col = i % GUK; } else { row = i % GUM; col = i / GUM; }
       const int m = m0 + row, k = k0 + col;
-      const float val = (m < Md && k < Kd) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
+      const float val = (m < Md && k < kend) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
       *reinterpret_cast<__nv_bfloat16*>(sA + kmajor_offset(row, col)) = __float2bfloat16(val);
     }
     for (int e = 0; e < GUN * GUK / kGemmThreads; ++e) {
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd,
       int row, col;
       if (sbk == 1) { row = i / GUK; col = i % GUK; } else { row = i % GUN; col = i / GUN; }
       const int n = n0 + row, k = k0 + col;
-      const float val = (n < Nd && k < Kd) ? B[(long long)n * sbn + (long long)k * sbk] : 0.f;
+      const float val = (n < Nd && k < kend) ? B[(long long)n * sbn + (long long)k * sbk] : 0.f;
       *reinterpret_cast<__nv_bfloat16*>(sB + kmajor_offset(row, col)) = __float2bfloat16(val);
     }
     // the tensor cores read shared memory through the async proxy
@@ -337,7 +343,10 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd,
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c4 * 16 + j;
           const float v = j < 8 ? a8[j] : b8[j - 8];
-          if (n < Nd) C[(long long)m * ldc + n] = v + (bias ? bias[n] : 0.f);
+          if (n < Nd) {
+            if (part) part[((size_t)blockIdx.z * Md + m) * Nd + n] = v;
+            else C[(long long)m * ldc + n] = v + (bias ? bias[n] : 0.f);
+          }
         }
       }
     }
@@ -347,12 +356,47 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(int Md, int Nd,
   if (warp == 0) tmem_dealloc(d_tmem, kGemmCols);
 }
 
+// C = sum over the split slices (fixed order) + bias
+__global__ void gemm_split_sum_kernel(int Md, int Nd, int S, const float* __restrict__ part,
+                                      const float* __restrict__ bias, float* __restrict__ C, long long ldc) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)Md * Nd) return;
+  const int m = (int)(i / Nd), n = (int)(i - (size_t)m * Nd);
+  float acc = 0.f;
+  for (int z = 0; z < S; ++z) acc += part[(size_t)z * Md * Nd + i];
+  C[(long long)m * ldc + n] = acc + (bias ? bias[n] : 0.f);
+}
+
+// C[m][n] = sum_k A(m,k) B(n,k) (+ bias[n]).  When the output tiles are too few to fill the
+// GPU and K is long (the weight gradients: K = the batch's rows), K is split over up to
+// kGemmMaxSplit slices of the grid (workspace ws, ws_elems floats), each slice's product goes to
+// its own part of ws, and a second kernel adds the slices in a fixed order: the result does not
+// depend on scheduling.
 cudaError_t gemm(int Md, int Nd, int Kd, const float* A, long long sam, long long sak, const float* B, long long sbn,
-                 long long sbk, const float* bias, float* C, long long ldc, int* status, cudaStream_t s) {
+                 long long sbk, const float* bias, float* C, long long ldc, float* ws, size_t ws_elems, int* status,
+                 cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmDynSmem);
   if (e != cudaSuccess) return e;
-  dim3 grid((Nd + GUN - 1) / GUN, (Md + GUM - 1) / GUM);
-  gemm_bf16_kernel<<<grid, kGemmThreads, kGemmDynSmem, s>>>(Md, Nd, Kd, A, sam, sak, B, sbn, sbk, bias, C, ldc, status);
+  const int gx = (Nd + GUN - 1) / GUN, gy = (Md + GUM - 1) / GUM;
+  const int nkb = (Kd + GUK - 1) / GUK;
+  int S = 1;
+  if (ws && gx * gy < 76 && nkb >= 4) {
+    S = std::min(std::min(kGemmMaxSplit, nkb / 2), std::max(1, 152 / (gx * gy)));
+    while (S > 1 && (size_t)S * Md * Nd > ws_elems) --S;
+  }
+  if (S == 1) {
+    gemm_bf16_kernel<<<dim3(gx, gy), kGemmThreads, kGemmDynSmem, s>>>(Md, Nd, Kd, A, sam, sak, B, sbn, sbk, bias, C, ldc,
+                                                                      0, nullptr, status);
+    return cudaGetLastError();
+  }
+  const int kchunk = ((nkb + S - 1) / S) * GUK;
+  S = (Kd + kchunk - 1) / kchunk;
+  gemm_bf16_kernel<<<dim3(gx, gy, S), kGemmThreads, kGemmDynSmem, s>>>(Md, Nd, Kd, A, sam, sak, B, sbn, sbk, nullptr,
+                                                                       C, ldc, kchunk, ws, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t n = (size_t)Md * Nd;
+  gemm_split_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Md, Nd, S, ws, bias, C, ldc);
   return cudaGetLastError();
 }
 
@@ -720,6 +764,8 @@ struct fastfca_net {
   float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *o = nullptr;
   float *dout = nullptr, *d2 = nullptr, *d1 = nullptr, *dconv = nullptr, *loss = nullptr, *scal = nullptr;
   int* gstat = nullptr;         // device status of the tensor-core products (bit 1: a wait ran out)
+  float* gws = nullptr;         // split-K partial products (kGemmMaxSplit x the largest weight gradient)
+  size_t gws_elems = 0;
   int step = 0;
   char msg[256] = "";
 };
@@ -763,12 +809,12 @@ fastfca_status net_status(fastfca_net* n) {
 fastfca_status net_forward(fastfca_net* n, int rows, const float* feats) {
   cudaStream_t s = n->stream;
   const float* P = n->params;
-  NCK(n, gemm(rows, kHidden, kDin, feats, kDin, 1, P + n->off_W1, kDin, 1, P + n->off_b1, n->z1, kHidden, n->gstat, s), "gemm 1");
+  NCK(n, gemm(rows, kHidden, kDin, feats, kDin, 1, P + n->off_W1, kDin, 1, P + n->off_b1, n->z1, kHidden, n->gws, n->gws_elems, n->gstat, s), "gemm 1");
   gelu_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z1, n->h1);
-  NCK(n, gemm(rows, kHidden, kHidden, n->h1, kHidden, 1, P + n->off_W2, kHidden, 1, P + n->off_b2, n->z2, kHidden, n->gstat, s),
+  NCK(n, gemm(rows, kHidden, kHidden, n->h1, kHidden, 1, P + n->off_W2, kHidden, 1, P + n->off_b2, n->z2, kHidden, n->gws, n->gws_elems, n->gstat, s),
       "gemm 2");
   gelu_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z2, n->h2);
-  NCK(n, gemm(rows, kOutPad, kHidden, n->h2, kHidden, 1, P + n->off_W3, kHidden, 1, P + n->off_b3, n->o, kOutPad, n->gstat, s),
+  NCK(n, gemm(rows, kOutPad, kHidden, n->h2, kHidden, 1, P + n->off_W3, kHidden, 1, P + n->off_b3, n->o, kOutPad, n->gws, n->gws_elems, n->gstat, s),
       "gemm 3");
   return FASTFCA_OK;
 }
@@ -805,17 +851,17 @@ fastfca_status net_loss_grad(fastfca_net* n, int rows, int T, const float* feats
   const int NKc = n->N * kConvK + n->N;
   colsum_kernel<<<blocks(NKc, 32), 256, 0, s>>>(rows, NKc, n->dconv, NKc, G + n->off_k);
   // backward through the MLP
-  NCK(n, gemm(kOutPad, kHidden, rows, n->dout, 1, kOutPad, n->h2, 1, kHidden, nullptr, G + n->off_W3, kHidden, n->gstat, s), "dW3");
+  NCK(n, gemm(kOutPad, kHidden, rows, n->dout, 1, kOutPad, n->h2, 1, kHidden, nullptr, G + n->off_W3, kHidden, n->gws, n->gws_elems, n->gstat, s), "dW3");
   colsum_kernel<<<blocks(kOutPad, 32), 256, 0, s>>>(rows, kOutPad, n->dout, kOutPad, G + n->off_b3);
-  NCK(n, gemm(rows, kHidden, kOutPad, n->dout, kOutPad, 1, n->params + n->off_W3, 1, kHidden, nullptr, n->d2, kHidden, n->gstat, s),
+  NCK(n, gemm(rows, kHidden, kOutPad, n->dout, kOutPad, 1, n->params + n->off_W3, 1, kHidden, nullptr, n->d2, kHidden, n->gws, n->gws_elems, n->gstat, s),
       "dh2");
   gelu_back_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z2, n->d2);
-  NCK(n, gemm(kHidden, kHidden, rows, n->d2, 1, kHidden, n->h1, 1, kHidden, nullptr, G + n->off_W2, kHidden, n->gstat, s), "dW2");
+  NCK(n, gemm(kHidden, kHidden, rows, n->d2, 1, kHidden, n->h1, 1, kHidden, nullptr, G + n->off_W2, kHidden, n->gws, n->gws_elems, n->gstat, s), "dW2");
   colsum_kernel<<<blocks(kHidden, 32), 256, 0, s>>>(rows, kHidden, n->d2, kHidden, G + n->off_b2);
-  NCK(n, gemm(rows, kHidden, kHidden, n->d2, kHidden, 1, n->params + n->off_W2, 1, kHidden, nullptr, n->d1, kHidden, n->gstat, s),
+  NCK(n, gemm(rows, kHidden, kHidden, n->d2, kHidden, 1, n->params + n->off_W2, 1, kHidden, nullptr, n->d1, kHidden, n->gws, n->gws_elems, n->gstat, s),
       "dh1");
   gelu_back_kernel<<<blocks((size_t)rows * kHidden, 256), 256, 0, s>>>((size_t)rows * kHidden, n->z1, n->d1);
-  NCK(n, gemm(kHidden, kDin, rows, n->d1, 1, kHidden, feats, 1, kDin, nullptr, G + n->off_W1, kDin, n->gstat, s), "dW1");
+  NCK(n, gemm(kHidden, kDin, rows, n->d1, 1, kHidden, feats, 1, kDin, nullptr, G + n->off_W1, kDin, n->gws, n->gws_elems, n->gstat, s), "dW1");
   colsum_kernel<<<blocks(kHidden, 32), 256, 0, s>>>(rows, kHidden, n->d1, kHidden, G + n->off_b1);
   NCK(n, cudaGetLastError(), "backward launches");
   if (loss) {
@@ -914,6 +960,8 @@ fastfca_status fastfca_net_create(int32_t M, int32_t N, int32_t max_rows, int32_
   if ((e = ffca::dev_malloc(&n->loss, sizeof(float) * (size_t)max_rows)) != cudaSuccess) return bail("loss", e);
   if ((e = ffca::dev_malloc(&n->scal, sizeof(float) * 4)) != cudaSuccess) return bail("scalar", e);
   if ((e = ffca::dev_malloc(&n->gstat, sizeof(int))) != cudaSuccess) return bail("status", e);
+  n->gws_elems = (size_t)kGemmMaxSplit * kHidden * kHidden;
+  if ((e = ffca::dev_malloc(&n->gws, sizeof(float) * n->gws_elems)) != cudaSuccess) return bail("GEMM workspace", e);
   cudaMemsetAsync(n->gstat, 0, sizeof(int), n->stream);
   cudaMemsetAsync(n->adam_m, 0, sizeof(float) * c, n->stream);
   cudaMemsetAsync(n->adam_v, 0, sizeof(float) * c, n->stream);
@@ -946,6 +994,7 @@ void fastfca_net_destroy(fastfca_net* n) {
                    n->dconv, n->loss, n->scal})
     ffca::dev_free(p);
   ffca::dev_free(n->gstat);
+  ffca::dev_free(n->gws);
   delete n;
 }
 
