@@ -40,15 +40,23 @@ inline int em_threads(int T) {
 // layout's, and enough more that the CTAs one SM holds at once never ask for more than the
 // SM's 512 TMEM columns together (32 columns per CTA up to four warps, 64 above), so no
 // allocation ever waits.  0 when that cannot be arranged.
+// The kernel's dynamic shared memory limit is set once to the device's opt-in maximum (a
+// permission, not a reservation: occupancy follows the size each launch asks for), so that
+// launches of one instantiation with different sizes, captured in one graph, never see a
+// lower limit than they were made with.
 template <typename Kernel>
 size_t em_tm_smem(Kernel kernel, int threads, size_t smem) {
   const int cap = 512 / (threads > 128 ? 64 : 32);
-  int dev = 0, per_sm_smem = 0;
+  int dev = 0, per_sm_smem = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
-  for (size_t dyn = smem; dyn <= (size_t)per_sm_smem; dyn += 1024) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || fa.sharedSizeBytes >= (size_t)optin) return 0;
+  const int max_dyn = optin - (int)fa.sharedSizeBytes;      // the limit counts dynamic bytes only
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn) != cudaSuccess) return 0;
+  for (size_t dyn = smem; dyn <= (size_t)std::min(per_sm_smem, max_dyn); dyn += 1024) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, dyn) != cudaSuccess) return 0;
     if (nb >= 1 && nb <= cap) return dyn;
