@@ -152,11 +152,13 @@ def test_batch_mixed_algorithms(ff):
     bt.close()
 
 
-def test_batch_bench_schedule_matches_oracle(ff):
-    """The schedule the benchmark's tuner picks for its 64-mixture batch (fine frame buckets,
-    grid share factor 4) on mixtures of the benchmark's frequency count range (F = 64) and
-    frame range (T up to 2000): every mixture's log-likelihood after each iteration, its final
-    parameters and its images against the oracle from the same start."""
+@pytest.mark.parametrize("scheme,factor", [("fine", 4.0), ("mixture", 8.0)])
+def test_batch_bench_schedule_matches_oracle(ff, scheme, factor):
+    """The schedules the benchmark's tuner picks for its 64-mixture batch (one launch per
+    mixture on 16 branches; before that, fine frame buckets with grid share factor 4) on
+    mixtures of the benchmark's frequency count range (F = 64) and frame range (T up to 2000):
+    every mixture's log-likelihood after each iteration, its final parameters and its images
+    against the oracle from the same start."""
     shapes = [(4, 7, 2000), (3, 6, 1650), (2, 5, 1210), (4, 5, 731), (3, 4, 203), (2, 3, 1999)]
     F, iters = 64, 3
     mixes, inits = [], []
@@ -166,7 +168,7 @@ def test_batch_bench_schedule_matches_oracle(ff):
         inits.append(synth.random_init(mix.x, N, seed=5100 + b))
     xs = [torch.from_numpy(m.x).cuda() for m in mixes]
     bt = ff.Batch(xs, [N for _, N, _ in shapes])
-    bt.schedule("fine", 4.0)
+    bt.schedule(scheme, factor)
     for b, init in enumerate(inits):
         bt.set_params(b, init.P, init.lam, init.v)
     lls = [bt.iterate(1)[0] for _ in range(iters)]      # the log-likelihood after each iteration
