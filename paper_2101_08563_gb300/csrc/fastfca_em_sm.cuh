@@ -484,9 +484,9 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
     if (!do_iter) break;
 
     // ---- Q_m = (1/T) sum_t x x^H / sigma^2_m (Eq. 33).  Warp w takes a contiguous block of
-    // frames; one load instruction brings 4 frames x 8 channels (lane 8 f + a holds x_a of
-    // frame f); each lane forms its two entries from four shuffled values and accumulates
-    // them for every m with the weights 1/sigma^2 read as two broadcast float4.
+    // frames; one load instruction brings 4 frames x 8 channels (lane 8 f + a loads x_a of
+    // frame f) into shared memory; each lane forms its two entries from two values read there
+    // and accumulates them for every m with the weights 1/sigma^2 read as two broadcast float4.
     {
       float acc[M][2];
 #pragma unroll
@@ -494,36 +494,35 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       const int per = (T + kSWarps - 1) / kSWarps;
       const int fb = warp * per, fe = min(fb + per, T);
       const int lf = lane >> 3, la = lane & 7;
+      // the block's x staged in this warp's 1 KB of the last-source H buffer (dead from pass A
+      // until the n-loop's first source): 16 frames x 8 channels
+      float2* sX = reinterpret_cast<float2*>(sHp) + warp * 128;
 #pragma unroll 1
-      for (int base = fb; base < fe; base += 32) {
-        float2 xr[8];
+      for (int base = fb; base < fe; base += 16) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 4; ++k) {
           const int fr = base + 4 * k + lf;
-          xr[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+          sX[(4 * k + lf) * 8 + la] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
         }
+        __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int fi = 0; fi < 16; ++fi) {
+          const int fr = base + fi;                    // warp-uniform
+          if (fr >= fe) break;
+          const float2 xa = sX[fi * 8 + ja], xb = sX[fi * 8 + jb];
+          const float ax = xa.x, ay = xa.y, bx = xb.x, by = xb.y;
+          const float v0 = (jkind == 0) ? fmaf(ax, bx, ay * by) : fmaf(ax, ax, ay * ay);
+          const float v1 = (jkind == 0) ? fmaf(ay, bx, -ax * by) : fmaf(bx, bx, by * by);
+          const float4 w0 = *reinterpret_cast<const float4*>(sRr + 4 * fr);
+          const float4 w1 = *reinterpret_cast<const float4*>(sRr + 4 * kSMaxT + 4 * fr);
+          const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-          for (int fi = 0; fi < 4; ++fi) {
-            const int fr = base + 4 * k + fi;          // warp-uniform
-            if (fr >= fe) break;
-            const float ax = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + ja);
-            const float ay = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + ja);
-            const float bx = __shfl_sync(0xffffffffu, xr[k].x, fi * 8 + jb);
-            const float by = __shfl_sync(0xffffffffu, xr[k].y, fi * 8 + jb);
-            const float v0 = (jkind == 0) ? fmaf(ax, bx, ay * by) : fmaf(ax, ax, ay * ay);
-            const float v1 = (jkind == 0) ? fmaf(ay, bx, -ax * by) : fmaf(bx, bx, by * by);
-            const float4 w0 = *reinterpret_cast<const float4*>(sRr + 4 * fr);
-            const float4 w1 = *reinterpret_cast<const float4*>(sRr + 4 * kSMaxT + 4 * fr);
-            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-              acc[m][0] = fmaf(wv[m], v0, acc[m][0]);
-              acc[m][1] = fmaf(wv[m], v1, acc[m][1]);
-            }
+          for (int m = 0; m < M; ++m) {
+            acc[m][0] = fmaf(wv[m], v0, acc[m][0]);
+            acc[m][1] = fmaf(wv[m], v1, acc[m][1]);
           }
         }
+        __syncwarp();                                  // the block's reads before the next stores
       }
       // per-warp partials, summed in a fixed order: warp w + 8 onto warp w, then warps 0..7
       if (warp >= kSWarps / 2) {
