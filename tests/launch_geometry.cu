@@ -108,6 +108,8 @@ void check_sm() {
   if (SmSmem<M>::bytes > kDynMax) fail("sm smem", M, 0, 0, SmSmem<M>::bytes);
   if (SmSmem<M>::oHp < sizeof(float) * 8 * (size_t)kSMaxT) fail("sm r planes", M, 0, 0, SmSmem<M>::oHp);
   if (SmSmem<M>::oQw - SmSmem<M>::oHp < sizeof(float) * (size_t)kSSlots * kSThreads) fail("sm h slots", M, 0, 0, SmSmem<M>::oQw);
+  // the Q pass's x blocks sit in the H slots (16 frames x 8 channels per warp)
+  if (sizeof(float) * (size_t)kSSlots * kSThreads < sizeof(float) * 2 * 16 * 8 * kSWarps) fail("sm q x blocks", M, 0, 0, 0);
   for (int T = 1; T <= kSMaxT; ++T) {
     const int KF = (T + kSThreads - 1) / kSThreads;
     if (KF > kSSlots || KF * kSThreads < T) fail("sm frame slots", M, 0, T, KF);
