@@ -469,6 +469,9 @@ class Batch:
         return self.SCHEMES[scheme.value], factor.value
 
     def schedule(self, scheme, factor=1.0):
+        """Sets the schedule: "fine", "coarse" or "single" frame bucketing of the persistent
+        class launches (factor scales each class's grid), or "mixture": one single-mixture
+        launch per mixture on round(2 factor) concurrent graph branches."""
         code = {v: k for k, v in self.SCHEMES.items()}[scheme] if isinstance(scheme, str) else int(scheme)
         self._check(self.lib.fastfca_batch_schedule(self._h, code, ctypes.c_double(factor)))
 
