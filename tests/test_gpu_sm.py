@@ -207,3 +207,25 @@ def test_frequency_ranges_run_alone_equal_the_whole_run(ff):
         part.close()
         assert np.array_equal(P, Pw[f0:f1]) and np.array_equal(lam, lw[f0:f1]) and np.array_equal(v, vw[f0:f1])
     assert np.allclose(ll_sum, ll_whole, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("M,N,T", [(8, 12, 1001), (6, 9, 611)])
+def test_filter_output_on_an_8_byte_boundary(ff, M, N, T):
+    """The large-bin filter writes each frame's images with one bulk copy when the output
+    starts on 16 bytes, and with plain stores otherwise (c on an 8-byte boundary, which the
+    API accepts): both give the same bits, ragged last tile included."""
+    mix = mixture(M, N, 2, T, 3)
+    init = synth.random_init(mix.x, N, seed=3)
+    sep = ff.Separator(torch.from_numpy(mix.x).cuda(), N)
+    sep.set_params(init.P, init.lam, init.v)
+    sep.iterate(2, return_ll=False)
+    n = 2 * T * N * M
+    aligned = torch.empty(n, dtype=torch.complex64, device="cuda")
+    base = torch.empty(n + 1, dtype=torch.complex64, device="cuda")
+    shifted = base[1:]
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    sep.separate(aligned.view(2, T, N, M))
+    sep.separate(shifted.view(2, T, N, M))
+    torch.cuda.synchronize()
+    sep.close()
+    assert torch.equal(aligned, shifted)
