@@ -318,7 +318,8 @@ def run_batch(shapes, data, dev, stream):
 def run_learned(n_train):
     """The learned initialiser end to end on the GPU: n_train generated mixtures of the
     learned-initialiser workload with 200-iteration FastFCA targets, 6 epochs of training, and
-    the comparison with the default start on 512 held-out mixtures (batched as one context)."""
+    the comparison of the default start with two learned starts (the network's W, L and H; the
+    network's W with the default L and H) on 512 held-out mixtures (batched as one context)."""
     import torch
     from paper_2101_08563_gb300 import learned as L
     w = synth.WORKLOADS["learned"]

@@ -301,12 +301,13 @@ def _timed_replay(sep, iters, before=None):
 
 def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3, conv=1e-6, early_iters=200,
              stream=None):
-    """Learned start vs the default start on n_mix held-out mixtures, batched as one context.
+    """Learned starts vs the default start on n_mix held-out mixtures, batched as one context.
 
-    Both starts are run to convergence (until no mixture's log-likelihood changes by more than
-    `conv` per bin in an iteration, at most max_iters iterations).  The reference of a mixture
-    is the better of the two converged log-likelihoods; a start has reached it once it is
-    within tol per bin (tol F T) of it.  Each start is then replayed, bit for bit the same
+    Three starts: the default one ("plain"), the network's W, L and H ("learned"), and the
+    network's W with the default start's L and H ("learned_w").  Each is run to convergence
+    (until no mixture's log-likelihood changes by more than `conv` per bin in an iteration, at
+    most max_iters iterations).  The reference of a mixture is the best of the three converged
+    log-likelihoods; a start has reached it once it is within tol per bin (tol F T) of it.  Each start is then replayed, bit for bit the same
     run, with a CUDA event after every iteration: its time to the reference is measured from
     the start (for the learned start: features, network, prediction, upload) to the iteration
     that crosses.  Reports, per start, the iterations and seconds at which 50 % and 90 % of the
@@ -335,31 +336,49 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
 
     learned_start()
     tr_learned, why_learned = _ll_trace(sep, n_mix, F, T, max_iters, conv)
-    ref = np.maximum(tr_plain[-1], tr_learned[-1])
+    # the network's W alone, with the default start's L and H
+    sep_w = ff.Separator(x, N, stream=stream, seed=0)
+
+    def learned_w_start():
+        feats, q = features(x, F, stream)
+        P, _, _ = net.predict(feats, q)
+        sep_w.set_params(P, lam0, v0)
+
+    learned_w_start()
+    tr_w, why_w = _ll_trace(sep_w, n_mix, F, T, max_iters, conv)
+    ref = np.maximum(np.maximum(tr_plain[-1], tr_learned[-1]), tr_w[-1])
     ref_early = tr_plain[min(early_iters, tr_plain.shape[0]) - 1]
 
     def first_hit(tr, r):
         hit = tr >= (r - tol * bins)[None, :]
         return np.where(hit.any(axis=0), hit.argmax(axis=0) + 1, np.inf)
 
-    hits = {name: first_hit(tr, ref) for name, tr in (("plain", tr_plain), ("learned", tr_learned))}
-    hits_early = {name: first_hit(tr, ref_early) for name, tr in (("plain", tr_plain), ("learned", tr_learned))}
+    traces = (("plain", tr_plain), ("learned", tr_learned), ("learned_w", tr_w))
+    hits = {name: first_hit(tr, ref) for name, tr in traces}
+    hits_early = {name: first_hit(tr, ref_early) for name, tr in traces}
     # timed replays of the same runs, up to the last crossing of either reference
     times, t_start = {}, {}
     for name, ctx, start in (("plain", plain, lambda: plain.set_params(P0, lam0, v0)),
-                             ("learned", sep, learned_start)):
+                             ("learned", sep, learned_start), ("learned_w", sep_w, learned_w_start)):
         fin = np.concatenate([hits[name][np.isfinite(hits[name])], hits_early[name][np.isfinite(hits_early[name])]])
         kmax = int(fin.max()) if fin.size else 1
         t_start[name], times[name] = _timed_replay(ctx, kmax, before=start)
     plain.close()
     sep.close()
+    sep_w.close()
     res = {"n_mix": n_mix, "max_iters": max_iters, "tol_per_bin": tol, "conv_per_bin": conv,
-           "iters_run": {"plain": int(tr_plain.shape[0]), "learned": int(tr_learned.shape[0])},
-           "trace_stopped": {"plain": why_plain, "learned": why_learned},
-           "reference": "per mixture, the better of the two starts' converged log-likelihoods",
+           "iters_run": {"plain": int(tr_plain.shape[0]), "learned": int(tr_learned.shape[0]),
+                         "learned_w": int(tr_w.shape[0])},
+           "trace_stopped": {"plain": why_plain, "learned": why_learned, "learned_w": why_w},
+           "starts": {"plain": "the default start (fastfca_create's W = I, L = 1, seeded H)",
+                      "learned": "the network's W, L and H",
+                      "learned_w": "the network's W with the default start's L and H"},
+           "reference": "per mixture, the best of the three starts' converged log-likelihoods",
            "timing": "CUDA events after every iteration of a replay of the same run, from the start "
                      "(the learned start's features, network, prediction and upload included)",
            "learned_ends_below_default_fraction": float(np.mean(tr_learned[-1] < tr_plain[-1] - tol * bins)),
+           "learned_w_ends_above_default_fraction": float(np.mean(tr_w[-1] > tr_plain[-1] + tol * bins)),
+           "learned_w_ends_below_default_fraction": float(np.mean(tr_w[-1] < tr_plain[-1] - tol * bins)),
            "learned_start_seconds": float(t_start["learned"]),
            "seconds_per_iteration": float(np.median(np.diff(times["plain"]))) if len(times["plain"]) > 1 else None}
     def crossing(name, its):
@@ -375,7 +394,7 @@ def evaluate(net, n_mix, F, T, M, N, K, spacing, seed, max_iters=1000, tol=1e-3,
     res[f"to_default_{early_iters}"] = {
         "reference": f"per mixture, the default start's log-likelihood after {early_iters} iterations "
                      f"(the training targets' iteration count), within tol per bin"}
-    for name, tr in (("plain", tr_plain), ("learned", tr_learned)):
+    for name, tr in traces:
         out = crossing(name, hits[name])
         out["converged_fraction"] = out.pop("reached_fraction")
         out.update({"final_ll_per_bin_minus_ref": float(np.median((tr[-1] - ref) / bins)),

@@ -326,6 +326,9 @@ def test_trained_network_gains_early_and_stays_near_the_converged_optimum(L, tra
     # the learned start may settle in a lower optimum; the loss stays small
     assert q["final_ll_per_bin_minus_ref"] >= -0.05
     assert p["final_ll_per_bin_minus_ref"] >= -0.05
+    # the network's W alone (default L and H) is reported beside them, timed the same way
+    w = res["learned_w"]
+    assert w["final_ll_per_bin_minus_ref"] >= -0.05 and res["to_default_200"]["learned_w"]["reached_fraction"] > 0
 
 
 def test_trajectory_from_the_learned_start_matches_the_oracle(L, trained):
