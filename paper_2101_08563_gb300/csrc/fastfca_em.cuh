@@ -16,7 +16,10 @@
 // The per-frame quantities r_{mt} (see below) stay in registers of the owning thread.
 // Phase 2 of source n (the H[n,:] update) and phase 1 of source n+1 run in one pass over
 // the frames, so each source costs one CTA barrier; the last phase 2 shares its pass with
-// the next iteration's sigma^2 / log-likelihood pass.
+// the next iteration's sigma^2 / log-likelihood pass.  The single-mixture launch (the TM
+// flag, IP+EM) keeps sigma^2 of every frame in tensor memory: pass A forms it as L H, and
+// after each source's update the n-loop changes it by that source's term (never below the
+// new term) instead of forming L H again from all N sources.
 //
 // NMF update in factored form.  With S = L[:,n] H[n,:], G = S / sigma^2 and
 // Phi = G^2 U + (1 - G) S, one has Phi = S * r with r = 1 + G (U / sigma^2 - 1).  Hence
