@@ -497,14 +497,23 @@ __global__ void __launch_bounds__(kSThreads, 1) fastfca_em_sm_kernel(EmArgs p) {
       // the block's x staged in this warp's 1 KB of the last-source H buffer (dead from pass A
       // until the n-loop's first source): 16 frames x 8 channels
       float2* sX = reinterpret_cast<float2*>(sHp) + warp * 128;
+      // the next block's x is loaded into registers while this block is accumulated
+      float2 xn[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int fr = fb + 4 * k + lf;
+        xn[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+      }
 #pragma unroll 1
       for (int base = fb; base < fe; base += 16) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int fr = base + 4 * k + lf;
-          sX[(4 * k + lf) * 8 + la] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
-        }
+        for (int k = 0; k < 4; ++k) sX[(4 * k + lf) * 8 + la] = xn[k];
         __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int fr = base + 16 + 4 * k + lf;
+          xn[k] = (fr < fe && la < M) ? __ldg(xf + (size_t)fr * M + la) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int fi = 0; fi < 16; ++fi) {
           const int fr = base + fi;                    // warp-uniform
